@@ -1,0 +1,528 @@
+#!/usr/bin/env python
+"""Benchmark of the Plenoxels optimisation step on one GB300 (or N replicas under torchrun).
+
+Workload (default, the 512^3 configuration the headline metric is quoted on): a
+synthetic 512^3 grid with 3% of nodes occupied (20 Gaussian density blobs plus a
+thin shell, SH ~ N(0, 0.2), the training grid = that ground truth + N(0, 0.02)),
+100 cameras of 800x800 on the upper hemisphere, 5000-ray batches drawn uniformly
+from all pixels, step 0.5 voxel, white background.  One step runs every
+per-step kernel of the method: ray generation, forward march, MSE gradient,
+adjoint, TV gradient on 1% of the nodes in 4096-node segments (Supp. A.1), and
+the sparse RMSProp update.  Targets are the ground truth rendered by the same
+kernels before timing.  The grid (1.0 GB in FP32) exceeds the 129 MB L2, and
+every step uses a different batch; L2 is not flushed between steps.
+
+Prints one JSON line: value = fwd+bwd rays/s of the whole step (FP32 rows),
+plus the BF16-SH form, full-frame render latency (p50/p99 over 25 held-out
+800x800 views), the roofline of the dominant kernel, an end-to-end number
+through the public API with host buffers, the CPU oracle baseline, grid
+prune/upsample timings and the SM clocks seen during the timed region.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "fwd+bwd rays/s on 512^3 sparse grid (FP32 vs BF16-SH); render p50/p99 ms; HBM frac"
+
+WORKLOADS = {
+    # name: (scene, R, cameras, W, H, n_views, test cameras)
+    "sparse512": ("sparse512", 512, "hemi100_800", 800, 800, 100, "hemi25_800_test"),
+    "sparse256": ("sparse256", 256, "hemi100_800", 800, 800, 100, "hemi25_800_test"),
+    "dense32": ("dense32", 32, "sphere8_64", 64, 64, 8, None),
+}
+
+
+def parse_args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=60)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", default="sparse512", choices=sorted(WORKLOADS))
+    ap.add_argument("--batch", type=int, default=5000)
+    ap.add_argument("--n-batches", type=int, default=16)
+    ap.add_argument("--render-reps", type=int, default=20)
+    ap.add_argument("--no-extras", action="store_true", help="only the headline step timing")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0, help="budget of the CPU oracle baseline")
+    return ap.parse_args()
+
+
+# --------------------------------------------------------------------------- helpers
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons while the timed region runs."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.idx = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.idx), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        for line in open(self.path):
+            p = [x.strip() for x in line.split(",")]
+            if len(p) < 9:
+                continue
+            try:
+                sm.append(float(p[1]))
+                smax.append(float(p[2]))
+            except ValueError:
+                continue
+            for name, val in zip(("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"),
+                                 p[5:9]):
+                if val.lower() == "active":
+                    reasons.add(name)
+        os.unlink(self.path)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"], "samples": 0}
+        hi = [x for x in sm if x > 0.5 * max(sm)]
+        return {"sm_mhz": statistics.median(hi), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def dist_setup():
+    import torch
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.barrier()
+
+
+def max_over_ranks(x: float, world: int) -> float:
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def sum_over_ranks(x: float, world: int) -> float:
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+# --------------------------------------------------------------------------- workload
+def build_workload(args, seed_offset=0):
+    import synth
+
+    scene_name, R, cam_name, W, H, n_views, test_cams = WORKLOADS[args.workload]
+    t0 = time.time()
+    gt = synth.scene_config(scene_name, seed=0)
+    train = synth.perturb(gt, 0.02, seed=1)
+    cams = synth.cameras_config(cam_name)
+    batches = []
+    for b in range(args.n_batches):
+        pix = synth.pixel_batch(n_views, W, H, args.batch, seed=1000 + b + seed_offset)
+        ss, sl = synth.tv_segments(R, 0.01, 4096 if R >= 128 else 256, seed=2000 + b + seed_offset)
+        batches.append((pix, ss, sl))
+    return dict(R=R, W=W, H=H, n_views=n_views, gt=gt, train=train, cams=cams, batches=batches,
+                test_cams=test_cams, gen_s=time.time() - t0)
+
+
+# --------------------------------------------------------------------------- our implementation
+def run_ours(args, world, rank, local):
+    import torch
+
+    from paper_2112_05131_gb300 import _lib
+    from paper_2112_05131_gb300.grid import Grid, RenderOpts, gen_rays
+    from paper_2112_05131_gb300.train import LAUNCHES_PER_STEP, StepConfig, Trainer, lr_sh, lr_sigma
+
+    _lib.load()
+    wl = build_workload(args, seed_offset=rank * 100000)
+    R, W, H = wl["R"], wl["W"], wl["H"]
+    dev = torch.device("cuda", torch.cuda.current_device())
+    stream = torch.cuda.current_stream()
+    opts = RenderOpts(0.5, (1.0, 1.0, 1.0), 0.0)
+    cams_t = torch.from_numpy(wl["cams"]).to(dev)
+
+    gt_grid = Grid.from_host(R, wl["gt"].idx, wl["gt"].rows)
+    dev_batches = []
+    for pix, ss, sl in wl["batches"]:
+        pix_t = torch.from_numpy(pix).to(dev)
+        o, d = gen_rays(cams_t, pix_t, W, H)
+        target = gt_grid.render(o, d, opts)
+        dev_batches.append((pix_t, target, torch.from_numpy(ss).to(dev), torch.from_numpy(sl).to(dev),
+                            int(sl.sum())))
+    torch.cuda.synchronize()
+
+    def timed_loop(grid, K, Wm, per_stage=True):
+        tr = Trainer(grid, cams_t, W, H, StepConfig(batch=args.batch, opts=opts))
+        nb = len(dev_batches)
+        for s in range(Wm):
+            b = dev_batches[s % nb]
+            tr.step(b[0], b[1], b[2], b[3], b[4], lr_sigma(s), lr_sh(s))
+        torch.cuda.synchronize()
+        evs = [[torch.cuda.Event(enable_timing=True) for _ in range(7)] for _ in range(K)] if per_stage else None
+        start, stop = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        barrier(world)
+        torch.cuda.synchronize()
+        clk = ClockSampler(local)
+        clk.start()
+        start.record(stream)
+        for s in range(K):
+            b = dev_batches[(Wm + s) % nb]
+            tr.step(b[0], b[1], b[2], b[3], b[4], lr_sigma(Wm + s), lr_sh(Wm + s),
+                    events=evs[s] if per_stage else None)
+        stop.record(stream)
+        torch.cuda.synchronize()
+        clocks = clk.stop()
+        barrier(world)
+        ms = start.elapsed_time(stop)
+        stages = None
+        if per_stage:
+            stages = {name: statistics.mean(e[i].elapsed_time(e[i + 1]) for e in evs)
+                      for i, name in enumerate(Trainer.STAGES)}
+        grid.check()
+        return ms, stages, clocks, tr
+
+    # ---- headline: FP32 rows
+    train32 = Grid.from_host(R, wl["train"].idx, wl["train"].rows)
+    ms32, st32, clocks, _ = timed_loop(train32, args.steps, args.warmup)
+    ms32 = max_over_ranks(ms32, world)
+    rays_total = sum_over_ranks(float(args.steps * args.batch), world)
+    value = rays_total / (ms32 / 1e3)
+    out = {
+        "metric": METRIC, "value": value, "unit": "rays/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms32 / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": f"{args.workload}: {R}^3 sparse grid "
+                               f"({wl['train'].M} rows, {100 * wl['train'].M / R ** 3:.2f}% occupied), "
+                               f"{args.batch}-ray batches from {wl['n_views']} views {W}x{H}, step 0.5 voxel, "
+                               "TV on 1% of nodes, sparse RMSProp",
+                   "global_batch": args.batch * world, "rays_per_step_per_gpu": args.batch,
+                   "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
+                   "l2": "grid exceeds the 129 MB L2 and every step uses a new batch; no flush"},
+        "gpu_launches": LAUNCHES_PER_STEP * args.steps,
+        "clocks": clocks,
+        "stage_ms": st32,
+    }
+    del train32
+    torch.cuda.empty_cache()
+
+    if rank == 0 and not args.no_extras:
+        out.update(extras(args, wl, dev_batches, cams_t, gt_grid, opts, timed_loop, st32, ms32))
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+
+
+def extras(args, wl, dev_batches, cams_t, gt_grid, opts, timed_loop, st32, ms32):
+    import torch
+
+    import synth
+    from paper_2112_05131_gb300.grid import Grid, gen_rays
+    from paper_2112_05131_gb300.train import StepConfig, Trainer, lr_sh, lr_sigma
+
+    R, W, H = wl["R"], wl["W"], wl["H"]
+    dev = cams_t.device
+    res = {}
+
+    # ---- BF16-SH form of the same step
+    train16 = Grid.from_host(R, wl["train"].idx, wl["train"].rows, sh_form=1)
+    ms16, st16, clocks16, _ = timed_loop(train16, args.steps, args.warmup)
+    res["bf16_sh"] = {"value": args.steps * args.batch / (ms16 / 1e3), "unit": "rays/s",
+                      "ms_per_step": ms16 / args.steps, "speedup_vs_f32": ms32 / ms16, "stage_ms": st16,
+                      "clocks": clocks16}
+    del train16
+    torch.cuda.empty_cache()
+
+    # ---- roofline of the dominant kernel (algorithmic bytes from the node counts of the timed batches)
+    peak, peak_kind = load_peaks()
+    train32 = Grid.from_host(R, wl["train"].idx, wl["train"].rows)
+    nodes = occ = 0
+    nb = len(dev_batches)
+    K, Wm = args.steps, args.warmup
+    for s in range(K):
+        b = dev_batches[(Wm + s) % nb]
+        o, d = gen_rays(cams_t, b[0], W, H)
+        c = train32.count_nodes(o, d, opts).sum(0).cpu().numpy()
+        nodes += int(c[0])
+        occ += int(c[1])
+    nodes /= K
+    occ /= K
+    n = args.batch
+    fwd_bytes = n * (24 + 12) + 4 * nodes + 112 * occ
+    bwd_bytes = 2 * (4 * nodes + 112 * occ) + n * (24 + 12) + 2 * 112 * occ
+    dom = max(st32, key=st32.get)
+    per_launch = {"render": fwd_bytes, "render_backward": bwd_bytes}
+    if dom in per_launch:
+        ach = per_launch[dom] / (st32[dom] / 1e3) / 1e9
+        res["roofline"] = {"kernel": dom, "bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s",
+                           "frac": ach / peak, "peak_source": f"{peak_kind} hbm_gbs (copy bandwidth)",
+                           "algorithmic_bytes_per_launch": per_launch[dom], "traffic": None}
+    res["algorithmic"] = {"distinct_nodes_per_ray": nodes / n, "occupied_nodes_per_ray": occ / n,
+                          "fwd_bytes_per_launch": fwd_bytes, "bwd_bytes_per_launch": bwd_bytes,
+                          "render_GBps": fwd_bytes / (st32["render"] / 1e3) / 1e9,
+                          "render_backward_GBps": bwd_bytes / (st32["render_backward"] / 1e3) / 1e9}
+
+    # ---- end to end through the public API with host buffers (pinned), copies inside the timed region
+    tr = Trainer(train32, cams_t, W, H, StepConfig(batch=args.batch, opts=opts))
+    host = []
+    for pix, ss, sl in wl["batches"]:
+        host.append((torch.from_numpy(pix).pin_memory(),
+                     None, torch.from_numpy(ss).pin_memory(), torch.from_numpy(sl).pin_memory(), int(sl.sum())))
+    host = [(h[0], dev_batches[i][1].cpu().pin_memory(), h[2], h[3], h[4]) for i, h in enumerate(host)]
+    d_pix = torch.empty(args.batch, dtype=torch.int64, device=dev)
+    d_tgt = torch.empty((args.batch, 3), dtype=torch.float32, device=dev)
+    max_seg = max(h[2].shape[0] for h in host)
+    d_ss = torch.empty(max_seg, dtype=torch.int64, device=dev)
+    d_sl = torch.empty(max_seg, dtype=torch.int64, device=dev)
+    loss_host = torch.empty(1, dtype=torch.float32).pin_memory()
+    stream = torch.cuda.current_stream()
+
+    def e2e_step(s):
+        h = host[s % nb]
+        ns = h[2].shape[0]
+        d_pix.copy_(h[0], non_blocking=True)
+        d_tgt.copy_(h[1], non_blocking=True)
+        d_ss[:ns].copy_(h[2], non_blocking=True)
+        d_sl[:ns].copy_(h[3], non_blocking=True)
+        tr.loss.zero_()
+        tr.step(d_pix, d_tgt, d_ss[:ns], d_sl[:ns], h[4], lr_sigma(s), lr_sh(s))
+        loss_host.copy_(tr.loss, non_blocking=True)
+
+    for s in range(args.warmup):
+        e2e_step(s)
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for s in range(K):
+        e2e_step(Wm + s)
+    b.record(stream)
+    torch.cuda.synchronize()
+    ms_e2e = a.elapsed_time(b)
+    h2d = args.batch * (8 + 12) + int(np.mean([h[2].shape[0] for h in host])) * 16
+    res["e2e"] = {"value": K * args.batch / (ms_e2e / 1e3), "unit": "rays/s", "h2d_bytes_per_step": h2d,
+                  "d2h_bytes_per_step": 4, "ms_per_step": ms_e2e / K}
+    del tr, train32
+    torch.cuda.empty_cache()
+
+    # ---- full-frame renders: 25 held-out 800x800 views, FP32 and BF16-SH
+    if wl["test_cams"]:
+        tc = synth.cameras_config(wl["test_cams"])
+        tc_t = torch.from_numpy(tc).to(dev)
+        npx = W * H
+        frames = []
+        for v in range(tc.shape[0]):
+            pix = torch.arange(v * npx, (v + 1) * npx, dtype=torch.int64, device=dev)
+            frames.append(gen_rays(tc_t, pix, W, H))
+        rgb = torch.empty((npx, 3), device=dev)
+        res["render"] = {}
+        for form, name in ((0, "f32"), (1, "bf16_sh")):
+            g = Grid.from_host(R, wl["gt"].idx, wl["gt"].rows, sh_form=form)
+            for o, d in frames[:3]:
+                g.render(o, d, opts, rgb)
+            times = []
+            for rep in range(args.render_reps):
+                for o, d in frames:
+                    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    e0.record(stream)
+                    g.render(o, d, opts, rgb)
+                    e1.record(stream)
+                    times.append((e0, e1))
+            torch.cuda.synchronize()
+            ms = np.array([x.elapsed_time(y) for x, y in times])
+            res["render"][name] = {"p50_ms": float(np.percentile(ms, 50)), "p99_ms": float(np.percentile(ms, 99)),
+                                   "mean_ms": float(ms.mean()), "frames": int(ms.size),
+                                   "Mrays_per_s": npx / (ms.mean() / 1e3) / 1e6, "resolution": f"{W}x{H}"}
+            del g
+        del frames
+        torch.cuda.empty_cache()
+
+    # ---- coarse-to-fine grid operations on this workload's grid
+    g = Grid.from_host(R, wl["train"].idx, wl["train"].rows)
+    t = []
+    for rep in range(3):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        gp = g.prune(5.0, True)
+        torch.cuda.synchronize()
+        t.append((time.perf_counter() - t0) * 1e3)
+        kept = gp.M
+        del gp
+    res["grid_ops"] = {"prune_sigma5_ms": min(t), "prune_kept_rows": kept, "rows": g.M}
+    del g
+    torch.cuda.empty_cache()
+    if R >= 64:
+        half = synth.scene_config(f"sparse{R // 2}_0.08") if R > 256 else None
+        if half is not None:
+            gh = Grid.from_host(R // 2, half.idx, half.rows)
+            t = []
+            for rep in range(3):
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                gu = gh.upsample(R)
+                torch.cuda.synchronize()
+                t.append((time.perf_counter() - t0) * 1e3)
+                rows_up = gu.M
+                del gu
+                torch.cuda.empty_cache()
+            res["grid_ops"].update({f"upsample_{R // 2}_to_{R}_ms": min(t), "upsampled_rows": rows_up})
+            del gh
+
+    # ---- CPU oracle baseline on a bounded sample of the same workload
+    res["cpu_baseline"] = cpu_baseline(args, wl, budget_s=args.cpu_seconds)
+    return res
+
+
+# --------------------------------------------------------------------------- CPU oracle
+def cpu_baseline(args, wl, budget_s=15.0):
+    """The FP64 oracle, as it stands, on the first rays of the first timed batch: fwd + MSE + adjoint."""
+    import oracle
+
+    R, W, H = wl["R"], wl["W"], wl["H"]
+    sc = wl["train"]
+    pix = wl["batches"][args.warmup % len(wl["batches"])][0]
+    rows64 = sc.rows.astype(np.float64)
+    o64, d64 = oracle.gen_rays(wl["cams"].astype(np.float64), pix)
+    tgt, _ = oracle.render(R, wl["gt"].idx, wl["gt"].rows.astype(np.float64), o64[:64], d64[:64])
+
+    def run(n):
+        t0 = time.perf_counter()
+        rgb, _ = oracle.render(R, sc.idx, rows64, o64[:n], d64[:n])
+        _, grgb = oracle.mse(rgb, np.resize(tgt, (n, 3)))
+        oracle.render_backward(R, sc.idx, rows64, o64[:n], d64[:n], grgb)
+        return time.perf_counter() - t0
+
+    t_probe = run(32)
+    n = int(min(args.batch, max(32, 32 * budget_s / max(t_probe, 1e-3))))
+    t = run(n)
+    return {"value": n / t, "unit": "rays/s", "cores": oracle.num_threads(), "kind": "oracle",
+            "sample": f"{n} rays of one {args.batch}-ray batch of the {wl['R']}^3 workload: ray generation, "
+                      "forward, MSE and adjoint in FP64 (OpenMP over rays)", "seconds": t}
+
+
+def run_reference(args, world, rank):
+    """--impl reference: the CPU oracle timed step by step on a bounded sample of the same workload."""
+    if rank != 0:
+        return
+    import oracle
+
+    wl = build_workload(args)
+    R = wl["R"]
+    sc = wl["train"]
+    rows64 = sc.rows.astype(np.float64)
+    M = sc.M
+    v = np.zeros((M, 28))
+    n = None
+    times = []
+
+    def one_step(s):
+        nonlocal rows64, v, n
+        pix, ss, sl = wl["batches"][s % len(wl["batches"])]
+        o64, d64 = oracle.gen_rays(wl["cams"].astype(np.float64), pix[:n])
+        tgt, _ = oracle.render(R, wl["gt"].idx, wl["gt"].rows.astype(np.float64), o64, d64)
+        t0 = time.perf_counter()
+        rgb, _ = oracle.render(R, sc.idx, rows64, o64, d64)
+        _, grgb = oracle.mse(rgb, tgt)
+        grad = oracle.render_backward(R, sc.idx, rows64, o64, d64, grgb)
+        k = max(1, int(round(ss.shape[0] * n / args.batch)))
+        oracle.tv(R, sc.idx, rows64, ss[:k], sl[:k], 1e-5, 1e-3, grad_rows=grad)
+        rows64, v, _ = oracle.rmsprop(rows64, v, grad, 30.0, 1e-2)
+        return time.perf_counter() - t0
+
+    n = 8
+    probe = one_step(0)
+    per_ray = probe / n
+    n = int(max(8, min(args.batch, 4.0 / max(per_ray, 1e-6))))  # ~4 s per step
+    for s in range(args.warmup):
+        one_step(s)
+    for s in range(args.steps):
+        times.append(one_step(args.warmup + s))
+    total = sum(times)
+    value = args.steps * n / total
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "rays/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"{args.workload} (oracle sample of {n} rays per step)"},
+            "cpu_baseline": {"value": value, "unit": "rays/s", "cores": oracle.num_threads(), "kind": "oracle",
+                             "sample": f"{n} rays per step of the {args.batch}-ray batches, plus the TV share "
+                                       "and a full RMSProp sweep, FP64"},
+            "e2e": {"value": value, "unit": "rays/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse_args()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, world, rank)
+        return
+    world, rank, local = dist_setup()
+    try:
+        run_ours(args, world, rank, local)
+    finally:
+        if world > 1:
+            import torch.distributed as dist
+
+            dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,276 @@
+/*
+ * plenoxel.h -- C ABI of libplenoxel, a CUDA (sm_103a) implementation of the
+ * Plenoxels differentiable volume renderer (Yu, Fridovich-Keil et al.,
+ * "Plenoxels: Radiance Fields without Neural Networks", arXiv 2112.05131).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * - Every call returns a plx_status.  PLX_OK is 0.  On failure,
+ *   plx_last_error() returns a message for the calling thread.  No C++
+ *   exception crosses this boundary.
+ * - Arguments are validated on the host before anything is launched; a bad
+ *   argument returns PLX_EINVAL and launches nothing.
+ * - Device pointers ("d_" prefix) are owned by the caller, who allocates and
+ *   frees them.  The library never allocates device memory: the derived
+ *   structures a grid needs live in a caller-provided workspace whose size
+ *   plx_grid_workspace_bytes() returns.  Host pointers ("h_" prefix, or
+ *   plain output integers) are only read or written during the call.
+ * - Work is enqueued asynchronously on `stream` (a cudaStream_t passed as
+ *   void*, NULL = the legacy default stream) unless a call says it
+ *   synchronises.  Inputs must stay valid until the stream reaches the work.
+ * - Kernels that meet corrupt data (an index volume entry >= n_rows) record
+ *   a code in the grid's device status word, skip the access and go on;
+ *   plx_check() reports it.  No kernel traps or waits on another kernel.
+ *
+ * Grid layout (Sec. 3.2; Supp. A.1 "Implementation Details")
+ * ---------------------------------------------------------
+ * - The grid is a dense R x R x R lattice of nodes ("each occupied voxel
+ *   corner stores ...", Sec. 3).  Node (i,j,k) has linear id
+ *   n = (i*R + j)*R + k (k fastest, i along x) and sits at world position
+ *   aabb_min + (i,j,k) * h, h = (aabb_max - aabb_min) / (R - 1).
+ * - d_idx: int32 [R^3]; -1 marks an empty (NULL) node, otherwise the row of
+ *   the node in the data table.  NULL nodes count as all-zero values.
+ * - F32 rows: float [n_rows][32] = [sigma, R0..R8, G0..G8, B0..B8, 4 x pad]
+ *   (28 values padded to 128 bytes; the pad is never read).  The base
+ *   pointer must be 16-byte aligned.
+ * - BF16-SH rows: uint16 [n_rows][32] = [sigma as FP32 in slots 0-1,
+ *   SH[0..26] as bfloat16 in slots 2..28, 3 x pad] (64 bytes per row).
+ *   Density stays FP32; the SH coefficients are rounded to nearest-even
+ *   from the F32 rows by plx_pack_bf16().  Compositing and all accumulation
+ *   are FP32 in both forms.
+ * - Gradient and RMSProp-state rows (d_grad_rows, d_v) use the F32 row
+ *   layout [n_rows][32].
+ *
+ * Rays and rendering (Eq. 1, Sec. 3.1)
+ * ------------------------------------
+ * - Rays: d_origins, d_dirs float [n][3]; directions must be unit length and
+ *   are used as given (no renormalisation); they are also the SH argument.
+ * - The ray is clipped to the box [aabb_min, aabb_max] (slab test,
+ *   t_near = max(t_in, 0)); samples sit at t_s = t_near + s * delta for
+ *   s = 0, 1, ... while t_s < t_far, with delta = step_vox * min_a h_a in
+ *   world units, and every sample has delta_s = delta.
+ * - Each sample interpolates all 28 values trilinearly from the 8 nodes of
+ *   its cell (Sec. 3.3): g = clamp((x - aabb_min)/h, 0, R-1),
+ *   base = min(floor(g), R-2), f = g - base.
+ * - sigma_s = max(0, interpolated sigma); colour c_ch = max(0, sum_l Y_l(d)
+ *   k_{ch,l}) with real degree-2 SH Y_0..Y_8 (Sec. 3.2; ReLU per Supp. A.1).
+ * - Compositing: T_0 = 1, alpha_s = 1 - exp(-sigma_s delta), w_s = T_s
+ *   alpha_s, T_{s+1} = T_s (1 - alpha_s); before sample s the march stops if
+ *   T_s < stop_thresh; C = sum_s w_s c_s + T_end * bg.
+ */
+#ifndef PLENOXEL_H
+#define PLENOXEL_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    PLX_OK = 0,
+    PLX_EINVAL = 1,       /* invalid argument; nothing was launched            */
+    PLX_ENOMEM = 2,       /* a caller-provided buffer is too small             */
+    PLX_ECUDA = 3,        /* the CUDA runtime reported an error                */
+    PLX_ETIMEOUT = 4,     /* a host-side wait reached its deadline             */
+    PLX_EBUSY = 5,        /* the object is in use by another call              */
+    PLX_EUNSUPPORTED = 6, /* valid but outside what this build supports        */
+    PLX_EDEVICE = 7       /* a kernel recorded corrupt data (see plx_check)    */
+} plx_status;
+
+enum { PLX_SH_F32 = 0, PLX_SH_BF16 = 1 };
+
+/* Descriptor of a sparse grid. */
+typedef struct {
+    int32_t reso;        /* R, nodes per axis, 2 <= R <= 2048                   */
+    float aabb_min[3];   /* world box; aabb_max > aabb_min on every axis        */
+    float aabb_max[3];
+    int64_t n_rows;      /* number of occupied nodes (rows), 0 <= n_rows < 2^31 */
+    int32_t sh_form;     /* which rows the renderer reads: PLX_SH_F32/PLX_SH_BF16 */
+} plx_grid_desc;
+
+/* Rendering options. */
+typedef struct {
+    float step_vox;      /* sample spacing in units of the smallest cell size (> 0) */
+    float bg[3];         /* background colour composited with T_end            */
+    float stop_thresh;   /* early termination threshold on T (0 = march to t_far) */
+} plx_render_opts;
+
+/* Opaque grid handle: the descriptor plus caller-owned device pointers. */
+typedef struct plx_grid plx_grid;
+
+/* ---------------------------------------------------------------- status */
+
+const char *plx_status_str(plx_status s);
+/* Message of the last failing call on this thread ("" if none). */
+const char *plx_last_error(void);
+/* Library version string. */
+const char *plx_version(void);
+
+/* ---------------------------------------------------------------- grid */
+
+/* Bytes of device workspace a grid with this descriptor needs (device status
+ * word, the per-cell occupancy bitmask of R^3 bits used for empty-space
+ * skipping, and the per-row "touched" bitmask that the sparse RMSProp reads).
+ * Returns 0 for an invalid descriptor. */
+size_t plx_grid_workspace_bytes(const plx_grid_desc *desc);
+
+/* Create a grid handle over caller-owned buffers and build its derived
+ * structures into d_workspace (asynchronously on `stream`).
+ *   d_idx        int32 [R^3] index volume (read-only to the library)
+ *   d_rows_f32   F32 rows [n_rows][32]; required for PLX_SH_F32, and for any
+ *                call that reads or updates the master values (TV, RMSProp,
+ *                prune, upsample, plx_pack_bf16); may be NULL for a
+ *                render-only BF16 grid
+ *   d_rows_bf16  BF16-SH rows [n_rows][32] uint16; required for PLX_SH_BF16,
+ *                must be NULL for PLX_SH_F32
+ *   d_workspace  plx_grid_workspace_bytes(desc) bytes, 256-byte aligned,
+ *                owned by the caller and reserved for this grid until destroy
+ * The handle itself is host memory freed by plx_grid_destroy. */
+plx_status plx_grid_create(const plx_grid_desc *desc, const int32_t *d_idx, float *d_rows_f32,
+                           uint16_t *d_rows_bf16, void *d_workspace, void *stream,
+                           plx_grid **out);
+plx_status plx_grid_destroy(plx_grid *grid);
+/* Copy the descriptor of a grid. */
+plx_status plx_grid_get_desc(const plx_grid *grid, plx_grid_desc *out);
+
+/* Round the SH of every F32 row to bfloat16 (nearest-even) into the BF16-SH
+ * rows, copying density as FP32 (the storage form of the grid's BF16 rows). */
+plx_status plx_pack_bf16(plx_grid *grid, void *stream);
+
+/* Synchronise `stream`, then read and clear the grid's device status word.
+ * Returns PLX_EDEVICE if a kernel recorded corrupt data since the last check. */
+plx_status plx_check(const plx_grid *grid, void *stream);
+
+/* ---------------------------------------------------------------- rays */
+
+/* Pinhole rays through pixel centres (Sec. 4.1; the centred-pixel convention
+ * of Supp. D), camera looking down -z with y up.
+ *   d_cams   float [n_cams][18] = c2w (3x4 row-major), fx, fy, cx, cy, W, H;
+ *            all cameras share W and H
+ *   d_pix    int64 [n] pixel ids view*H*W + v*W + u, 0 <= id < n_cams*W*H
+ *   d_origins, d_dirs  float [n][3] outputs
+ * W, H     the shared image size (must equal the cameras' W and H entries)
+ * With pixel centre (u+0.5, v+0.5): d = normalise(R (((u+0.5)-cx)/fx,
+ * -((v+0.5)-cy)/fy, -1)), o = camera centre.  d is evaluated in double-float
+ * arithmetic and rounded once, i.e. it is the FP32 rounding of the exact
+ * direction except within ~1e-14 of a rounding midpoint.  An id outside
+ * [0, n_cams*W*H) yields a zero origin and direction. */
+plx_status plx_gen_rays(const float *d_cams, int32_t n_cams, int32_t W, int32_t H,
+                        const int64_t *d_pix, int64_t n, float *d_origins, float *d_dirs,
+                        void *stream);
+
+/* ---------------------------------------------------------------- render */
+
+/* Forward render of n rays (Eq. 1) into d_rgb float [n][3] and, if d_T_end is
+ * not NULL, the final transmittance float [n].  Reads the grid's F32 or
+ * BF16-SH rows according to its sh_form. */
+plx_status plx_render(const plx_grid *grid, const float *d_origins, const float *d_dirs, int64_t n,
+                      const plx_render_opts *opts, float *d_rgb, float *d_T_end, void *stream);
+
+/* Adjoint of plx_render (Sec. 3.4: the renderer is differentiated end to end;
+ * Supp. A.1 "gradient kernels").  d_grad_rgb float [n][3] = dL/dC.  Adds
+ * dL/d(row values) into d_grad_rows F32 [n_rows][32] (+=; padding columns
+ * untouched) and marks the rows it touches in the grid's touched bitmask.
+ * The march is recomputed (no per-sample state is stored).  Per sample:
+ *   dL/dc_ch = g_ch w_s;  dL/dk_{ch,l} = dL/dc_ch [pre_ch > 0] Y_l;
+ *   dL/dsigma_s = delta sum_ch g_ch (T_{s+1} c_ch - R_ch) [sigma_pre > 0],
+ *   R = sum_{j>s} w_j c_j + T_end bg,
+ * scattered to the 8 corners with their trilinear weights (NULL corners skip).
+ * Rows are accumulated with float atomics, so the summation order (and the
+ * last bits) can vary between runs. */
+plx_status plx_render_backward(const plx_grid *grid, const float *d_origins, const float *d_dirs,
+                               int64_t n, const plx_render_opts *opts, const float *d_grad_rgb,
+                               float *d_grad_rows, void *stream);
+
+/* Traffic accounting (a measurement aid, not part of the method): for each
+ * ray, d_counts int64 [n][2] receives (a) the number of distinct lattice
+ * nodes that are corners of the ray's sampled cells having at least one
+ * occupied corner, and (b) how many of those nodes are occupied, following the
+ * same samples and early termination as plx_render.  (a) x 4 bytes of index
+ * reads plus (b) x row bytes is the least a forward march must move. */
+plx_status plx_count_nodes(const plx_grid *grid, const float *d_origins, const float *d_dirs, int64_t n,
+                           const plx_render_opts *opts, int64_t *d_counts, void *stream);
+
+/* Reconstruction loss of a ray batch (Sec. 3.4, the MSE term of the loss):
+ *   L = 1/n sum_r ||C_r - Chat_r||^2  and  dL/dChat_r = 2 (Chat_r - C_r) / n.
+ *   d_rgb, d_target  float [n][3]: rendered and target colours
+ *   d_grad_rgb       float [n][3] output (may alias neither input)
+ *   d_loss           float [1] or NULL: L is added to it (atomically) */
+plx_status plx_mse_grad(const float *d_rgb, const float *d_target, int64_t n, float *d_grad_rgb, float *d_loss,
+                        void *stream);
+
+/* ---------------------------------------------------------------- regulariser / optimiser */
+
+/* Total-variation gradient (Sec. 3.4 loss; Supp. A.1: stochastic contiguous
+ * segments, differences scaled by R/256, missing density neighbour = 0,
+ * missing SH neighbour = own value).  For each selected node v (empty nodes
+ * may be selected) and value d:
+ *   D_a = (V_d(v + e_a) - V_d(v)) * R/256,  t = sqrt(D_x^2 + D_y^2 + D_z^2),
+ *   L += lambda_d / n_selected * t,
+ * lambda_0 = lambda_sigma, lambda_{d>0} = lambda_sh; t = 0 gives no gradient.
+ *   d_seg_start, d_seg_len  int64 [n_seg]: runs of linear node ids, each
+ *                           inside [0, R^3); runs must not overlap
+ *   n_selected              sum of d_seg_len (the host knows it)
+ *   d_grad_rows             F32 [n_rows][32], += (occupied rows only; marks them touched)
+ *   d_loss                  float [1] or NULL: L is added to it (atomically)
+ * Reads the F32 rows (d_rows_f32 must be set). */
+plx_status plx_tv_grad(const plx_grid *grid, const int64_t *d_seg_start, const int64_t *d_seg_len,
+                       int64_t n_seg, int64_t n_selected, float lambda_sigma, float lambda_sh,
+                       float *d_grad_rows, float *d_loss, void *stream);
+
+/* RMSProp (Sec. 3.4) on every entry with a non-zero gradient:
+ *   v <- beta v + (1 - beta) g^2;  x <- x - lr g / (sqrt(v) + eps);  g <- 0,
+ * lr = lr_sigma for the density column, lr_sh for the SH columns.  Entries
+ * with g == 0 keep x and v unchanged.  Updates the F32 rows in place and,
+ * for a BF16-SH grid, re-packs the updated rows.
+ *   sparse = 0: sweep every row.
+ *   sparse = 1: visit only rows marked in the grid's touched bitmask (by
+ *               plx_render_backward / plx_tv_grad since the last step), which
+ *               is exact whenever every non-zero gradient came from those calls.
+ * Both modes clear the touched bitmask. */
+plx_status plx_rmsprop_step(plx_grid *grid, float *d_grad_rows, float *d_v, float lr_sigma,
+                            float lr_sh, float beta, float eps, int32_t sparse, void *stream);
+
+/* ---------------------------------------------------------------- prune / upsample */
+
+/* Density-threshold pruning with dilation (Sec. 3.4 "Coarse to Fine"):
+ * hot(n) = occupied and sigma >= tau; a node is kept if it is occupied and
+ * (dilate ? some node of its 3x3x3 neighbourhood, clipped to the grid, is hot
+ * : it is hot).  Kept nodes get new rows in ascending node id.
+ * Two phases around one caller allocation:
+ *   plx_grid_prune_count  computes the keep map into d_ws
+ *                         (plx_prune_workspace_bytes(R) bytes, 256-aligned),
+ *                         synchronises `stream` and returns the count
+ *   plx_grid_prune_apply  writes d_idx_new int32 [R^3] and d_rows_new F32
+ *                         [n_keep][32] (NULL allowed when n_keep is 0); d_ws
+ *                         must still hold the count's result and n_keep must
+ *                         be the count it returned (rows beyond it are never
+ *                         written; a mismatch is recorded for plx_check) */
+size_t plx_prune_workspace_bytes(int32_t reso);
+plx_status plx_grid_prune_count(const plx_grid *grid, float tau, int32_t dilate, void *d_ws,
+                                int64_t *n_keep, void *stream);
+plx_status plx_grid_prune_apply(const plx_grid *grid, const void *d_ws, int64_t n_keep, int32_t *d_idx_new,
+                                float *d_rows_new, void *stream);
+
+/* Trilinear resampling to a new resolution (Sec. 3.4: subdivide and
+ * initialise by trilinear interpolation; any resolution).  New node i' along
+ * an axis sits at old grid coordinate i'(R-1)/(R'-1): base = floor of it
+ * (integer division), rem = i'(R-1) mod (R'-1), frac = rem/(R'-1); the +1
+ * node has weight frac and takes part only if rem != 0.  A new node is
+ * occupied iff one of its taking-part old nodes is; values interpolate with
+ * NULL = 0.  Two phases as for pruning, with
+ * plx_upsample_workspace_bytes(R') bytes of d_ws; n_rows_new is the count
+ * plx_grid_upsample_count returned. */
+size_t plx_upsample_workspace_bytes(int32_t new_reso);
+plx_status plx_grid_upsample_count(const plx_grid *grid, int32_t new_reso, void *d_ws,
+                                   int64_t *n_rows_new, void *stream);
+plx_status plx_grid_upsample_apply(const plx_grid *grid, int32_t new_reso, const void *d_ws, int64_t n_rows_new,
+                                   int32_t *d_idx_new, float *d_rows_new, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PLENOXEL_H */

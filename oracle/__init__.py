@@ -58,6 +58,7 @@ def _load():
             "orc_clip": (None, [P, P, I64, P, P]),
             "orc_render": (None, [I64, P, P, I64, P, P, P, I64, P, P, P]),
             "orc_render_backward": (None, [I64, P, P, I64, P, P, P, I64, P, P, P]),
+            "orc_render_backward_abs": (None, [I64, P, P, I64, P, P, P, I64, P, P, P]),
             "orc_mse": (D, [P, P, I64, P]),
             "orc_tv": (D, [I64, P, P, I64, P, P, I64, D, D, P]),
             "orc_rmsprop": (None, [I64, P, P, P, D, D, D, D]),
@@ -176,6 +177,23 @@ def render_backward(R, idx, rows, o, d, grad_rgb, step_vox=0.5, bg=(1.0, 1.0, 1.
     lib.orc_render_backward(R, _p(idx), _p(rows), rows.shape[1], _p(_aabb(aabb)), _p(o), _p(d),
                             o.shape[0], _p(_opts(step_vox, bg, stop_thresh)), _p(g), _p(grad_rows))
     return grad_rows
+
+
+def render_backward_abs(R, idx, rows, o, d, grad_rgb, step_vox=0.5, bg=(1.0, 1.0, 1.0), stop_thresh=0.0,
+                        aabb=None):
+    """The adjoint with every per-sample, per-corner term taken in absolute value (grad_rgb >= 0): an
+    entrywise bound on |render_backward(g')| for all |g'| <= grad_rgb, used to propagate uncertainty."""
+    lib = _load()
+    idx = _c(idx, np.int32)
+    rows = _rows(rows)
+    o = _c(o, np.float64)
+    d = _c(d, np.float64)
+    g = _c(grad_rgb, np.float64)
+    assert np.all(g >= 0)
+    out = np.zeros((rows.shape[0], NV), np.float64)
+    lib.orc_render_backward_abs(R, _p(idx), _p(rows), rows.shape[1], _p(_aabb(aabb)), _p(o), _p(d),
+                                o.shape[0], _p(_opts(step_vox, bg, stop_thresh)), _p(g), _p(out))
+    return out
 
 
 def mse(pred, target):

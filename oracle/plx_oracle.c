@@ -32,6 +32,8 @@
  *                       telescoped (T_i - T_{i+1}) form, brute force on 4^3,
  *                       empty grid = background, sum of weights + T_end = 1
  *   orc_render_backward pinned: central finite differences of orc_render
+ *   orc_render_backward_abs  pinned: bounds the adjoint of every smaller g
+ *                       (triangle inequality), equals it for one-sign terms
  *   orc_tv              pinned: linear-ramp closed form, finite differences
  *   orc_rmsprop         pinned: constant-gradient closed form
  *   orc_prune           pinned: exhaustive 3x3x3 enumeration on small grids
@@ -353,9 +355,15 @@ void orc_render(int64_t R, const int32_t *idx, const double *rows, int64_t row_s
  * and each per-sample gradient reaches corner node c with its trilinear
  * weight; NULL corners receive nothing.
  */
-void orc_render_backward(int64_t R, const int32_t *idx, const double *rows, int64_t row_stride,
-                         const double *aabb, const double *o, const double *d, int64_t n,
-                         const double *opts, const double *grad_rgb, double *grad_rows)
+/*
+ * abs_mode = 1 adds every per-sample, per-corner term in absolute value
+ * (|g_ch| and |T_{s+1} c - R_s|, |Y_l| in place of the signed factors): for
+ * g >= 0 the result bounds |adjoint(g')| for every g' with |g'| <= g, which
+ * the tests use to carry an uncertainty of dL/dC into the gradient.
+ */
+static void render_backward_impl(int64_t R, const int32_t *idx, const double *rows, int64_t row_stride,
+                                 const double *aabb, const double *o, const double *d, int64_t n,
+                                 const double *opts, const double *grad_rgb, double *grad_rows, int abs_mode)
 {
     orc_grid g;
     grid_init(&g, R, idx, rows, row_stride, aabb);
@@ -391,13 +399,16 @@ void orc_render_backward(int64_t R, const int32_t *idx, const double *rows, int6
                 double T_next = q->T * (1.0 - q->alpha);
                 double gsig = 0.0;
                 if (q->sigma_pre > 0.0)
-                    for (int ch = 0; ch < 3; ++ch)
-                        gsig += gr[ch] * delta * (T_next * q->c[ch] - Rs[s][ch]);
+                    for (int ch = 0; ch < 3; ++ch) {
+                        double term = gr[ch] * delta * (T_next * q->c[ch] - Rs[s][ch]);
+                        gsig += abs_mode ? fabs(term) : term;
+                    }
                 double gk[ORC_NV - 1];
                 for (int ch = 0; ch < 3; ++ch) {
                     double gc = gr[ch] * q->w;
                     double gpre = q->pre[ch] > 0.0 ? gc : 0.0;
-                    for (int l = 0; l < ORC_NSH; ++l) gk[ch * ORC_NSH + l] = gpre * Y[l];
+                    for (int l = 0; l < ORC_NSH; ++l)
+                        gk[ch * ORC_NSH + l] = abs_mode ? fabs(gpre * Y[l]) : gpre * Y[l];
                 }
                 for (int c = 0; c < 8; ++c) {
                     int32_t row = g.idx[q->node[c]];
@@ -416,6 +427,20 @@ void orc_render_backward(int64_t R, const int32_t *idx, const double *rows, int6
         free(smp);
         free(Rs);
     }
+}
+
+void orc_render_backward(int64_t R, const int32_t *idx, const double *rows, int64_t row_stride,
+                         const double *aabb, const double *o, const double *d, int64_t n,
+                         const double *opts, const double *grad_rgb, double *grad_rows)
+{
+    render_backward_impl(R, idx, rows, row_stride, aabb, o, d, n, opts, grad_rgb, grad_rows, 0);
+}
+
+void orc_render_backward_abs(int64_t R, const int32_t *idx, const double *rows, int64_t row_stride,
+                             const double *aabb, const double *o, const double *d, int64_t n,
+                             const double *opts, const double *grad_rgb, double *grad_rows)
+{
+    render_backward_impl(R, idx, rows, row_stride, aabb, o, d, n, opts, grad_rgb, grad_rows, 1);
 }
 
 /* ------------------------------------------------------------------------- */

@@ -1,0 +1,97 @@
+"""The optimisation step of Sec. 3.4 as a sequence of library calls, and the learning-rate schedules.
+
+One step (Supp. A.1: 5000-ray batches, RMSProp, stochastic TV on contiguous segments):
+  plx_gen_rays -> plx_render -> plx_mse_grad -> plx_render_backward -> plx_tv_grad -> plx_rmsprop_step
+All six are kernels of libplenoxel enqueued on one stream with no host synchronisation.
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass, field
+from typing import List, Optional
+
+import torch
+
+from .grid import ROW, Grid, RenderOpts, gen_rays, mse_grad
+
+LAUNCHES_PER_STEP = 6
+
+
+def lr_sigma(step: int, init: float = 30.0, final: float = 0.05, max_steps: int = 250000, delay_steps: int = 15000,
+             delay_mult: float = 0.01) -> float:
+    """Delayed exponential decay for density (Supp. A.1, the Mip-NeRF schedule): log-linear from
+    `init` to `final` over `max_steps`, scaled during the first `delay_steps` by
+    delay_mult + (1 - delay_mult) sin(pi/2 clip(step/delay_steps, 0, 1)).  The paper does not print the
+    delay multiplier; 0.01 is this implementation's choice."""
+    if delay_steps > 0:
+        d = delay_mult + (1.0 - delay_mult) * math.sin(0.5 * math.pi * min(max(step / delay_steps, 0.0), 1.0))
+    else:
+        d = 1.0
+    t = min(max(step / max_steps, 0.0), 1.0)
+    return d * math.exp((1.0 - t) * math.log(init) + t * math.log(final))
+
+
+def lr_sh(step: int, init: float = 1e-2, final: float = 5e-6, max_steps: int = 250000) -> float:
+    """Pure exponential decay for the SH coefficients (Supp. A.1)."""
+    t = min(max(step / max_steps, 0.0), 1.0)
+    return math.exp((1.0 - t) * math.log(init) + t * math.log(final))
+
+
+@dataclass
+class StepConfig:
+    batch: int = 5000
+    opts: RenderOpts = field(default_factory=lambda: RenderOpts(0.5, (1.0, 1.0, 1.0), 0.0))
+    lambda_tv_sigma: float = 1e-5
+    lambda_tv_sh: float = 1e-3
+    beta: float = 0.95
+    eps: float = 1e-8
+    sparse_rmsprop: bool = True
+
+
+class Trainer:
+    """Holds the optimiser state (gradient rows, RMSProp running average) and the step's scratch buffers."""
+
+    def __init__(self, grid: Grid, cams: torch.Tensor, W: int, H: int, cfg: StepConfig = StepConfig()):
+        dev = grid.idx.device
+        self.grid = grid
+        self.cams = cams
+        self.W, self.H = int(W), int(H)
+        self.cfg = cfg
+        self.grad = torch.zeros((grid.M, ROW), dtype=torch.float32, device=dev)
+        self.v = torch.zeros((grid.M, ROW), dtype=torch.float32, device=dev)
+        n = cfg.batch
+        self.o = torch.empty((n, 3), dtype=torch.float32, device=dev)
+        self.d = torch.empty((n, 3), dtype=torch.float32, device=dev)
+        self.rgb = torch.empty((n, 3), dtype=torch.float32, device=dev)
+        self.grad_rgb = torch.empty((n, 3), dtype=torch.float32, device=dev)
+        self.loss = torch.zeros(1, dtype=torch.float32, device=dev)
+
+    def step(self, pix: torch.Tensor, target: torch.Tensor, seg_start: Optional[torch.Tensor],
+             seg_len: Optional[torch.Tensor], n_selected: int, lr_s: float, lr_h: float,
+             events: Optional[List[torch.cuda.Event]] = None, stream=None):
+        """One optimisation step; `events`, if given, must hold 7 events recorded at the stage boundaries."""
+        g, c = self.grid, self.cfg
+        n = pix.shape[0]
+        o, d, rgb, grgb = self.o[:n], self.d[:n], self.rgb[:n], self.grad_rgb[:n]
+
+        def mark(i):
+            if events is not None:
+                events[i].record(stream if stream is not None else torch.cuda.current_stream())
+
+        mark(0)
+        gen_rays(self.cams, pix, self.W, self.H, o, d, stream=stream)
+        mark(1)
+        g.render(o, d, c.opts, rgb, stream=stream)
+        mark(2)
+        mse_grad(rgb, target, grgb, self.loss, stream=stream)
+        mark(3)
+        g.render_backward(o, d, grgb, c.opts, self.grad, stream=stream)
+        mark(4)
+        if seg_start is not None and n_selected > 0:
+            g.tv_grad(seg_start, seg_len, n_selected, c.lambda_tv_sigma, c.lambda_tv_sh, self.grad, stream=stream)
+        mark(5)
+        g.rmsprop_step(self.grad, self.v, lr_s, lr_h, c.beta, c.eps, sparse=c.sparse_rmsprop, stream=stream)
+        mark(6)
+        return rgb
+
+    STAGES = ("gen_rays", "render", "mse_grad", "render_backward", "tv_grad", "rmsprop_step")

@@ -11,7 +11,8 @@ datasets that are not available; the generators below stand in for them with
 the same shapes.  Scene recipes:
 
 * ``scene_dense_blobs`` -- dense R^3 grid, density = sum of isotropic Gaussian
-  blobs (peak 50, std ``blob_std_vox`` voxels, centres ~ U[-0.5,0.5]^3), SH ~ N(0, sh_std).
+  blobs (peak 50, std ``blob_std_vox`` voxels, centres ~ U[-0.5,0.5]^3) evaluated
+  on every node (strictly positive), SH ~ N(0, sh_std).
 * ``scene_sparse`` -- R^3 grid whose density is 20 Gaussian blobs (peak 50,
   std ~ U(0.04, 0.12) world units) plus a thin spherical shell (radius 0.6,
   Gaussian profile of width 1.5 voxels, peak 50).  The top ``occupancy``
@@ -47,11 +48,15 @@ def _node_coords_1d(R: int) -> np.ndarray:
     return (-1.0 + 2.0 * np.arange(R, dtype=np.float64) / (R - 1)).astype(np.float32)
 
 
-def _add_blob(sigma: np.ndarray, R: int, centre, std: float, peak: float) -> None:
-    """Add peak*exp(-|x-c|^2/(2 std^2)) inside a +-4 std box (values beyond are < 4e-6 * peak)."""
+def _add_blob(sigma: np.ndarray, R: int, centre, std: float, peak: float, truncate: bool = True) -> None:
+    """Add peak*exp(-|x-c|^2/(2 std^2)), either on the whole grid or inside a +-4 std box
+    (values beyond it are below 4e-6 * peak, far under the occupancy thresholds of sparse scenes)."""
     h = 2.0 / (R - 1)
-    lo = [max(0, int(math.floor((c - 4 * std + 1.0) / h))) for c in centre]
-    hi = [min(R - 1, int(math.ceil((c + 4 * std + 1.0) / h))) for c in centre]
+    if truncate:
+        lo = [max(0, int(math.floor((c - 4 * std + 1.0) / h))) for c in centre]
+        hi = [min(R - 1, int(math.ceil((c + 4 * std + 1.0) / h))) for c in centre]
+    else:
+        lo, hi = [0, 0, 0], [R - 1, R - 1, R - 1]
     xs = [(-1.0 + h * np.arange(lo[a], hi[a] + 1)).astype(np.float32) - np.float32(centre[a]) for a in range(3)]
     inv = np.float32(1.0 / (2.0 * std * std))
     ex = np.exp(-(xs[0] ** 2) * inv)
@@ -69,7 +74,7 @@ def scene_dense_blobs(R: int = 32, n_blobs: int = 3, peak: float = 50.0, blob_st
     centres = rng.uniform(-0.5, 0.5, size=(n_blobs, 3))
     sigma = np.zeros((R, R, R), np.float32)
     for b in range(n_blobs):
-        _add_blob(sigma, R, centres[b], blob_std_vox * h, peak)
+        _add_blob(sigma, R, centres[b], blob_std_vox * h, peak, truncate=False)
     M = R ** 3
     rows = np.empty((M, NV), np.float32)
     rows[:, 0] = sigma.reshape(-1)

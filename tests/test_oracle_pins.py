@@ -417,6 +417,30 @@ def test_render_backward_matches_central_differences(R, frac_empty, stop, sig_lo
     assert np.all(err <= 1e-6 * np.maximum(np.abs(an), 1e-3 * scale) + floor)
 
 
+def test_backward_abs_bounds_the_adjoint():
+    """|adjoint(g')| <= abs-adjoint(g) for every |g'| <= g (triangle inequality), with equality for a
+    single ray and channel on the SH columns of its colour-channel (one sign per term there)."""
+    R = 6
+    idx, rows = random_sparse(R, 0.2, 140, sigma_range=(-1.0, 6.0))
+    o, d = synth.random_rays(20, seed=141)
+    o, d = o.astype(float), d.astype(float)
+    rng = np.random.default_rng(142)
+    gb = rng.uniform(0.1, 1.0, size=(20, 3))
+    bound = oracle.render_backward_abs(R, idx, rows, o, d, gb)
+    for trial in range(4):
+        gp = gb * rng.uniform(-1, 1, size=gb.shape)
+        a = oracle.render_backward(R, idx, rows, o, d, gp)
+        assert np.all(np.abs(a) <= bound * (1 + 1e-12) + 1e-300)
+    # a single ray, one channel: the SH gradient of channel 0 is g w [pre>0] Y_l per sample and corner
+    # (all of one sign per (corner, l) only if Y_l keeps its sign, which it does for a fixed direction)
+    g1 = np.zeros((1, 3))
+    g1[0, 0] = 0.7
+    a1 = oracle.render_backward(R, idx, rows, o[:1], d[:1], g1)
+    b1 = oracle.render_backward_abs(R, idx, rows, o[:1], d[:1], g1)
+    assert np.allclose(np.abs(a1[:, 1:10]), b1[:, 1:10], rtol=1e-13, atol=0)
+    assert np.all(b1[:, 10:] == 0)
+
+
 def test_mse_gradient():
     rng = np.random.default_rng(0)
     p, t = rng.uniform(size=(10, 3)), rng.uniform(size=(10, 3))
