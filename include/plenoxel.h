@@ -269,6 +269,37 @@ plx_status plx_grid_upsample_count(const plx_grid *grid, int32_t new_reso, void 
 plx_status plx_grid_upsample_apply(const plx_grid *grid, int32_t new_reso, const void *d_ws, int64_t n_rows_new,
                                    int32_t *d_idx_new, float *d_rows_new, void *stream);
 
+/* ---------------------------------------------------------------- pruning without allocation */
+
+/* The paper has no counterpart to this entry point; it serves callers that
+ * cannot allocate device memory while they run (an embedder with a fixed memory
+ * budget and no allocator to lend, or a real-time loop that cannot afford the
+ * device-wide synchronisation an allocation may cause).
+ *
+ * plx_grid_prune_noalloc performs plx_grid_prune_count followed by
+ * plx_grid_prune_apply in one call, with the same result, but keeps its scratch
+ * in a fixed device array inside the library instead of a caller workspace:
+ *   d_idx_new   int32 [R^3] output index volume
+ *   d_rows_new  F32 rows output with room for the grid's n_rows rows (pruning
+ *               never adds rows); may be NULL only when n_rows is 0
+ *   n_keep      host output: the number of rows written
+ * It allocates nothing and synchronises `stream` (it needs the count on the
+ * host).  Limits and sharing rules of the fixed array:
+ *   - grids of at most PLX_PRUNE_NOALLOC_MAX_RESO nodes per axis; larger grids
+ *     return PLX_EUNSUPPORTED without launching anything;
+ *   - every GPU that loads the library holds PLX_PRUNE_NOALLOC_SCRATCH_BYTES
+ *     of device memory for it until the process exits;
+ *   - the first call on a device resolves the array's device address
+ *     (cudaGetSymbolAddress) with that device current: make that first call
+ *     before any stream capture;
+ *   - all calls share the array, which keeps the last call's contents; calls
+ *     whose work overlaps on the GPU (other streams or host threads on the same
+ *     device) race on it and must be serialised by the caller. */
+#define PLX_PRUNE_NOALLOC_MAX_RESO 256
+#define PLX_PRUNE_NOALLOC_SCRATCH_BYTES 4325632 /* the prune workspace of a 256^3 grid */
+plx_status plx_grid_prune_noalloc(const plx_grid *grid, float tau, int32_t dilate, int32_t *d_idx_new,
+                                  float *d_rows_new, int64_t *n_keep, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -63,6 +63,8 @@ SIGNATURES = {
     "plx_prune_workspace_bytes": (c_size_t, [c_int32]),
     "plx_grid_prune_count": (c_int32, [c_void_p, c_float, c_int32, c_void_p, ctypes.POINTER(c_int64), c_void_p]),
     "plx_grid_prune_apply": (c_int32, [c_void_p, c_void_p, c_int64, c_void_p, c_void_p, c_void_p]),
+    "plx_grid_prune_noalloc": (c_int32, [c_void_p, c_float, c_int32, c_void_p, c_void_p, ctypes.POINTER(c_int64),
+                                         c_void_p]),
     "plx_upsample_workspace_bytes": (c_size_t, [c_int32]),
     "plx_grid_upsample_count": (c_int32, [c_void_p, c_int32, c_void_p, ctypes.POINTER(c_int64), c_void_p]),
     "plx_grid_upsample_apply": (c_int32, [c_void_p, c_int32, c_void_p, c_int64, c_void_p, c_void_p, c_void_p]),

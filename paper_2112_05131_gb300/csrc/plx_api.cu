@@ -88,6 +88,11 @@ plx::RenderParams make_params(const plx_grid *g, const plx_render_opts *o) {
 
 }  // namespace
 
+namespace plx {
+const GridView *grid_view(const plx_grid *grid) { return grid ? &grid->view : nullptr; }
+plx_status set_error(plx_status s, const char *message) { return fail(s, "%s", message); }
+}  // namespace plx
+
 extern "C" {
 
 const char *plx_status_str(plx_status s) {

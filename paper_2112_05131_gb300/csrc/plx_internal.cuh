@@ -335,4 +335,8 @@ cudaError_t launch_upsample_apply(const GridView &g, int R2, const void *ws, int
 // total kept/occupied count written by the count kernels, at this byte offset of ws
 constexpr size_t kWsCountOff = 0;
 
+// host helpers defined in plx_api.cu for entry points in other translation units
+const GridView *grid_view(const plx_grid *grid);  // NULL for a NULL grid
+plx_status set_error(plx_status s, const char *message);
+
 }  // namespace plx
