@@ -308,17 +308,30 @@ def extras(args, wl, dev_batches, cams_t, gt_grid, opts, timed_loop, st32, ms32)
     n = args.batch
     fwd_bytes = n * (24 + 12) + 4 * nodes + 112 * occ
     bwd_bytes = 2 * (4 * nodes + 112 * occ) + n * (24 + 12) + 2 * 112 * occ
-    dom = max(st32, key=st32.get)
-    per_launch = {"render": fwd_bytes, "render_backward": bwd_bytes}
-    if dom in per_launch:
-        ach = per_launch[dom] / (st32[dom] / 1e3) / 1e9
-        res["roofline"] = {"kernel": dom, "bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s",
-                           "frac": ach / peak, "peak_source": f"{peak_kind} hbm_gbs (copy bandwidth)",
-                           "algorithmic_bytes_per_launch": per_launch[dom], "traffic": None}
+    # RMSProp: every touched row is read (gradient, value, state) and written back (112 bytes each),
+    # plus one bit per row of the touched mask; touched rows counted on the timed batches
+    tr_count = Trainer(train32, cams_t, W, H, StepConfig(batch=args.batch, opts=opts))
+    touched = []
+    for s in range(min(K, 8)):
+        b = dev_batches[(Wm + s) % nb]
+        o, d = gen_rays(cams_t, b[0], W, H)
+        tr_count.grad.zero_()
+        train32.render_backward(o, d, torch.full((args.batch, 3), 1e-3, device=dev), opts, tr_count.grad)
+        train32.tv_grad(b[2], b[3], b[4], 1e-5, 1e-3, tr_count.grad)
+        touched.append(int((tr_count.grad[:, :28] != 0).any(1).sum()))
+        train32.rmsprop_step(tr_count.grad, tr_count.v, 0.0, 0.0, sparse=True)  # clears gradient and marks
+    del tr_count
+    rms_bytes = float(np.mean(touched)) * 6 * 112 + train32.M / 8
+    per_launch = {"render": fwd_bytes, "render_backward": bwd_bytes, "rmsprop_step": rms_bytes}
+    dom = max(per_launch, key=lambda k: st32[k])
+    ach = per_launch[dom] / (st32[dom] / 1e3) / 1e9
+    res["roofline"] = {"kernel": dom, "bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s",
+                       "frac": ach / peak, "peak_source": f"{peak_kind} hbm_gbs (STREAM-style copy)",
+                       "algorithmic_bytes_per_launch": per_launch[dom], "traffic": None}
     res["algorithmic"] = {"distinct_nodes_per_ray": nodes / n, "occupied_nodes_per_ray": occ / n,
-                          "fwd_bytes_per_launch": fwd_bytes, "bwd_bytes_per_launch": bwd_bytes,
-                          "render_GBps": fwd_bytes / (st32["render"] / 1e3) / 1e9,
-                          "render_backward_GBps": bwd_bytes / (st32["render_backward"] / 1e3) / 1e9}
+                          "touched_rows_per_step": float(np.mean(touched)),
+                          "bytes_per_launch": per_launch,
+                          "GBps": {k: per_launch[k] / (st32[k] / 1e3) / 1e9 for k in per_launch}}
 
     # ---- end to end through the public API with host buffers (pinned), copies inside the timed region
     tr = Trainer(train32, cams_t, W, H, StepConfig(batch=args.batch, opts=opts))
@@ -432,29 +445,33 @@ def extras(args, wl, dev_batches, cams_t, gt_grid, opts, timed_loop, st32, ms32)
 
 # --------------------------------------------------------------------------- CPU oracle
 def cpu_baseline(args, wl, budget_s=15.0):
-    """The FP64 oracle, as it stands, on the first rays of the first timed batch: fwd + MSE + adjoint."""
+    """The FP64 oracle, as it stands, on whole batches of the same workload (ray generation, forward,
+    MSE and adjoint), batch after batch until the time budget is spent."""
     import oracle
 
-    R, W, H = wl["R"], wl["W"], wl["H"]
+    R = wl["R"]
     sc = wl["train"]
-    pix = wl["batches"][args.warmup % len(wl["batches"])][0]
     rows64 = sc.rows.astype(np.float64)
-    o64, d64 = oracle.gen_rays(wl["cams"].astype(np.float64), pix)
-    tgt, _ = oracle.render(R, wl["gt"].idx, wl["gt"].rows.astype(np.float64), o64[:64], d64[:64])
-
-    def run(n):
+    gt64 = wl["gt"].rows.astype(np.float64)
+    cams64 = wl["cams"].astype(np.float64)
+    rays = 0
+    spent = 0.0
+    b = 0
+    while spent < budget_s and b < 4 * len(wl["batches"]):
+        pix = wl["batches"][b % len(wl["batches"])][0]
+        o64, d64 = oracle.gen_rays(cams64, pix)
+        tgt, _ = oracle.render(R, wl["gt"].idx, gt64, o64, d64)  # targets: not timed
         t0 = time.perf_counter()
-        rgb, _ = oracle.render(R, sc.idx, rows64, o64[:n], d64[:n])
-        _, grgb = oracle.mse(rgb, np.resize(tgt, (n, 3)))
-        oracle.render_backward(R, sc.idx, rows64, o64[:n], d64[:n], grgb)
-        return time.perf_counter() - t0
-
-    t_probe = run(32)
-    n = int(min(args.batch, max(32, 32 * budget_s / max(t_probe, 1e-3))))
-    t = run(n)
-    return {"value": n / t, "unit": "rays/s", "cores": oracle.num_threads(), "kind": "oracle",
-            "sample": f"{n} rays of one {args.batch}-ray batch of the {wl['R']}^3 workload: ray generation, "
-                      "forward, MSE and adjoint in FP64 (OpenMP over rays)", "seconds": t}
+        o64, d64 = oracle.gen_rays(cams64, pix)
+        rgb, _ = oracle.render(R, sc.idx, rows64, o64, d64)
+        _, grgb = oracle.mse(rgb, tgt)
+        oracle.render_backward(R, sc.idx, rows64, o64, d64, grgb)
+        spent += time.perf_counter() - t0
+        rays += pix.shape[0]
+        b += 1
+    return {"value": rays / spent, "unit": "rays/s", "cores": oracle.num_threads(), "kind": "oracle",
+            "sample": f"{b} batches of {args.batch} rays ({rays} rays) of the {R}^3 workload: ray generation, "
+                      "forward, MSE and adjoint in FP64, OpenMP over rays", "seconds": spent}
 
 
 def run_reference(args, world, rank):

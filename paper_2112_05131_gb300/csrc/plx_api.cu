@@ -210,6 +210,7 @@ plx_status plx_check(const plx_grid *grid, void *stream) {
     if (code == plx::kDevBadRow) return fail(PLX_EDEVICE, "an index volume entry is >= n_rows");
     if (code == plx::kDevTooManySamples) return fail(PLX_EDEVICE, "a ray needed more samples than the backward supports");
     if (code == plx::kDevCountMismatch) return fail(PLX_EDEVICE, "apply was given a row count that its workspace does not hold");
+    if (code == plx::kDevCopyTimeout) return fail(PLX_ETIMEOUT, "a row copy into shared memory did not complete; the ray was abandoned");
     if (code != 0) return fail(PLX_EDEVICE, "device status %d", code);
     return PLX_OK;
 }

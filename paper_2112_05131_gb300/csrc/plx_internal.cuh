@@ -21,7 +21,7 @@ constexpr int kRowH = 32;        // uint16 per BF16 row (64 bytes)
 constexpr unsigned kFull = 0xffffffffu;
 
 // device status codes (stored in the grid workspace's first word)
-enum : int { kDevOk = 0, kDevBadRow = 1, kDevTooManySamples = 2, kDevCountMismatch = 3 };
+enum : int { kDevOk = 0, kDevBadRow = 1, kDevTooManySamples = 2, kDevCountMismatch = 3, kDevCopyTimeout = 4 };
 
 // Workspace layout of a grid: [status block 256 B][occupancy bits][touched bits]
 struct WorkspaceLayout {

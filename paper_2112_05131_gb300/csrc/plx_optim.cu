@@ -170,70 +170,77 @@ cudaError_t launch_tv(const GridView &g, const int64_t *seg_start, const int64_t
 }
 
 // --------------------------------------------------------------------------- RMSProp
-// Thread per row; a warp covers the 32 rows of one word of the touched mask.
-// Dense mode visits every row, sparse mode only the marked ones.  Entries
-// with a zero gradient keep x and v; a row with any update is re-packed into
-// its BF16-SH form when the grid has one.
-__global__ void __launch_bounds__(256) rmsprop_kernel(GridView g, float *__restrict__ rows,
-                                                      uint16_t *__restrict__ rows_h, float *__restrict__ grad,
-                                                      float *__restrict__ v, float lr_sigma, float lr_sh,
-                                                      float beta, float eps, int sparse, int64_t n_words) {
+// One warp per word of the touched mask (32 rows): the word's marked rows (all
+// rows in dense mode) are updated four at a time with 8 lanes per row (lane q
+// owns values 4q..4q+3), so each warp instruction covers 4 whole rows.  The
+// grid has enough warps to keep every touched row's loads in flight at once,
+// which the scattered rows need to reach DRAM efficiently.  Entries with a zero
+// gradient keep x and v; a row with any update is re-packed into its BF16-SH
+// form when the grid has one.
+__device__ __forceinline__ void rms_quarter(int64_t r, int q, float *__restrict__ rows, uint16_t *__restrict__ rows_h,
+                                            float *__restrict__ grad, float *__restrict__ v, float lr_sigma, float lr_sh,
+                                            float beta, float eps, bool active) {
+    float4 g4 = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+    if (active && q < 7) g4 = reinterpret_cast<const float4 *>(grad + r * kRowF)[q];
+    const bool nz = g4.x != 0.0f || g4.y != 0.0f || g4.z != 0.0f || g4.w != 0.0f;
+    const unsigned grp = __ballot_sync(kFull, nz);
     const int lane = threadIdx.x & 31;
+    const bool row_any = (grp >> (lane & ~7)) & 0xffu;
+    if (!active || !row_any || q == 7) return;
+    float4 *xp = reinterpret_cast<float4 *>(rows + r * kRowF) + q;
+    float4 *vp = reinterpret_cast<float4 *>(v + r * kRowF) + q;
+    float4 x4 = *xp, v4 = *vp;
+    float *xe = &x4.x, *ve = &v4.x;
+    const float *ge = &g4.x;
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+        const float gg = ge[c];
+        if (gg != 0.0f) {
+            const float lr = (q == 0 && c == 0) ? lr_sigma : lr_sh;
+            const float vv = fmaf(beta, ve[c], (1.0f - beta) * gg * gg);
+            ve[c] = vv;
+            xe[c] = xe[c] - lr * gg / (sqrtf(vv) + eps);
+        }
+    }
+    *xp = x4;
+    *vp = v4;
+    if (nz) reinterpret_cast<float4 *>(grad + r * kRowF)[q] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+    if (rows_h) {
+        // column col sits in BF16 slot col + 1 (SH), density bits in slots 0-1
+        uint16_t *hp = rows_h + r * kRowH;
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            const int col = 4 * q + c;
+            if (col == 0)
+                *reinterpret_cast<uint32_t *>(hp) = __float_as_uint(xe[0]);
+            else
+                hp[col + 1] = bf16_bits_rn(xe[c]);
+        }
+    }
+}
+
+__global__ void __launch_bounds__(256) rmsprop_kernel(GridView g, float *__restrict__ rows, uint16_t *__restrict__ rows_h,
+                                                      float *__restrict__ grad, float *__restrict__ v, float lr_sigma,
+                                                      float lr_sh, float beta, float eps, int sparse, int64_t n_words) {
+    const int lane = threadIdx.x & 31;
+    const int q = lane & 7;
+    const int grp = lane >> 3;
     for (int64_t w = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); w < n_words;
          w += (int64_t)gridDim.x * (blockDim.x >> 5)) {
-        const uint32_t mask = sparse ? g.touched[w] : 0xffffffffu;
-        const int64_t r = w * 32 + lane;
-        if (((mask >> lane) & 1u) && r < g.M) {
-            float4 *gp = reinterpret_cast<float4 *>(grad + r * kRowF);
-            float4 *xp = reinterpret_cast<float4 *>(rows + r * kRowF);
-            float4 *vp = reinterpret_cast<float4 *>(v + r * kRowF);
-            float4 g4[7];
-            bool any = false;
-#pragma unroll
-            for (int q = 0; q < 7; ++q) {
-                g4[q] = gp[q];
-                any = any || g4[q].x != 0.0f || g4[q].y != 0.0f || g4[q].z != 0.0f || g4[q].w != 0.0f;
-            }
-            if (any) {
-                float x[kNV];
-#pragma unroll
-                for (int q = 0; q < 7; ++q) {
-                    float4 x4 = xp[q], v4 = vp[q];
-                    float *xe = &x4.x, *ve = &v4.x;
-                    const float *ge = &g4[q].x;
-#pragma unroll
-                    for (int c = 0; c < 4; ++c) {
-                        const float gg = ge[c];
-                        if (gg != 0.0f) {
-                            const float lr = (q == 0 && c == 0) ? lr_sigma : lr_sh;
-                            const float vv = fmaf(beta, ve[c], (1.0f - beta) * gg * gg);
-                            ve[c] = vv;
-                            xe[c] = xe[c] - lr * gg / (sqrtf(vv) + eps);
-                        }
-                        x[4 * q + c] = xe[c];
-                    }
-                    xp[q] = x4;
-                    vp[q] = v4;
-                    gp[q] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
-                }
-                if (rows_h) {
-                    // slot 0-1: density bits; slot 2+s: bf16 of SH s (= column s+1); slots 29-31: 0
-                    uint32_t wd[16];
-                    wd[0] = __float_as_uint(x[0]);
-#pragma unroll
-                    for (int p = 0; p < 14; ++p) {
-                        const uint32_t lo = bf16_bits_rn(x[1 + 2 * p]);
-                        const uint32_t hi = (2 * p + 1 < 27) ? bf16_bits_rn(x[min(2 + 2 * p, kNV - 1)]) : 0u;
-                        wd[1 + p] = lo | (hi << 16);
-                    }
-                    wd[15] = 0u;
-                    uint4 *hp = reinterpret_cast<uint4 *>(rows_h + r * kRowH);
-#pragma unroll
-                    for (int q = 0; q < 4; ++q) hp[q] = make_uint4(wd[4 * q], wd[4 * q + 1], wd[4 * q + 2], wd[4 * q + 3]);
-                }
-            }
+        const uint32_t word = g.touched[w];
+        uint32_t mask = sparse ? word : 0xffffffffu;
+        const int64_t left = g.M - w * 32;  // rows beyond M in the last word
+        if (left < 32) mask &= (1u << left) - 1u;
+        __syncwarp();
+        if (lane == 0 && word) g.touched[w] = 0u;  // both modes leave the mask clear
+        while (mask) {  // uniform
+            const int n = __popc(mask);
+            const bool active = grp < n;
+            const int bit = active ? __fns(mask, 0, grp + 1) : 0;
+            rms_quarter(w * 32 + bit, q, rows, rows_h, grad, v, lr_sigma, lr_sh, beta, eps, active);
+            // drop the (up to) four rows just handled
+            for (int k = 0; k < 4 && mask; ++k) mask &= mask - 1;
         }
-        if (lane == 0) g.touched[w] = 0u;
     }
 }
 
