@@ -59,6 +59,7 @@ def _load():
             "orc_render": (None, [I64, P, P, I64, P, P, P, I64, P, P, P]),
             "orc_render_backward": (None, [I64, P, P, I64, P, P, P, I64, P, P, P]),
             "orc_render_backward_abs": (None, [I64, P, P, I64, P, P, P, I64, P, P, P]),
+            "orc_render_backward_mag": (None, [I64, P, P, I64, P, P, P, I64, P, P, P]),
             "orc_mse": (D, [P, P, I64, P]),
             "orc_tv": (D, [I64, P, P, I64, P, P, I64, D, D, P]),
             "orc_rmsprop": (None, [I64, P, P, P, D, D, D, D]),
@@ -192,6 +193,23 @@ def render_backward_abs(R, idx, rows, o, d, grad_rgb, step_vox=0.5, bg=(1.0, 1.0
     assert np.all(g >= 0)
     out = np.zeros((rows.shape[0], NV), np.float64)
     lib.orc_render_backward_abs(R, _p(idx), _p(rows), rows.shape[1], _p(_aabb(aabb)), _p(o), _p(d),
+                                o.shape[0], _p(_opts(step_vox, bg, stop_thresh)), _p(g), _p(out))
+    return out
+
+
+def render_backward_mag(R, idx, rows, o, d, grad_rgb, step_vox=0.5, bg=(1.0, 1.0, 1.0), stop_thresh=0.0,
+                        aabb=None):
+    """The magnitude adjoint: as render_backward_abs, but the density term takes |g| delta (T_{s+1} |c| + |R_s|),
+    the size of the two numbers the adjoint subtracts.  Times a unit roundoff it bounds the rounding error
+    of an implementation that forms T_{s+1} c - R_s in lower precision."""
+    lib = _load()
+    idx = _c(idx, np.int32)
+    rows = _rows(rows)
+    o = _c(o, np.float64)
+    d = _c(d, np.float64)
+    g = _c(np.abs(np.asarray(grad_rgb, np.float64)), np.float64)
+    out = np.zeros((rows.shape[0], NV), np.float64)
+    lib.orc_render_backward_mag(R, _p(idx), _p(rows), rows.shape[1], _p(_aabb(aabb)), _p(o), _p(d),
                                 o.shape[0], _p(_opts(step_vox, bg, stop_thresh)), _p(g), _p(out))
     return out
 

@@ -34,6 +34,8 @@
  *   orc_render_backward pinned: central finite differences of orc_render
  *   orc_render_backward_abs  pinned: bounds the adjoint of every smaller g
  *                       (triangle inequality), equals it for one-sign terms
+ *   orc_render_backward_mag  pinned: dominates the absolute-value adjoint,
+ *                       equals it where T_{s+1} c and R_s do not cancel
  *   orc_tv              pinned: linear-ramp closed form, finite differences
  *   orc_rmsprop         pinned: constant-gradient closed form
  *   orc_prune           pinned: exhaustive 3x3x3 enumeration on small grids
@@ -360,6 +362,10 @@ void orc_render(int64_t R, const int32_t *idx, const double *rows, int64_t row_s
  * (|g_ch| and |T_{s+1} c - R_s|, |Y_l| in place of the signed factors): for
  * g >= 0 the result bounds |adjoint(g')| for every g' with |g'| <= g, which
  * the tests use to carry an uncertainty of dL/dC into the gradient.
+ * abs_mode = 2 ("magnitude") takes the density term's two operands apart,
+ * |g_ch| delta (T_{s+1} |c| + |R_s|): the size of the numbers an FP32
+ * implementation subtracts, which bounds its rounding error where they
+ * nearly cancel (long rays whose colours resemble what lies behind them).
  */
 static void render_backward_impl(int64_t R, const int32_t *idx, const double *rows, int64_t row_stride,
                                  const double *aabb, const double *o, const double *d, int64_t n,
@@ -401,7 +407,10 @@ static void render_backward_impl(int64_t R, const int32_t *idx, const double *ro
                 if (q->sigma_pre > 0.0)
                     for (int ch = 0; ch < 3; ++ch) {
                         double term = gr[ch] * delta * (T_next * q->c[ch] - Rs[s][ch]);
-                        gsig += abs_mode ? fabs(term) : term;
+                        if (abs_mode == 2)
+                            gsig += fabs(gr[ch]) * delta * (T_next * fabs(q->c[ch]) + fabs(Rs[s][ch]));
+                        else
+                            gsig += abs_mode ? fabs(term) : term;
                     }
                 double gk[ORC_NV - 1];
                 for (int ch = 0; ch < 3; ++ch) {
@@ -441,6 +450,13 @@ void orc_render_backward_abs(int64_t R, const int32_t *idx, const double *rows, 
                              const double *opts, const double *grad_rgb, double *grad_rows)
 {
     render_backward_impl(R, idx, rows, row_stride, aabb, o, d, n, opts, grad_rgb, grad_rows, 1);
+}
+
+void orc_render_backward_mag(int64_t R, const int32_t *idx, const double *rows, int64_t row_stride,
+                             const double *aabb, const double *o, const double *d, int64_t n,
+                             const double *opts, const double *grad_rgb, double *grad_rows)
+{
+    render_backward_impl(R, idx, rows, row_stride, aabb, o, d, n, opts, grad_rgb, grad_rows, 2);
 }
 
 /* ------------------------------------------------------------------------- */

@@ -441,6 +441,29 @@ def test_backward_abs_bounds_the_adjoint():
     assert np.all(b1[:, 10:] == 0)
 
 
+def test_backward_mag_dominates_abs_and_matches_it_without_cancellation():
+    """The magnitude adjoint replaces |T_{s+1} c - R_s| by T_{s+1} c + R_s (both non-negative): it dominates
+    the absolute-value adjoint, agrees with it on the SH columns, and equals it when every ray has one
+    sample and the background is black (then R_s = 0 for that sample)."""
+    R = 6
+    idx, rows = random_sparse(R, 0.3, 150, sigma_range=(0.5, 6.0))
+    o, d = synth.random_rays(30, seed=151)
+    o, d = o.astype(float), d.astype(float)
+    g = np.random.default_rng(152).uniform(0.1, 1.0, size=(30, 3))
+    a = oracle.render_backward_abs(R, idx, rows, o, d, g, bg=(0.3, 0.5, 0.7))
+    m = oracle.render_backward_mag(R, idx, rows, o, d, g, bg=(0.3, 0.5, 0.7))
+    assert np.all(m >= a * (1 - 1e-13))
+    assert np.allclose(m[:, 1:], a[:, 1:], rtol=1e-13, atol=0)
+    assert np.any(m[:, 0] > a[:, 0] * (1 + 1e-6))  # the density column does see cancellation here
+    # one sample per ray: the step is longer than the box diagonal; black background
+    a1 = oracle.render_backward_abs(R, idx, rows, o, d, g, step_vox=20.0, bg=(0.0, 0.0, 0.0))
+    m1 = oracle.render_backward_mag(R, idx, rows, o, d, g, step_vox=20.0, bg=(0.0, 0.0, 0.0))
+    assert np.any(a1[:, 0] > 0)
+    assert np.allclose(m1, a1, rtol=1e-13, atol=0)
+    # signs of g do not matter to it
+    assert np.allclose(oracle.render_backward_mag(R, idx, rows, o, d, -g, bg=(0.3, 0.5, 0.7)), m, rtol=1e-12, atol=0)
+
+
 def test_mse_gradient():
     rng = np.random.default_rng(0)
     p, t = rng.uniform(size=(10, 3)), rng.uniform(size=(10, 3))
