@@ -184,6 +184,71 @@ plx_status plx_render_backward(const plx_grid *grid, const float *d_origins, con
                                int64_t n, const plx_render_opts *opts, const float *d_grad_rgb,
                                float *d_grad_rows, void *stream);
 
+/* ---------------------------------------------------------------- training march
+ *
+ * The forward/adjoint pair of the optimisation step (Sec. 3.4; Supp. A.1:
+ * batches of 5000 rays), computing exactly what plx_render and
+ * plx_render_backward compute (up to FP32 summation order), but splitting
+ * every ray into chunks of 32 compacted samples that run as independent work
+ * items, so that the few rays with hundreds of non-empty samples do not set
+ * the time of a small batch.  plx_render_train leaves a march state in a
+ * caller buffer (per chunk: where its samples start, its transmittance before
+ * it and the colour that arrives after it); plx_render_backward_train reads it
+ * instead of re-marching the rays.
+ *
+ * With stop_thresh > 0 both calls use the one-warp-per-ray kernels of
+ * plx_render / plx_render_backward (the state then only records that). */
+
+/* Bytes of march state for n rays on this grid with these options (0 for
+ * invalid arguments or n >= 2^31).  The layout is private to the library. */
+size_t plx_march_state_bytes(const plx_grid *grid, int64_t n, const plx_render_opts *opts);
+
+/* As plx_render, and writes the march state of these rays into d_state
+ * (device, 16-byte aligned, at least plx_march_state_bytes(grid, n, opts)
+ * bytes, caller-owned).  Requires n x (chunks per ray) < 2^31, where chunks
+ * per ray = ceil((longest chord / delta + 2) / 32) + 1. */
+plx_status plx_render_train(const plx_grid *grid, const float *d_origins, const float *d_dirs, int64_t n,
+                            const plx_render_opts *opts, float *d_rgb, float *d_T_end, void *d_state,
+                            size_t state_bytes, void *stream);
+
+/* As plx_render_backward, for the rays, grid and options of the last
+ * plx_render_train that wrote d_state, enqueued after it, before the grid's
+ * rows change.  The kernel checks the state's header (ray buffers, grid rows,
+ * sizes, options) on the device; on a mismatch it adds nothing and plx_check
+ * then returns PLX_EDEVICE. */
+plx_status plx_render_backward_train(const plx_grid *grid, const float *d_origins, const float *d_dirs, int64_t n,
+                                     const plx_render_opts *opts, const float *d_grad_rgb, const void *d_state,
+                                     size_t state_bytes, float *d_grad_rows, void *stream);
+
+/* ---------------------------------------------------------------- serving
+ *
+ * Rendering image requests of several resident scenes in one launch (Sec. 3:
+ * a trained grid renders novel views directly, with no network).  A request
+ * is cut into 16x16-pixel tiles; a launch takes any list of tiles, from any
+ * requests and scenes, which lets a scheduler batch requests continuously.
+ * Each pixel's ray is generated as plx_gen_rays does and marched as plx_render
+ * does, so its colour does not depend on the rest of the launch. */
+#define PLX_TILE_W 16
+#define PLX_TILE_H 16
+#define PLX_TILES_MAX_SCENES 8
+
+typedef struct {
+    int32_t scene;   /* index into the call's grids[] */
+    int32_t camera;  /* index into d_cams (float [18] each, the layout of plx_gen_rays) */
+    int32_t x0, y0;  /* top-left pixel of the tile */
+    int32_t W, H;    /* size of the request's image; the tile's pixels outside it are skipped */
+    float *d_rgb;    /* the request's image, float [H][W][3] row-major, device, caller-owned */
+} plx_tile;
+
+/* Renders n_tiles tiles (d_tiles: device array) with the background and
+ * step of *opts.  grids: host array of 1..PLX_TILES_MAX_SCENES grid handles,
+ * all of the same sh_form, each with the rows its form renders from.  A tile
+ * whose scene or camera index is out of range, or whose d_rgb is NULL, is
+ * skipped and recorded in grids[0]'s status (plx_check on grids[0] then
+ * returns PLX_EDEVICE).  Tiles must not overlap. */
+plx_status plx_render_tiles(const plx_grid *const *grids, int32_t n_grids, const float *d_cams, int32_t n_cams,
+                            const plx_tile *d_tiles, int64_t n_tiles, const plx_render_opts *opts, void *stream);
+
 /* Traffic accounting (a measurement aid, not part of the method): for each
  * ray, d_counts int64 [n][2] receives (a) the number of distinct lattice
  * nodes that are corners of the ray's sampled cells having at least one

@@ -209,8 +209,14 @@ plx_status plx_check(const plx_grid *grid, void *stream) {
     if (e != cudaSuccess) return cuda_status(e, "plx_check");
     if (code == plx::kDevBadRow) return fail(PLX_EDEVICE, "an index volume entry is >= n_rows");
     if (code == plx::kDevTooManySamples) return fail(PLX_EDEVICE, "a ray needed more samples than the backward supports");
-    if (code == plx::kDevCountMismatch) return fail(PLX_EDEVICE, "apply was given a row count that its workspace does not hold");
-    if (code == plx::kDevCopyTimeout) return fail(PLX_ETIMEOUT, "a row copy into shared memory did not complete; the ray was abandoned");
+    if (code == plx::kDevCountMismatch)
+        return fail(PLX_EDEVICE, "a count disagreed with its plan (apply given a row count its workspace does not "
+                                 "hold, or a training chunk rescan found a different sample count)");
+    if (code == plx::kDevBadTile)
+        return fail(PLX_EDEVICE, "plx_render_tiles skipped a tile with an out-of-range scene or camera or a NULL image");
+    if (code == plx::kDevStateMismatch)
+        return fail(PLX_EDEVICE, "plx_render_backward_train was given a march state that plx_render_train did not "
+                                 "write for these rays, this grid and these options; no gradient was added");
     if (code != 0) return fail(PLX_EDEVICE, "device status %d", code);
     return PLX_OK;
 }
@@ -252,6 +258,117 @@ plx_status plx_render_backward(const plx_grid *grid, const float *d_origins, con
                     p.max_chunks * 32);
     return cuda_status(plx::launch_render_backward(grid->view, d_origins, d_dirs, n, p, d_grad_rgb, d_grad_rows,
                                                    static_cast<cudaStream_t>(stream)), "plx_render_backward");
+}
+
+size_t plx_march_state_bytes(const plx_grid *grid, int64_t n, const plx_render_opts *opts) {
+    if (!grid || check_opts(opts) != PLX_OK || n < 0 || n >= (int64_t(1) << 31)) return 0;
+    const plx::RenderParams p = make_params(grid, opts);
+    return plx::MarchLayout::make(n, p.max_chunks).total;
+}
+
+namespace {
+
+// Validates a march-state buffer for n rays and fills the pointers and the header it must carry.
+plx_status march_state(const plx_grid *grid, const float *d_origins, const float *d_dirs, int64_t n,
+                       const plx_render_opts *opts, const plx::RenderParams &p, void *d_state, size_t state_bytes,
+                       plx::MarchPtrs *ptrs, plx::MarchHeader *hdr) {
+    if (!d_state) return fail(PLX_EINVAL, "d_state is NULL");
+    if (!aligned(d_state, 16)) return fail(PLX_EINVAL, "d_state must be 16-byte aligned");
+    if (n * (int64_t)p.max_chunks >= (int64_t(1) << 31))
+        return fail(PLX_EINVAL, "n x chunks per ray (%lld x %d) exceeds the work-item limit 2^31; split the batch",
+                    (long long)n, p.max_chunks);
+    const plx::MarchLayout L = plx::MarchLayout::make(n, p.max_chunks);
+    if (state_bytes < L.total)
+        return fail(PLX_EINVAL, "d_state holds %zu bytes, plx_march_state_bytes gives %zu", state_bytes, L.total);
+    char *b = static_cast<char *>(d_state);
+    ptrs->hdr = reinterpret_cast<plx::MarchHeader *>(b + L.hdr_off);
+    ptrs->n_occ = reinterpret_cast<int32_t *>(b + L.nocc_off);
+    ptrs->first = reinterpret_cast<int32_t *>(b + L.first_off);
+    ptrs->items = reinterpret_cast<int2 *>(b + L.items_off);
+    ptrs->part = reinterpret_cast<float4 *>(b + L.part_off);
+    ptrs->live = reinterpret_cast<uint8_t *>(b + L.live_off);
+    ptrs->max_chunks = p.max_chunks;
+    std::memset(hdr, 0, sizeof(*hdr));
+    hdr->magic = plx::kMarchMagic;
+    hdr->max_chunks = p.max_chunks;
+    hdr->n = n;
+    hdr->total_items = 0;
+    hdr->R = grid->desc.reso;
+    hdr->M = grid->desc.n_rows;
+    hdr->delta = p.delta;
+    hdr->delta_lo = p.delta_lo;
+    hdr->stop = p.stop;
+    hdr->mode = opts->stop_thresh > 0.0f ? plx::kMarchRecompute : plx::kMarchChunked;
+    hdr->ro = d_origins;
+    hdr->rd = d_dirs;
+    hdr->rows = grid->rows ? static_cast<const void *>(grid->rows) : static_cast<const void *>(grid->rows_h);
+    return PLX_OK;
+}
+
+}  // namespace
+
+plx_status plx_render_train(const plx_grid *grid, const float *d_origins, const float *d_dirs, int64_t n,
+                            const plx_render_opts *opts, float *d_rgb, float *d_T_end, void *d_state,
+                            size_t state_bytes, void *stream) {
+    plx_status st = check_grid(grid);
+    if (st == PLX_OK) st = check_opts(opts);
+    if (st != PLX_OK) return st;
+    if (n < 0 || n >= (int64_t(1) << 31)) return fail(PLX_EINVAL, "n out of range");
+    if (n > 0 && (!d_origins || !d_dirs || !d_rgb)) return fail(PLX_EINVAL, "NULL ray or output buffer");
+    if (grid->desc.sh_form == PLX_SH_F32 && grid->desc.n_rows > 0 && !grid->rows) return fail(PLX_EINVAL, "grid has no F32 rows");
+    const plx::RenderParams p = make_params(grid, opts);
+    plx::MarchPtrs ptrs;
+    plx::MarchHeader hdr;
+    st = march_state(grid, d_origins, d_dirs, n, opts, p, d_state, state_bytes, &ptrs, &hdr);
+    if (st != PLX_OK) return st;
+    return cuda_status(plx::launch_render_train(grid->view, d_origins, d_dirs, n, p, ptrs, hdr, d_rgb, d_T_end,
+                                                static_cast<cudaStream_t>(stream)), "plx_render_train");
+}
+
+plx_status plx_render_backward_train(const plx_grid *grid, const float *d_origins, const float *d_dirs, int64_t n,
+                                     const plx_render_opts *opts, const float *d_grad_rgb, const void *d_state,
+                                     size_t state_bytes, float *d_grad_rows, void *stream) {
+    plx_status st = check_grid(grid);
+    if (st == PLX_OK) st = check_opts(opts);
+    if (st != PLX_OK) return st;
+    if (n < 0 || n >= (int64_t(1) << 31)) return fail(PLX_EINVAL, "n out of range");
+    if (n > 0 && (!d_origins || !d_dirs || !d_grad_rgb || !d_grad_rows)) return fail(PLX_EINVAL, "NULL buffer");
+    if (d_grad_rows && !aligned(d_grad_rows, 16)) return fail(PLX_EINVAL, "d_grad_rows must be 16-byte aligned");
+    const plx::RenderParams p = make_params(grid, opts);
+    plx::MarchPtrs ptrs;
+    plx::MarchHeader hdr;
+    st = march_state(grid, d_origins, d_dirs, n, opts, p, const_cast<void *>(d_state), state_bytes, &ptrs, &hdr);
+    if (st != PLX_OK) return st;
+    if (hdr.mode == plx::kMarchRecompute && p.max_chunks > 256)
+        return fail(PLX_EUNSUPPORTED, "rays of up to %d samples with stop_thresh > 0 exceed the backward's 8192-sample "
+                    "limit; raise step_vox", p.max_chunks * 32);
+    return cuda_status(plx::launch_render_backward_train(grid->view, d_origins, d_dirs, n, p, ptrs, hdr, d_grad_rgb,
+                                                         d_grad_rows, static_cast<cudaStream_t>(stream)),
+                       "plx_render_backward_train");
+}
+
+plx_status plx_render_tiles(const plx_grid *const *grids, int32_t n_grids, const float *d_cams, int32_t n_cams,
+                            const plx_tile *d_tiles, int64_t n_tiles, const plx_render_opts *opts, void *stream) {
+    plx_status st = check_opts(opts);
+    if (st != PLX_OK) return st;
+    if (!grids || n_grids < 1 || n_grids > PLX_TILES_MAX_SCENES)
+        return fail(PLX_EINVAL, "need 1..%d grids", PLX_TILES_MAX_SCENES);
+    if (n_tiles < 0 || n_tiles >= (int64_t(1) << 30)) return fail(PLX_EINVAL, "n_tiles out of range");
+    if (n_tiles > 0 && (!d_tiles || !d_cams || n_cams < 1)) return fail(PLX_EINVAL, "NULL tiles or cameras");
+    if (n_tiles > 0 && !aligned(d_tiles, 8)) return fail(PLX_EINVAL, "d_tiles must be 8-byte aligned");
+    plx::GridView views[PLX_TILES_MAX_SCENES];
+    plx::RenderParams params[PLX_TILES_MAX_SCENES];
+    for (int i = 0; i < n_grids; ++i) {
+        const plx_grid *g = grids[i];
+        if (!g) return fail(PLX_EINVAL, "grids[%d] is NULL", i);
+        if (g->desc.sh_form != grids[0]->desc.sh_form) return fail(PLX_EINVAL, "grids of one call must share sh_form");
+        if (g->desc.sh_form == PLX_SH_F32 && g->desc.n_rows > 0 && !g->rows)
+            return fail(PLX_EINVAL, "grids[%d] has no F32 rows", i);
+        views[i] = g->view;
+        params[i] = make_params(g, opts);
+    }
+    return cuda_status(plx::launch_render_tiles(views, params, n_grids, d_cams, n_cams, d_tiles, n_tiles,
+                                                static_cast<cudaStream_t>(stream)), "plx_render_tiles");
 }
 
 plx_status plx_count_nodes(const plx_grid *grid, const float *d_origins, const float *d_dirs, int64_t n,

@@ -21,7 +21,7 @@ constexpr int kRowH = 32;        // uint16 per BF16 row (64 bytes)
 constexpr unsigned kFull = 0xffffffffu;
 
 // device status codes (stored in the grid workspace's first word)
-enum : int { kDevOk = 0, kDevBadRow = 1, kDevTooManySamples = 2, kDevCountMismatch = 3, kDevCopyTimeout = 4 };
+enum : int { kDevOk = 0, kDevBadRow = 1, kDevTooManySamples = 2, kDevCountMismatch = 3, kDevStateMismatch = 4, kDevBadTile = 5 };
 
 // Workspace layout of a grid: [status block 256 B][occupancy bits][touched bits]
 struct WorkspaceLayout {
@@ -305,6 +305,55 @@ struct RenderParams {
     int max_chunks;
 };
 
+// March state written by plx_render_train and read by plx_render_backward_train.
+// Per ray: the number of compacted (occupied-cell) samples and, per chunk of 32
+// of them, the index of its first sample (plus one past the last sample); per
+// chunk a float4 that first holds the chunk's local colour and transmittance
+// product (C_loc, P) and, after the per-ray combine, the remaining colour after
+// the chunk and the transmittance before it (R_after, T_before); a flag for
+// chunks with positive density; and the flat list of (ray, chunk) work items.
+struct MarchHeader {
+    uint32_t magic;
+    int32_t max_chunks;
+    int64_t n;
+    int32_t total_items;  // appended to by the plan kernel
+    int32_t R;
+    int64_t M;
+    float delta, delta_lo, stop;
+    int32_t mode;         // kMarchChunked, or kMarchRecompute when the adjoint re-marches
+    const void *ro, *rd;  // the rays the state belongs to
+    const void *rows;     // the grid's row storage
+};
+constexpr uint32_t kMarchMagic = 0x53584c50u;
+enum : int32_t { kMarchChunked = 1, kMarchRecompute = 2 };
+
+struct MarchLayout {
+    size_t hdr_off, nocc_off, first_off, items_off, part_off, live_off, total;
+    static size_t round256(size_t b) { return (b + 255) & ~size_t(255); }
+    static MarchLayout make(int64_t n, int max_chunks) {
+        MarchLayout L;
+        const size_t slots = size_t(n) * size_t(max_chunks);
+        L.hdr_off = 0;
+        L.nocc_off = 256;
+        L.first_off = L.nocc_off + round256(size_t(n) * 4);
+        L.items_off = L.first_off + round256(size_t(n) * size_t(max_chunks + 1) * 4);
+        L.part_off = L.items_off + round256(slots * 8);
+        L.live_off = L.part_off + round256(slots * 16);
+        L.total = L.live_off + round256(slots);
+        return L;
+    }
+};
+
+struct MarchPtrs {
+    MarchHeader *hdr;
+    int32_t *n_occ;   // [n] compacted samples per ray
+    int32_t *first;   // [n][max_chunks + 1] first sample of each chunk, then one past the last sample
+    int2 *items;      // [total_items] (ray, chunk)
+    float4 *part;     // [n][max_chunks] (C_loc, P), then (R_after, T_before)
+    uint8_t *live;    // [n][max_chunks] 1 if any sample of the chunk has positive density
+    int max_chunks;
+};
+
 cudaError_t launch_gen_rays(const float *cams, int n_cams, int W, int H, const int64_t *pix, int64_t n,
                             float *o, float *d, cudaStream_t s);
 cudaError_t launch_render(const GridView &g, const float *o, const float *d, int64_t n,
@@ -312,6 +361,13 @@ cudaError_t launch_render(const GridView &g, const float *o, const float *d, int
 cudaError_t launch_render_backward(const GridView &g, const float *o, const float *d, int64_t n,
                                    const RenderParams &p, const float *grad_rgb, float *grad_rows,
                                    cudaStream_t s);
+cudaError_t launch_render_train(const GridView &g, const float *o, const float *d, int64_t n, const RenderParams &p,
+                                const MarchPtrs &st, const MarchHeader &hdr, float *rgb, float *T_end, cudaStream_t s);
+cudaError_t launch_render_backward_train(const GridView &g, const float *o, const float *d, int64_t n,
+                                         const RenderParams &p, const MarchPtrs &st, const MarchHeader &hdr,
+                                         const float *grad_rgb, float *grad_rows, cudaStream_t s);
+cudaError_t launch_render_tiles(const GridView *g, const RenderParams *p, int n_scenes, const float *cams,
+                                int n_cams, const plx_tile *tiles, int64_t n_tiles, cudaStream_t s);
 cudaError_t launch_count_nodes(const GridView &g, const float *o, const float *d, int64_t n, const RenderParams &p,
                                int64_t *out, cudaStream_t s);
 cudaError_t launch_mse_grad(const float *rgb, const float *target, int64_t n, float *grad, float *loss,

@@ -1,0 +1,378 @@
+// plx_march.cuh -- the pieces of the ray march (Eq. 1) that the forward, the
+// adjoint and the chunk-parallel training kernels share: per-ray setup, sample
+// positions, the trilinear gather, SH colour, chunk compositing and sample
+// compaction against the occupancy mask.
+#pragma once
+
+#include "plx_internal.cuh"
+
+namespace plx {
+
+// Four resident 4-warp CTAs per SM: up to 128 registers a thread, enough for the
+// gather to keep most of a chunk's row loads in flight (measured on the 512^3
+// training batch against 2 and 3 CTAs, which buy more registers but fewer warps).
+constexpr int kGatherBlocks = 4;
+
+// --------------------------------------------------------------------------- per-ray setup
+struct RaySetup {
+    DF A[3];       // origin minus box corner, exact as a double-float
+    float d[3];    // unit direction as given
+    DF tn, tf;     // clipped parameter range
+    float og[3];   // FP32 grid-coordinate origin and direction, for the cheap candidate test
+    float dg[3];
+    float Y[9];    // SH basis at the direction
+    bool hit;
+};
+
+__device__ __forceinline__ RaySetup ray_setup_od(const GridView &g, const float o[3], const float d[3]) {
+    RaySetup rs;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) rs.d[a] = d[a];
+    rs.hit = clip_box(g, o, rs.d, rs.tn, rs.tf);
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        rs.A[a] = df_two_sum(o[a], -g.lo[a]);
+        rs.og[a] = (o[a] - g.lo[a]) * g.inv_h[a];
+        rs.dg[a] = rs.d[a] * g.inv_h[a];
+    }
+    sh_basis(rs.d, rs.Y);
+    return rs;
+}
+
+__device__ __forceinline__ RaySetup ray_setup(const GridView &g, const float *__restrict__ ro,
+                                              const float *__restrict__ rd, int64_t ray) {
+    float o[3], d[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        o[a] = __ldg(ro + 3 * ray + a);
+        d[a] = __ldg(rd + 3 * ray + a);
+    }
+    return ray_setup_od(g, o, d);
+}
+
+// t_s = t_near + s * delta as a double-float (s * delta_hi is exact for s < 2^24).
+__device__ __forceinline__ DF sample_t(const RaySetup &rs, const RenderParams &p, int s) {
+    DF sd = df_two_prod((float)s, p.delta);
+    sd.lo = fmaf((float)s, p.delta_lo, sd.lo);
+    return df_add(rs.tn, sd);
+}
+
+// Grid coordinates of the point at parameter t: ((o - lo) + t d) / h per axis.
+__device__ __forceinline__ void sample_coords(const GridView &g, const RaySetup &rs, DF t, DF gc[3]) {
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        DF td = df_two_prod(t.hi, rs.d[a]);
+        td.lo = fmaf(t.lo, rs.d[a], td.lo);
+        gc[a] = df_mul(df_add(rs.A[a], td), DF{g.inv_h[a], g.inv_h_lo[a]});
+    }
+}
+
+// Read-only vector loads issued as volatile asm: the compiler keeps them in
+// program order ahead of their uses instead of sinking each next to its FMAs.
+__device__ __forceinline__ float4 ldg4_pinned(const float4 *p) {
+    float4 v;
+    asm volatile("ld.global.nc.v4.f32 {%0, %1, %2, %3}, [%4];" : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w) : "l"(p));
+    return v;
+}
+__device__ __forceinline__ uint4 ldg4_pinned(const uint4 *p) {
+    uint4 v;
+    asm volatile("ld.global.nc.v4.u32 {%0, %1, %2, %3}, [%4];" : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w) : "l"(p));
+    return v;
+}
+
+// Full sample: interpolated values at grid point gc, whose cell the caller has
+// already found occupied (compaction).  rows_out/f_out receive the corners.
+__device__ __forceinline__ bool gather_sample(const GridView &g, int form, const DF gc[3], float acc[kNV],
+                                              int32_t rows_out[8], float f_out[3]) {
+#pragma unroll
+    for (int q = 0; q < kNV; ++q) acc[q] = 0.0f;
+    Cell c = locate(g, gc);
+    f_out[0] = c.f[0];
+    f_out[1] = c.f[1];
+    f_out[2] = c.f[2];
+    int32_t r[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) r[k] = row_of(g, corner_node(g, c.base, k));
+    // every corner's row is requested before any is used: one memory round trip per
+    // chunk instead of eight (a NULL corner contributes w * 0, i.e. nothing)
+    if (form == PLX_SH_F32) {
+        float4 v[8][7];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            const float4 *p = reinterpret_cast<const float4 *>(g.rows + (int64_t)max(r[k], 0) * kRowF);
+#pragma unroll
+            for (int q = 0; q < 7; ++q) v[k][q] = r[k] >= 0 ? ldg4_pinned(p + q) : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+        }
+        // an empty volatile use of every loaded value, after all the loads: no FMA can be
+        // scheduled between two loads, so all 56 requests are in flight together
+#pragma unroll
+        for (int k = 0; k < 8; ++k)
+#pragma unroll
+            for (int q = 0; q < 7; ++q)
+                asm volatile("" : "+f"(v[k][q].x), "+f"(v[k][q].y), "+f"(v[k][q].z), "+f"(v[k][q].w));
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            const float w = corner_weight(c.f, k);
+#pragma unroll
+            for (int q = 0; q < 7; ++q) {
+                acc[4 * q + 0] = fmaf(w, v[k][q].x, acc[4 * q + 0]);
+                acc[4 * q + 1] = fmaf(w, v[k][q].y, acc[4 * q + 1]);
+                acc[4 * q + 2] = fmaf(w, v[k][q].z, acc[4 * q + 2]);
+                acc[4 * q + 3] = fmaf(w, v[k][q].w, acc[4 * q + 3]);
+            }
+        }
+    } else {
+        uint4 v[8][4];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            const uint4 *p = reinterpret_cast<const uint4 *>(g.rows_h + (int64_t)max(r[k], 0) * kRowH);
+#pragma unroll
+            for (int q = 0; q < 4; ++q) v[k][q] = r[k] >= 0 ? ldg4_pinned(p + q) : make_uint4(0u, 0u, 0u, 0u);
+        }
+#pragma unroll
+        for (int k = 0; k < 8; ++k)
+#pragma unroll
+            for (int q = 0; q < 4; ++q) asm volatile("" : "+r"(v[k][q].x), "+r"(v[k][q].y), "+r"(v[k][q].z), "+r"(v[k][q].w));
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            const float w = corner_weight(c.f, k);
+            const uint32_t wd[16] = {v[k][0].x, v[k][0].y, v[k][0].z, v[k][0].w, v[k][1].x, v[k][1].y,
+                                     v[k][1].z, v[k][1].w, v[k][2].x, v[k][2].y, v[k][2].z, v[k][2].w,
+                                     v[k][3].x, v[k][3].y, v[k][3].z, v[k][3].w};
+            acc[0] = fmaf(w, __uint_as_float(wd[0]), acc[0]);
+#pragma unroll
+            for (int sh = 0; sh < 27; ++sh) {
+                const uint32_t word = wd[1 + (sh >> 1)];
+                const uint32_t bits = (sh & 1) ? (word & 0xffff0000u) : (word << 16);
+                acc[1 + sh] = fmaf(w, __uint_as_float(bits), acc[1 + sh]);
+            }
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < 8; ++k) rows_out[k] = r[k];
+    return true;
+}
+
+// Density only (backward pass 1 and node counting).  The caller has already
+// found the sample's cell occupied (compaction), so the mask is not re-read.
+__device__ __forceinline__ float gather_sigma(const GridView &g, int form, const DF gc[3]) {
+    Cell c = locate(g, gc);
+    int32_t r[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) r[k] = row_of(g, corner_node(g, c.base, k));
+    float s = 0.0f;
+#pragma unroll
+    for (int k = 0; k < 8; ++k)
+        if (r[k] >= 0) s = fmaf(corner_weight(c.f, k), row_sigma(g, form, r[k]), s);
+    return s;
+}
+
+__device__ __forceinline__ void colour_of(const float acc[kNV], const float Y[9], float pre[3], float c[3]) {
+#pragma unroll
+    for (int ch = 0; ch < 3; ++ch) {
+        float p = 0.0f;
+#pragma unroll
+        for (int l = 0; l < 9; ++l) p = fmaf(Y[l], acc[1 + 9 * ch + l], p);
+        pre[ch] = p;
+        c[ch] = fmaxf(p, 0.0f);
+    }
+}
+
+// Warp inclusive prefix product (lane order).
+__device__ __forceinline__ float warp_incl_prod(float x, int lane) {
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+        const float v = __shfl_up_sync(kFull, x, off);
+        if (lane >= off) x *= v;
+    }
+    return x;
+}
+
+// Per-chunk compositing state shared by the kernels: given this lane's
+// density, returns alpha, T_s (before the sample), T_{s+1} and whether the
+// sample is taken (valid and T_s >= stop); Tc is the transmittance before
+// the chunk.  Transmittance is the running product of exp(-sigma delta).
+struct Composite {
+    float alpha, T, Tn;
+    bool take;
+    unsigned tmask;
+    float chunk_prod;  // product over the taken lanes, to advance Tc
+};
+
+__device__ __forceinline__ Composite composite(float sig, bool valid, float Tc, const RenderParams &p, int lane) {
+    Composite r;
+    r.alpha = -expm1f(-sig * p.delta);
+    const float e = 1.0f - r.alpha;
+    const float incl = warp_incl_prod(e, lane);
+    float excl = __shfl_up_sync(kFull, incl, 1);
+    if (lane == 0) excl = 1.0f;
+    r.T = Tc * excl;
+    r.Tn = Tc * incl;
+    r.take = valid && r.T >= p.stop;
+    r.tmask = __ballot_sync(kFull, r.take);
+    const int k = __popc(r.tmask);
+    r.chunk_prod = k > 0 ? __shfl_sync(kFull, incl, k - 1) : 1.0f;
+    return r;
+}
+
+// --------------------------------------------------------------------------- sample compaction
+// The candidates (all samples of the ray, in order) are tested against the
+// cell occupancy mask, kCand per lane at a time so that many mask loads are in
+// flight; samples whose cell has an occupied corner are appended, in order, to
+// a per-warp ring buffer in shared memory and processed 32 at a time.  A
+// skipped sample lies in a cell whose 8 corners are NULL (all values zero):
+// its alpha is exactly 0, it multiplies T by exactly 1 and adds nothing, so
+// the compacted march evaluates the same sum.
+constexpr int kCand = 8;    // candidates per lane per refill
+constexpr int kRing = 512;  // ring capacity >= 31 + 32 kCand, a power of two
+
+struct Cand {
+    bool valid, occ;
+};
+
+// Is sample s inside the clipped ray (valid), and is its cell non-empty (occ)?
+// The answer must equal the double-float one exactly (it decides which samples
+// are marched).  Plain FP32 coordinates are within ~3e-4 of a cell of the
+// double-float ones (rounding of t_near, delta, the direction and the grid
+// scale, for R <= 2048); a candidate whose FP32 coordinate lies within kFaceEps
+// of a cell face on any axis, or whose t lies within kTEps of t_far, is
+// re-evaluated in double-float, so the cheap path is taken only where both agree.
+constexpr float kFaceEps = 2e-3f;
+
+__device__ __forceinline__ Cand test_candidate(const GridView &g, const RaySetup &rs, const RenderParams &p, int s) {
+    Cand c;
+    c.occ = false;
+    c.valid = false;
+    if (s >= p.max_chunks * 32) return c;
+    const float t32 = fmaf((float)s, p.delta, rs.tn.hi);
+    const float kTEps = 1e-5f * (fabsf(rs.tf.hi) + 1.0f);
+    bool exact = fabsf(t32 - rs.tf.hi) <= kTEps;
+    if (!exact && t32 > rs.tf.hi) return c;  // clearly past t_far
+    int b[3];
+    const float rm1 = (float)(g.R - 1);
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        const float x = fmaf(t32, rs.dg[a], rs.og[a]);
+        const float fl = floorf(x);
+        exact = exact || (x - fl) < kFaceEps || (fl + 1.0f - x) < kFaceEps || x < kFaceEps || x > rm1 - kFaceEps;
+        b[a] = (int)fl;
+    }
+    if (exact) {
+        const DF t = sample_t(rs, p, s);
+        c.valid = df_lt(t, rs.tf);
+        if (c.valid) {
+            DF gc[3];
+            sample_coords(g, rs, t, gc);
+            c.occ = cell_occupied(g, locate(g, gc).base);
+        }
+        return c;
+    }
+    c.valid = true;
+    c.occ = cell_occupied(g, ((int64_t)b[0] * g.R + b[1]) * g.R + b[2]);
+    return c;
+}
+
+struct Stream {
+    int next;   // next candidate sample index to test
+    int head;   // ring read position (absolute)
+    int tail;   // ring write position (absolute)
+    bool exhausted;
+};
+
+// Append occupied candidates until 32 are queued or the ray has no candidates left.
+__device__ __forceinline__ void refill(const GridView &g, const RaySetup &rs, const RenderParams &p, int *ring,
+                                       Stream &st, int lane) {
+    const unsigned lt = (1u << lane) - 1u;
+    while (st.tail - st.head < 32 && !st.exhausted) {
+        Cand c[kCand];
+#pragma unroll
+        for (int j = 0; j < kCand; ++j) c[j] = test_candidate(g, rs, p, st.next + 32 * j + lane);
+#pragma unroll
+        for (int j = 0; j < kCand; ++j) {
+            const unsigned m = __ballot_sync(kFull, c[j].occ);
+            if (c[j].occ) ring[(st.tail + __popc(m & lt)) & (kRing - 1)] = st.next + 32 * j + lane;
+            st.tail += __popc(m);
+        }
+        // valid candidates form a prefix of the sample indices
+        st.exhausted = __ballot_sync(kFull, c[kCand - 1].valid) != kFull;
+        st.next += 32 * kCand;
+    }
+    __syncwarp();
+}
+
+// Take the next (up to) 32 queued samples: returns the count; lane i gets sample s (if i < count).
+__device__ __forceinline__ int take_chunk(const int *ring, Stream &st, int lane, int &s) {
+    const int cnt = min(st.tail - st.head, 32);
+    s = lane < cnt ? ring[(st.head + lane) & (kRing - 1)] : 0;
+    st.head += cnt;
+    __syncwarp();
+    return cnt;
+}
+
+// The occupied samples with index in [first, end), in order, into buf (at most 32 are kept).
+__device__ __forceinline__ int scan_range(const GridView &g, const RaySetup &rs, const RenderParams &p, int first,
+                                          int end, int *buf, int lane) {
+    const unsigned lt = (1u << lane) - 1u;
+    int cnt = 0;
+    for (int base = first; base < end; base += 32 * kCand) {
+        Cand c[kCand];
+#pragma unroll
+        for (int j = 0; j < kCand; ++j) {
+            const int s = base + 32 * j + lane;
+            if (s < end) {
+                c[j] = test_candidate(g, rs, p, s);
+            } else {
+                c[j].valid = c[j].occ = false;
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < kCand; ++j) {
+            const unsigned m = __ballot_sync(kFull, c[j].occ);
+            const int pos = cnt + __popc(m & lt);
+            if (c[j].occ && pos < 32) buf[pos] = base + 32 * j + lane;
+            cnt += __popc(m);
+        }
+    }
+    __syncwarp();
+    return cnt;
+}
+
+// --------------------------------------------------------------------------- adjoint of one sample
+// Gradients of one taken sample with positive density with respect to its
+// interpolated values (the adjoint of Eq. 1 with SH colour and ReLUs), scattered
+// to the cell's 8 corners with their trilinear weights (NULL corners skip):
+//   dL/dsigma = delta sum_ch g_ch (T_{s+1} c_ch - R_ch),   R = colour after the sample,
+//   dL/dk_{ch,l} = g_ch w [pre_ch > 0] Y_l.
+// Rows are accumulated with float4 atomics and marked in the touched mask.
+__device__ __forceinline__ void scatter_sample(const GridView &g, const int32_t rr[8], const float ff[3],
+                                               const float Y[9], const float gr[3], const float pre[3],
+                                               const float col[3], float w, float Tn, const float Rs[3],
+                                               float delta, float *__restrict__ grad_rows) {
+    float gsig = 0.0f;
+#pragma unroll
+    for (int ch = 0; ch < 3; ++ch) gsig = fmaf(gr[ch], Tn * col[ch] - Rs[ch], gsig);
+    gsig *= delta;
+    float gpre[3];
+#pragma unroll
+    for (int ch = 0; ch < 3; ++ch) gpre[ch] = pre[ch] > 0.0f ? gr[ch] * w : 0.0f;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+        if (rr[k] < 0) continue;
+        const float wk = corner_weight(ff, k);
+        if (wk == 0.0f) continue;
+        float v[kNV];
+        v[0] = wk * gsig;
+#pragma unroll
+        for (int ch = 0; ch < 3; ++ch) {
+            const float gw = wk * gpre[ch];
+#pragma unroll
+            for (int l = 0; l < 9; ++l) v[1 + 9 * ch + l] = gw * Y[l];
+        }
+        float4 *dst = reinterpret_cast<float4 *>(grad_rows + (int64_t)rr[k] * kRowF);
+#pragma unroll
+        for (int q = 0; q < 7; ++q) atomicAdd(dst + q, make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]));
+        mark_touched(g, rr[k]);
+    }
+}
+
+}  // namespace plx

@@ -16,33 +16,18 @@
 // formed per chunk by a warp prefix product (relative error grows like the
 // square root of the sample count, independent of the optical depth).  The
 // ray parameter and sample coordinates are double-floats (see DF).
-#include "plx_internal.cuh"
+#include <cstring>
+
+#include "plx_march.cuh"
 
 namespace plx {
 
 // --------------------------------------------------------------------------- rays
-__global__ void gen_rays_kernel(const float *__restrict__ cams, int n_cams, int W, int H,
-                                const int64_t *__restrict__ pix, int64_t n, float *__restrict__ o,
-                                float *__restrict__ d) {
-    int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (r >= n) return;
-    int64_t p = pix[r];
-    int64_t hw = (int64_t)W * H;
-    if (p < 0 || p >= hw * n_cams) {
-#pragma unroll
-        for (int i = 0; i < 3; ++i) {
-            o[3 * r + i] = 0.0f;
-            d[3 * r + i] = 0.0f;
-        }
-        return;
-    }
-    int64_t view = p / hw;
-    int64_t rem = p - view * hw;
-    int v = (int)(rem / W);
-    int u = (int)(rem - (int64_t)v * W);
-    const float *c = cams + 18 * view;
-    // double-float throughout, then one rounding: the result is the FP32 rounding of the
-    // exact ray (up to inputs within ~1e-14 of a rounding midpoint)
+// The pixel-centre ray of pixel (u, v) of camera c (float [18]: c2w 3x4, fx, fy, cx, cy, W, H),
+// camera looking down -z with y up: d = normalize(R ((u + 1/2 - cx)/fx, -(v + 1/2 - cy)/fy, -1)),
+// o = the camera centre.  Double-float throughout, then one rounding: d is the FP32 rounding of
+// the exact direction (up to inputs within ~1e-14 of a rounding midpoint).
+__device__ __forceinline__ void pixel_ray(const float *__restrict__ c, int u, int v, float o[3], float d[3]) {
     const DF dc0 = df_div(df_two_sum((float)u + 0.5f, -c[14]), c[12]);
     DF dc1 = df_div(df_two_sum((float)v + 0.5f, -c[15]), c[13]);
     dc1.hi = -dc1.hi;
@@ -58,8 +43,30 @@ __global__ void gen_rays_kernel(const float *__restrict__ cams, int n_cams, int 
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
         const DF q = df_div_df(dw[i], len);
-        d[3 * r + i] = q.hi + q.lo;
-        o[3 * r + i] = c[4 * i + 3];
+        d[i] = q.hi + q.lo;
+        o[i] = c[4 * i + 3];
+    }
+}
+
+__global__ void gen_rays_kernel(const float *__restrict__ cams, int n_cams, int W, int H,
+                                const int64_t *__restrict__ pix, int64_t n, float *__restrict__ o,
+                                float *__restrict__ d) {
+    int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= n) return;
+    int64_t p = pix[r];
+    int64_t hw = (int64_t)W * H;
+    float oo[3] = {0.0f, 0.0f, 0.0f}, dd[3] = {0.0f, 0.0f, 0.0f};
+    if (p >= 0 && p < hw * n_cams) {
+        const int64_t view = p / hw;
+        const int64_t rem = p - view * hw;
+        const int v = (int)(rem / W);
+        const int u = (int)(rem - (int64_t)v * W);
+        pixel_ray(cams + 18 * view, u, v, oo, dd);
+    }
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        o[3 * r + i] = oo[i];
+        d[3 * r + i] = dd[i];
     }
 }
 
@@ -97,346 +104,18 @@ cudaError_t launch_mse_grad(const float *rgb, const float *target, int64_t n, fl
     return cudaGetLastError();
 }
 
-// --------------------------------------------------------------------------- per-ray setup
-struct RaySetup {
-    DF A[3];       // origin minus box corner, exact as a double-float
-    float d[3];    // unit direction as given
-    DF tn, tf;     // clipped parameter range
-    float og[3];   // FP32 grid-coordinate origin and direction, for the cheap candidate test
-    float dg[3];
-    float Y[9];    // SH basis at the direction
-    bool hit;
-};
-
-__device__ __forceinline__ RaySetup ray_setup(const GridView &g, const float *__restrict__ ro,
-                                              const float *__restrict__ rd, int64_t ray) {
-    RaySetup rs;
-    float o[3];
-#pragma unroll
-    for (int a = 0; a < 3; ++a) {
-        o[a] = __ldg(ro + 3 * ray + a);
-        rs.d[a] = __ldg(rd + 3 * ray + a);
-    }
-    rs.hit = clip_box(g, o, rs.d, rs.tn, rs.tf);
-#pragma unroll
-    for (int a = 0; a < 3; ++a) {
-        rs.A[a] = df_two_sum(o[a], -g.lo[a]);
-        rs.og[a] = (o[a] - g.lo[a]) * g.inv_h[a];
-        rs.dg[a] = rs.d[a] * g.inv_h[a];
-    }
-    sh_basis(rs.d, rs.Y);
-    return rs;
-}
-
-// t_s = t_near + s * delta as a double-float (s * delta_hi is exact for s < 2^24).
-__device__ __forceinline__ DF sample_t(const RaySetup &rs, const RenderParams &p, int s) {
-    DF sd = df_two_prod((float)s, p.delta);
-    sd.lo = fmaf((float)s, p.delta_lo, sd.lo);
-    return df_add(rs.tn, sd);
-}
-
-// Grid coordinates of the point at parameter t: ((o - lo) + t d) / h per axis.
-__device__ __forceinline__ void sample_coords(const GridView &g, const RaySetup &rs, DF t, DF gc[3]) {
-#pragma unroll
-    for (int a = 0; a < 3; ++a) {
-        DF td = df_two_prod(t.hi, rs.d[a]);
-        td.lo = fmaf(t.lo, rs.d[a], td.lo);
-        gc[a] = df_mul(df_add(rs.A[a], td), DF{g.inv_h[a], g.inv_h_lo[a]});
-    }
-}
-
-// Read-only vector loads issued as volatile asm: the compiler keeps them in
-// program order ahead of their uses instead of sinking each next to its FMAs.
-__device__ __forceinline__ float4 ldg4_pinned(const float4 *p) {
-    float4 v;
-    asm volatile("ld.global.nc.v4.f32 {%0, %1, %2, %3}, [%4];" : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w) : "l"(p));
-    return v;
-}
-__device__ __forceinline__ uint4 ldg4_pinned(const uint4 *p) {
-    uint4 v;
-    asm volatile("ld.global.nc.v4.u32 {%0, %1, %2, %3}, [%4];" : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w) : "l"(p));
-    return v;
-}
-
-// Full sample: interpolated values at grid point gc, whose cell the caller has
-// already found occupied (compaction).  rows_out/f_out receive the corners.
-__device__ __forceinline__ bool gather_sample(const GridView &g, int form, const DF gc[3], float acc[kNV],
-                                              int32_t rows_out[8], float f_out[3]) {
-#pragma unroll
-    for (int q = 0; q < kNV; ++q) acc[q] = 0.0f;
-    Cell c = locate(g, gc);
-    f_out[0] = c.f[0];
-    f_out[1] = c.f[1];
-    f_out[2] = c.f[2];
-    int32_t r[8];
-#pragma unroll
-    for (int k = 0; k < 8; ++k) r[k] = row_of(g, corner_node(g, c.base, k));
-    // every corner's row is requested before any is used: one memory round trip per
-    // chunk instead of eight (a NULL corner contributes w * 0, i.e. nothing)
-    if (form == PLX_SH_F32) {
-        float4 v[8][7];
-#pragma unroll
-        for (int k = 0; k < 8; ++k) {
-            const float4 *p = reinterpret_cast<const float4 *>(g.rows + (int64_t)max(r[k], 0) * kRowF);
-#pragma unroll
-            for (int q = 0; q < 7; ++q) v[k][q] = r[k] >= 0 ? ldg4_pinned(p + q) : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
-        }
-        // an empty volatile use of every loaded value, after all the loads: no FMA can be
-        // scheduled between two loads, so all 56 requests are in flight together
-#pragma unroll
-        for (int k = 0; k < 8; ++k)
-#pragma unroll
-            for (int q = 0; q < 7; ++q)
-                asm volatile("" : "+f"(v[k][q].x), "+f"(v[k][q].y), "+f"(v[k][q].z), "+f"(v[k][q].w));
-#pragma unroll
-        for (int k = 0; k < 8; ++k) {
-            const float w = corner_weight(c.f, k);
-#pragma unroll
-            for (int q = 0; q < 7; ++q) {
-                acc[4 * q + 0] = fmaf(w, v[k][q].x, acc[4 * q + 0]);
-                acc[4 * q + 1] = fmaf(w, v[k][q].y, acc[4 * q + 1]);
-                acc[4 * q + 2] = fmaf(w, v[k][q].z, acc[4 * q + 2]);
-                acc[4 * q + 3] = fmaf(w, v[k][q].w, acc[4 * q + 3]);
-            }
-        }
-    } else {
-        uint4 v[8][4];
-#pragma unroll
-        for (int k = 0; k < 8; ++k) {
-            const uint4 *p = reinterpret_cast<const uint4 *>(g.rows_h + (int64_t)max(r[k], 0) * kRowH);
-#pragma unroll
-            for (int q = 0; q < 4; ++q) v[k][q] = r[k] >= 0 ? ldg4_pinned(p + q) : make_uint4(0u, 0u, 0u, 0u);
-        }
-#pragma unroll
-        for (int k = 0; k < 8; ++k)
-#pragma unroll
-            for (int q = 0; q < 4; ++q) asm volatile("" : "+r"(v[k][q].x), "+r"(v[k][q].y), "+r"(v[k][q].z), "+r"(v[k][q].w));
-#pragma unroll
-        for (int k = 0; k < 8; ++k) {
-            const float w = corner_weight(c.f, k);
-            const uint32_t wd[16] = {v[k][0].x, v[k][0].y, v[k][0].z, v[k][0].w, v[k][1].x, v[k][1].y,
-                                     v[k][1].z, v[k][1].w, v[k][2].x, v[k][2].y, v[k][2].z, v[k][2].w,
-                                     v[k][3].x, v[k][3].y, v[k][3].z, v[k][3].w};
-            acc[0] = fmaf(w, __uint_as_float(wd[0]), acc[0]);
-#pragma unroll
-            for (int sh = 0; sh < 27; ++sh) {
-                const uint32_t word = wd[1 + (sh >> 1)];
-                const uint32_t bits = (sh & 1) ? (word & 0xffff0000u) : (word << 16);
-                acc[1 + sh] = fmaf(w, __uint_as_float(bits), acc[1 + sh]);
-            }
-        }
-    }
-#pragma unroll
-    for (int k = 0; k < 8; ++k) rows_out[k] = r[k];
-    return true;
-}
-
-// Density only (backward pass 1 and node counting).  The caller has already
-// found the sample's cell occupied (compaction), so the mask is not re-read.
-__device__ __forceinline__ float gather_sigma(const GridView &g, int form, const DF gc[3]) {
-    Cell c = locate(g, gc);
-    int32_t r[8];
-#pragma unroll
-    for (int k = 0; k < 8; ++k) r[k] = row_of(g, corner_node(g, c.base, k));
-    float s = 0.0f;
-#pragma unroll
-    for (int k = 0; k < 8; ++k)
-        if (r[k] >= 0) s = fmaf(corner_weight(c.f, k), row_sigma(g, form, r[k]), s);
-    return s;
-}
-
-__device__ __forceinline__ void colour_of(const float acc[kNV], const float Y[9], float pre[3], float c[3]) {
-#pragma unroll
-    for (int ch = 0; ch < 3; ++ch) {
-        float p = 0.0f;
-#pragma unroll
-        for (int l = 0; l < 9; ++l) p = fmaf(Y[l], acc[1 + 9 * ch + l], p);
-        pre[ch] = p;
-        c[ch] = fmaxf(p, 0.0f);
-    }
-}
-
-// Warp inclusive prefix product (lane order).
-__device__ __forceinline__ float warp_incl_prod(float x, int lane) {
-#pragma unroll
-    for (int off = 1; off < 32; off <<= 1) {
-        const float v = __shfl_up_sync(kFull, x, off);
-        if (lane >= off) x *= v;
-    }
-    return x;
-}
-
-// Per-chunk compositing state shared by the kernels: given this lane's
-// density, returns alpha, T_s (before the sample), T_{s+1} and whether the
-// sample is taken (valid and T_s >= stop); Tc is the transmittance before
-// the chunk.  Transmittance is the running product of exp(-sigma delta).
-struct Composite {
-    float alpha, T, Tn;
-    bool take;
-    unsigned tmask;
-    float chunk_prod;  // product over the taken lanes, to advance Tc
-};
-
-__device__ __forceinline__ Composite composite(float sig, bool valid, float Tc, const RenderParams &p, int lane) {
-    Composite r;
-    r.alpha = -expm1f(-sig * p.delta);
-    const float e = 1.0f - r.alpha;
-    const float incl = warp_incl_prod(e, lane);
-    float excl = __shfl_up_sync(kFull, incl, 1);
-    if (lane == 0) excl = 1.0f;
-    r.T = Tc * excl;
-    r.Tn = Tc * incl;
-    r.take = valid && r.T >= p.stop;
-    r.tmask = __ballot_sync(kFull, r.take);
-    const int k = __popc(r.tmask);
-    r.chunk_prod = k > 0 ? __shfl_sync(kFull, incl, k - 1) : 1.0f;
-    return r;
-}
-
-// --------------------------------------------------------------------------- sample compaction
-// The candidates (all samples of the ray, in order) are tested against the
-// cell occupancy mask, kCand per lane at a time so that many mask loads are in
-// flight; samples whose cell has an occupied corner are appended, in order, to
-// a per-warp ring buffer in shared memory and processed 32 at a time.  A
-// skipped sample lies in a cell whose 8 corners are NULL (all values zero):
-// its alpha is exactly 0, it multiplies T by exactly 1 and adds nothing, so
-// the compacted march evaluates the same sum.
-constexpr int kCand = 8;    // candidates per lane per refill
-constexpr int kRing = 512;  // ring capacity >= 31 + 32 kCand, a power of two
-
-struct Cand {
-    bool valid, occ;
-};
-
-// Is sample s inside the clipped ray (valid), and is its cell non-empty (occ)?
-// The answer must equal the double-float one exactly (it decides which samples
-// are marched).  Plain FP32 coordinates are within ~3e-4 of a cell of the
-// double-float ones (rounding of t_near, delta, the direction and the grid
-// scale, for R <= 2048); a candidate whose FP32 coordinate lies within kFaceEps
-// of a cell face on any axis, or whose t lies within kTEps of t_far, is
-// re-evaluated in double-float, so the cheap path is taken only where both agree.
-constexpr float kFaceEps = 2e-3f;
-
-__device__ __forceinline__ Cand test_candidate(const GridView &g, const RaySetup &rs, const RenderParams &p, int s) {
-    Cand c;
-    c.occ = false;
-    c.valid = false;
-    if (s >= p.max_chunks * 32) return c;
-    const float t32 = fmaf((float)s, p.delta, rs.tn.hi);
-    const float kTEps = 1e-5f * (fabsf(rs.tf.hi) + 1.0f);
-    bool exact = fabsf(t32 - rs.tf.hi) <= kTEps;
-    if (!exact && t32 > rs.tf.hi) return c;  // clearly past t_far
-    int b[3];
-    const float rm1 = (float)(g.R - 1);
-#pragma unroll
-    for (int a = 0; a < 3; ++a) {
-        const float x = fmaf(t32, rs.dg[a], rs.og[a]);
-        const float fl = floorf(x);
-        exact = exact || (x - fl) < kFaceEps || (fl + 1.0f - x) < kFaceEps || x < kFaceEps || x > rm1 - kFaceEps;
-        b[a] = (int)fl;
-    }
-    if (exact) {
-        const DF t = sample_t(rs, p, s);
-        c.valid = df_lt(t, rs.tf);
-        if (c.valid) {
-            DF gc[3];
-            sample_coords(g, rs, t, gc);
-            c.occ = cell_occupied(g, locate(g, gc).base);
-        }
-        return c;
-    }
-    c.valid = true;
-    c.occ = cell_occupied(g, ((int64_t)b[0] * g.R + b[1]) * g.R + b[2]);
-    return c;
-}
-
-struct Stream {
-    int next;   // next candidate sample index to test
-    int head;   // ring read position (absolute)
-    int tail;   // ring write position (absolute)
-    bool exhausted;
-};
-
-// Append occupied candidates until 32 are queued or the ray has no candidates left.
-__device__ __forceinline__ void refill(const GridView &g, const RaySetup &rs, const RenderParams &p, int *ring,
-                                       Stream &st, int lane) {
-    const unsigned lt = (1u << lane) - 1u;
-    while (st.tail - st.head < 32 && !st.exhausted) {
-        Cand c[kCand];
-#pragma unroll
-        for (int j = 0; j < kCand; ++j) c[j] = test_candidate(g, rs, p, st.next + 32 * j + lane);
-#pragma unroll
-        for (int j = 0; j < kCand; ++j) {
-            const unsigned m = __ballot_sync(kFull, c[j].occ);
-            if (c[j].occ) ring[(st.tail + __popc(m & lt)) & (kRing - 1)] = st.next + 32 * j + lane;
-            st.tail += __popc(m);
-        }
-        // valid candidates form a prefix of the sample indices
-        st.exhausted = __ballot_sync(kFull, c[kCand - 1].valid) != kFull;
-        st.next += 32 * kCand;
-    }
-    __syncwarp();
-}
-
-// Take the next (up to) 32 queued samples: returns the count; lane i gets sample s (if i < count).
-__device__ __forceinline__ int take_chunk(const int *ring, Stream &st, int lane, int &s) {
-    const int cnt = min(st.tail - st.head, 32);
-    s = lane < cnt ? ring[(st.head + lane) & (kRing - 1)] : 0;
-    st.head += cnt;
-    __syncwarp();
-    return cnt;
-}
-
-// The occupied samples with index in [first, end), in order, into buf (at most 32 are kept).
-__device__ __forceinline__ int scan_range(const GridView &g, const RaySetup &rs, const RenderParams &p, int first,
-                                          int end, int *buf, int lane) {
-    const unsigned lt = (1u << lane) - 1u;
-    int cnt = 0;
-    for (int base = first; base < end; base += 32 * kCand) {
-        Cand c[kCand];
-#pragma unroll
-        for (int j = 0; j < kCand; ++j) {
-            const int s = base + 32 * j + lane;
-            if (s < end) {
-                c[j] = test_candidate(g, rs, p, s);
-            } else {
-                c[j].valid = c[j].occ = false;
-            }
-        }
-#pragma unroll
-        for (int j = 0; j < kCand; ++j) {
-            const unsigned m = __ballot_sync(kFull, c[j].occ);
-            const int pos = cnt + __popc(m & lt);
-            if (c[j].occ && pos < 32) buf[pos] = base + 32 * j + lane;
-            cnt += __popc(m);
-        }
-    }
-    __syncwarp();
-    return cnt;
-}
-
 // --------------------------------------------------------------------------- forward
-// Four resident 4-warp CTAs per SM: up to 128 registers a thread, enough for the
-// gather to keep most of a chunk's row loads in flight (measured on the 512^3
-// training batch against 2 and 3 CTAs, which buy more registers but fewer warps).
-constexpr int kGatherBlocks = 4;
 constexpr int kFwdWarps = 4;
 
+// The forward march of one ray by one warp (Eq. 1 over the compacted samples, chunk by chunk):
+// returns, in every lane, the composited colour without the background and the final
+// transmittance.  ring: this warp's kRing ints of shared memory.
 template <int FORM>
-__global__ void __launch_bounds__(kFwdWarps * 32, kGatherBlocks) render_fwd_kernel(GridView g, const float *__restrict__ ro,
-                                                                    const float *__restrict__ rd, int64_t n,
-                                                                    RenderParams p, float *__restrict__ rgb,
-                                                                    float *__restrict__ T_out) {
-    __shared__ int s_ring[kFwdWarps][kRing];
-    const int lane = threadIdx.x & 31;
-    const int wid = threadIdx.x >> 5;
-    const int64_t ray = (int64_t)blockIdx.x * kFwdWarps + wid;
-    if (ray >= n) return;  // uniform per warp
-    const RaySetup rs = ray_setup(g, ro, rd, ray);
-    float C[3] = {0.0f, 0.0f, 0.0f};
-    float Tc = 1.0f;  // transmittance before the current chunk
+__device__ __forceinline__ void march_forward(const GridView &g, const RenderParams &p, const RaySetup &rs, int *ring,
+                                              int lane, float C[3], float &Tc) {
+    C[0] = C[1] = C[2] = 0.0f;
+    Tc = 1.0f;  // transmittance before the current chunk
     if (rs.hit) {
-        int *ring = s_ring[wid];
         Stream st = {0, 0, 0, false};
         for (;;) {
             refill(g, rs, p, ring, st, lane);
@@ -471,6 +150,21 @@ __global__ void __launch_bounds__(kFwdWarps * 32, kGatherBlocks) render_fwd_kern
     C[0] = warp_sum(C[0]);
     C[1] = warp_sum(C[1]);
     C[2] = warp_sum(C[2]);
+}
+
+template <int FORM>
+__global__ void __launch_bounds__(kFwdWarps * 32, kGatherBlocks) render_fwd_kernel(GridView g, const float *__restrict__ ro,
+                                                                    const float *__restrict__ rd, int64_t n,
+                                                                    RenderParams p, float *__restrict__ rgb,
+                                                                    float *__restrict__ T_out) {
+    __shared__ int s_ring[kFwdWarps][kRing];
+    const int lane = threadIdx.x & 31;
+    const int wid = threadIdx.x >> 5;
+    const int64_t ray = (int64_t)blockIdx.x * kFwdWarps + wid;
+    if (ray >= n) return;  // uniform per warp
+    const RaySetup rs = ray_setup(g, ro, rd, ray);
+    float C[3], Tc;
+    march_forward<FORM>(g, p, rs, s_ring[wid], lane, C, Tc);
     if (lane == 0) {
         rgb[3 * ray + 0] = fmaf(Tc, p.bg[0], C[0]);
         rgb[3 * ray + 1] = fmaf(Tc, p.bg[1], C[1]);
@@ -487,6 +181,70 @@ cudaError_t launch_render(const GridView &g, const float *o, const float *d, int
         render_fwd_kernel<PLX_SH_F32><<<(unsigned)blocks, kFwdWarps * 32, 0, s>>>(g, o, d, n, p, rgb, T_end);
     else
         render_fwd_kernel<PLX_SH_BF16><<<(unsigned)blocks, kFwdWarps * 32, 0, s>>>(g, o, d, n, p, rgb, T_end);
+    return cudaGetLastError();
+}
+
+// --------------------------------------------------------------------------- serving
+// plx_render_tiles: image requests of several resident scenes in one launch.
+// Each tile is 16x16 pixels of one request; warp w renders pixel (w mod 256)
+// of tile w / 256, generating its ray in-kernel with the same code as
+// plx_gen_rays and marching it with the same code as plx_render, so a pixel's
+// value does not depend on what else is in the launch.
+struct SceneTable {
+    GridView g[PLX_TILES_MAX_SCENES];
+    RenderParams p[PLX_TILES_MAX_SCENES];
+};
+
+template <int FORM>
+__global__ void __launch_bounds__(kFwdWarps * 32, kGatherBlocks) render_tiles_kernel(
+    const __grid_constant__ SceneTable tab, int n_scenes, const float *__restrict__ cams, int n_cams,
+    const plx_tile *__restrict__ tiles, int64_t n_rays) {
+    __shared__ int s_ring[kFwdWarps][kRing];
+    const int lane = threadIdx.x & 31;
+    const int wid = threadIdx.x >> 5;
+    const int64_t ray = (int64_t)blockIdx.x * kFwdWarps + wid;
+    if (ray >= n_rays) return;  // uniform per warp
+    const plx_tile tile = tiles[ray / (PLX_TILE_W * PLX_TILE_H)];
+    const int px = (int)(ray % (PLX_TILE_W * PLX_TILE_H));
+    const int x = tile.x0 + px % PLX_TILE_W;
+    const int y = tile.y0 + px / PLX_TILE_W;
+    if (x < 0 || y < 0 || x >= tile.W || y >= tile.H) return;  // a tile over the image's edge
+    if (tile.scene < 0 || tile.scene >= n_scenes || tile.camera < 0 || tile.camera >= n_cams || !tile.d_rgb) {
+        if (lane == 0) report(tab.g[0].status, kDevBadTile);
+        return;
+    }
+    const GridView &g = tab.g[tile.scene];
+    const RenderParams &p = tab.p[tile.scene];
+    float o[3], d[3];
+    pixel_ray(cams + 18 * (int64_t)tile.camera, x, y, o, d);
+    const RaySetup rs = ray_setup_od(g, o, d);
+    float C[3], Tc;
+    march_forward<FORM>(g, p, rs, s_ring[wid], lane, C, Tc);
+    if (lane == 0) {
+        float *out = tile.d_rgb + ((int64_t)y * tile.W + x) * 3;
+        out[0] = fmaf(Tc, p.bg[0], C[0]);
+        out[1] = fmaf(Tc, p.bg[1], C[1]);
+        out[2] = fmaf(Tc, p.bg[2], C[2]);
+    }
+}
+
+cudaError_t launch_render_tiles(const GridView *g, const RenderParams *p, int n_scenes, const float *cams,
+                                int n_cams, const plx_tile *tiles, int64_t n_tiles, cudaStream_t s) {
+    if (n_tiles == 0) return cudaSuccess;
+    SceneTable tab;
+    memset(&tab, 0, sizeof(tab));
+    for (int i = 0; i < n_scenes; ++i) {
+        tab.g[i] = g[i];
+        tab.p[i] = p[i];
+    }
+    const int64_t n_rays = n_tiles * PLX_TILE_W * PLX_TILE_H;
+    const int64_t blocks = n_rays / kFwdWarps;
+    if (g[0].form == PLX_SH_F32)
+        render_tiles_kernel<PLX_SH_F32><<<(unsigned)blocks, kFwdWarps * 32, 0, s>>>(tab, n_scenes, cams, n_cams, tiles,
+                                                                                     n_rays);
+    else
+        render_tiles_kernel<PLX_SH_BF16><<<(unsigned)blocks, kFwdWarps * 32, 0, s>>>(tab, n_scenes, cams, n_cams, tiles,
+                                                                                      n_rays);
     return cudaGetLastError();
 }
 
@@ -596,36 +354,8 @@ __global__ void __launch_bounds__(kBwdWarps * 32, kGatherBlocks) render_bwd_kern
             Rs[ch] = Rsuf[ch] + suf_ex;
             Rsuf[ch] += __shfl_sync(kFull, suf, 0);
         }
-        if (take && occupied && sig > 0.0f) {
-            // per-sample gradients w.r.t. the interpolated values
-            float gsig = 0.0f;
-#pragma unroll
-            for (int ch = 0; ch < 3; ++ch) gsig = fmaf(gr[ch], cp.Tn * col[ch] - Rs[ch], gsig);
-            gsig *= p.delta;
-            float gpre[3];
-#pragma unroll
-            for (int ch = 0; ch < 3; ++ch) gpre[ch] = pre[ch] > 0.0f ? gr[ch] * w : 0.0f;
-            // scatter to corners
-#pragma unroll
-            for (int k = 0; k < 8; ++k) {
-                if (rr[k] < 0) continue;
-                const float wk = corner_weight(ff, k);
-                if (wk == 0.0f) continue;
-                float v[kNV];
-                v[0] = wk * gsig;
-#pragma unroll
-                for (int ch = 0; ch < 3; ++ch) {
-                    const float gw = wk * gpre[ch];
-#pragma unroll
-                    for (int l = 0; l < 9; ++l) v[1 + 9 * ch + l] = gw * rs.Y[l];
-                }
-                float4 *dst = reinterpret_cast<float4 *>(grad_rows + (int64_t)rr[k] * kRowF);
-#pragma unroll
-                for (int q = 0; q < 7; ++q)
-                    atomicAdd(dst + q, make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]));
-                mark_touched(g, rr[k]);
-            }
-        }
+        if (take && occupied && sig > 0.0f)
+            scatter_sample(g, rr, ff, rs.Y, gr, pre, col, w, cp.Tn, Rs, p.delta, grad_rows);
     }
 }
 

@@ -1,0 +1,327 @@
+// plx_train.cu -- the chunk-parallel march of the optimisation step (Eq. 1 and
+// its adjoint for a batch of training rays, Sec. 3.4 / Supp. A.1).
+//
+// Why a second march: a 5000-ray batch is about two waves of one-warp-per-ray
+// work on a 152-SM part, and a ray through the dense shell and blobs carries
+// 10-20x the average number of non-empty samples.  With a warp per ray those
+// rays set the kernel time while most SMs idle.  Here every chunk of 32
+// compacted samples of every ray is one work item of equal cost:
+//
+//   plan     (warp per ray)    compacts the ray's samples against the
+//                              occupancy mask, records where each chunk of 32
+//                              starts, and appends its (ray, chunk) items;
+//   chunks   (one resident wave, warps stride over the items)
+//                              gathers a chunk and composites it from T = 1:
+//                              local colour C_loc and transmittance product P;
+//   combine  (warp per ray)    T_before(k) = prod_{j<k} P_j, C = sum_k
+//                              T_before(k) C_loc(k) + T_end bg, and, for the
+//                              adjoint, R_after(k) = sum_{j>k} T_before(j)
+//                              C_loc(j) + T_end bg (a suffix sum of
+//                              non-negative terms: no cancellation);
+//   adjoint  (one resident wave over the same items)
+//                              recomputes a chunk's samples with T_s =
+//                              T_before(k) x (in-chunk prefix) and R_s =
+//                              R_after(k) + (in-chunk suffix), and scatters.
+//
+// The state between the calls lives in a caller buffer (MarchLayout).  The
+// results equal plx_render / plx_render_backward up to FP32 summation order.
+// Early termination (stop_thresh > 0) needs the global transmittance inside a
+// chunk, so with stop_thresh > 0 the pair falls back to the one-warp-per-ray
+// kernels, recorded in the state's mode.
+#include <algorithm>
+#include <mutex>
+
+#include "plx_march.cuh"
+
+namespace plx {
+
+namespace {
+
+constexpr int kPlanWarps = 4;
+constexpr int kChunkWarps = 4;
+constexpr int kCombineWarps = 8;
+
+int sm_count() {
+    static std::mutex mu;
+    static int cache[64] = {};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 152;
+    std::lock_guard<std::mutex> lock(mu);
+    if (cache[dev] == 0) {
+        int v = 0;
+        if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || v <= 0) v = 152;
+        cache[dev] = v;
+    }
+    return cache[dev];
+}
+
+__global__ void march_header_kernel(MarchHeader *dst, MarchHeader v) { *dst = v; }
+
+// ---------------------------------------------------------------------------- plan
+__global__ void __launch_bounds__(kPlanWarps * 32) march_plan_kernel(GridView g, const float *__restrict__ ro,
+                                                                     const float *__restrict__ rd, int64_t n,
+                                                                     RenderParams p, MarchPtrs st) {
+    const int lane = threadIdx.x & 31;
+    const int64_t ray = (int64_t)blockIdx.x * kPlanWarps + (threadIdx.x >> 5);
+    if (ray >= n) return;  // uniform per warp
+    const RaySetup rs = ray_setup(g, ro, rd, ray);
+    const int mc = st.max_chunks;
+    int32_t *first = st.first + ray * (mc + 1);
+    const unsigned lt = (1u << lane) - 1u;
+    int n_occ = 0, last = -1;
+    if (rs.hit) {
+        // test_candidate admits at most max_chunks * 32 samples, so rank / 32 < max_chunks
+        for (int next = 0;; next += 32 * kCand) {
+            Cand c[kCand];
+#pragma unroll
+            for (int j = 0; j < kCand; ++j) c[j] = test_candidate(g, rs, p, next + 32 * j + lane);
+#pragma unroll
+            for (int j = 0; j < kCand; ++j) {
+                const unsigned m = __ballot_sync(kFull, c[j].occ);
+                if (c[j].occ) {
+                    const int rank = n_occ + __popc(m & lt);
+                    if ((rank & 31) == 0) first[rank >> 5] = next + 32 * j + lane;
+                }
+                if (m) last = next + 32 * j + 31 - __clz((int)m);
+                n_occ += __popc(m);
+            }
+            // valid candidates form a prefix of the sample indices
+            if (__ballot_sync(kFull, c[kCand - 1].valid) != kFull) break;
+        }
+    }
+    const int nch = (n_occ + 31) >> 5;
+    int base = 0;
+    if (lane == 0) {
+        first[nch] = last + 1;
+        st.n_occ[ray] = n_occ;
+        if (nch > 0) base = atomicAdd(&st.hdr->total_items, nch);
+    }
+    base = __shfl_sync(kFull, base, 0);
+    for (int k = lane; k < nch; k += 32) st.items[base + k] = make_int2((int)ray, k);
+}
+
+// The samples of item (ray, k): returns the count (lane i gets sample s if i < count), or -1 when
+// the rescan disagrees with the plan (reported; cannot happen for a deterministic occupancy test).
+__device__ __forceinline__ int item_samples(const GridView &g, const RaySetup &rs, const RenderParams &p,
+                                            const MarchPtrs &st, int64_t ray, int k, int *buf, int lane, int &s) {
+    const int32_t *first = st.first + ray * (st.max_chunks + 1);
+    const int expect = min(32, st.n_occ[ray] - 32 * k);
+    const int cnt = scan_range(g, rs, p, first[k], first[k + 1], buf, lane);
+    s = lane < cnt ? buf[lane] : 0;
+    __syncwarp();
+    if (cnt != expect) {
+        if (lane == 0) report(g.status, kDevCountMismatch);
+        return -1;
+    }
+    return cnt;
+}
+
+// ---------------------------------------------------------------------------- chunks (forward)
+template <int FORM>
+__global__ void __launch_bounds__(kChunkWarps * 32, kGatherBlocks) march_chunks_fwd_kernel(
+    GridView g, const float *__restrict__ ro, const float *__restrict__ rd, RenderParams p, MarchPtrs st) {
+    __shared__ int s_buf[kChunkWarps][32];
+    const int lane = threadIdx.x & 31;
+    const int wid = threadIdx.x >> 5;
+    const int total = st.hdr->total_items;
+    const int stride = gridDim.x * kChunkWarps;
+    const int mc = st.max_chunks;
+    for (int it = blockIdx.x * kChunkWarps + wid; it < total; it += stride) {
+        const int2 item = st.items[it];
+        const int64_t ray = item.x;
+        const int k = item.y;
+        const RaySetup rs = ray_setup(g, ro, rd, ray);
+        int s;
+        const int cnt = item_samples(g, rs, p, st, ray, k, s_buf[wid], lane, s);
+        if (cnt < 0) continue;
+        const bool valid = lane < cnt;
+        float sig = 0.0f, col[3] = {0.0f, 0.0f, 0.0f};
+        if (valid) {
+            DF gc[3];
+            sample_coords(g, rs, sample_t(rs, p, s), gc);
+            float acc[kNV];
+            int32_t rr[8];
+            float ff[3];
+            gather_sample(g, FORM, gc, acc, rr, ff);
+            sig = fmaxf(acc[0], 0.0f);
+            float pre[3];
+            colour_of(acc, rs.Y, pre, col);
+        }
+        const Composite cp = composite(sig, valid, 1.0f, p, lane);  // stop_thresh is 0 on this path
+        const float w = cp.take ? cp.T * cp.alpha : 0.0f;
+        const float c0 = warp_sum(w * col[0]);
+        const float c1 = warp_sum(w * col[1]);
+        const float c2 = warp_sum(w * col[2]);
+        const unsigned live = __ballot_sync(kFull, valid && sig > 0.0f);
+        if (lane == 0) {
+            st.part[ray * mc + k] = make_float4(c0, c1, c2, cp.chunk_prod);
+            st.live[ray * mc + k] = live ? 1 : 0;
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------- combine
+__global__ void __launch_bounds__(kCombineWarps * 32) march_combine_kernel(int64_t n, RenderParams p, MarchPtrs st,
+                                                                           float *__restrict__ rgb,
+                                                                           float *__restrict__ T_out) {
+    const int lane = threadIdx.x & 31;
+    const int64_t ray = (int64_t)blockIdx.x * kCombineWarps + (threadIdx.x >> 5);
+    if (ray >= n) return;
+    const int mc = st.max_chunks;
+    const int nch = (st.n_occ[ray] + 31) >> 5;
+    float4 *part = st.part + ray * mc;
+    // forward over chunks: T_before and the colour
+    float Tc = 1.0f;
+    float C[3] = {0.0f, 0.0f, 0.0f};
+    for (int b = 0; b < nch; b += 32) {
+        const int k = b + lane;
+        const bool valid = k < nch;
+        const float4 q = valid ? part[k] : make_float4(0.0f, 0.0f, 0.0f, 1.0f);
+        const float incl = warp_incl_prod(q.w, lane);
+        float excl = __shfl_up_sync(kFull, incl, 1);
+        if (lane == 0) excl = 1.0f;
+        const float Tb = Tc * excl;
+        C[0] = fmaf(Tb, q.x, C[0]);
+        C[1] = fmaf(Tb, q.y, C[1]);
+        C[2] = fmaf(Tb, q.z, C[2]);
+        if (valid) part[k].w = Tb;
+        Tc *= __shfl_sync(kFull, incl, 31);
+    }
+    C[0] = warp_sum(C[0]);
+    C[1] = warp_sum(C[1]);
+    C[2] = warp_sum(C[2]);
+    if (lane == 0) {
+        rgb[3 * ray + 0] = fmaf(Tc, p.bg[0], C[0]);
+        rgb[3 * ray + 1] = fmaf(Tc, p.bg[1], C[1]);
+        rgb[3 * ray + 2] = fmaf(Tc, p.bg[2], C[2]);
+        if (T_out) T_out[ray] = Tc;
+    }
+    // reverse over chunks: the colour that arrives after each chunk
+    float Rs[3] = {Tc * p.bg[0], Tc * p.bg[1], Tc * p.bg[2]};
+    for (int b = nch > 0 ? ((nch - 1) >> 5) << 5 : -32; b >= 0; b -= 32) {
+        const int k = b + lane;
+        const bool valid = k < nch;
+        const float4 q = valid ? part[k] : make_float4(0.0f, 0.0f, 0.0f, 0.0f);  // (C_loc, T_before)
+        const float cl[3] = {q.x, q.y, q.z};
+        float Ra[3];
+#pragma unroll
+        for (int ch = 0; ch < 3; ++ch) {
+            const float suf = warp_incl_suffix(q.w * cl[ch], lane);
+            float suf_ex = __shfl_down_sync(kFull, suf, 1);
+            if (lane == 31) suf_ex = 0.0f;
+            Ra[ch] = Rs[ch] + suf_ex;
+            Rs[ch] += __shfl_sync(kFull, suf, 0);
+        }
+        if (valid) part[k] = make_float4(Ra[0], Ra[1], Ra[2], q.w);
+    }
+}
+
+// ---------------------------------------------------------------------------- adjoint
+__device__ __forceinline__ bool header_matches(const MarchHeader &h, const MarchHeader &e) {
+    return h.magic == kMarchMagic && h.mode == kMarchChunked && h.n == e.n && h.max_chunks == e.max_chunks &&
+           h.R == e.R && h.M == e.M && __float_as_uint(h.delta) == __float_as_uint(e.delta) &&
+           __float_as_uint(h.delta_lo) == __float_as_uint(e.delta_lo) &&
+           __float_as_uint(h.stop) == __float_as_uint(e.stop) && h.ro == e.ro && h.rd == e.rd &&
+           h.rows == e.rows && h.total_items >= 0 && (int64_t)h.total_items <= e.n * (int64_t)e.max_chunks;
+}
+
+template <int FORM>
+__global__ void __launch_bounds__(kChunkWarps * 32, kGatherBlocks) march_chunks_bwd_kernel(
+    GridView g, const float *__restrict__ ro, const float *__restrict__ rd, RenderParams p, MarchPtrs st,
+    MarchHeader expect, const float *__restrict__ grad_rgb, float *__restrict__ grad_rows) {
+    __shared__ int s_buf[kChunkWarps][32];
+    const int lane = threadIdx.x & 31;
+    const int wid = threadIdx.x >> 5;
+    const MarchHeader h = *st.hdr;
+    if (!header_matches(h, expect)) {  // uniform over the grid
+        if (threadIdx.x == 0 && blockIdx.x == 0) report(g.status, kDevStateMismatch);
+        return;
+    }
+    const int total = h.total_items;
+    const int stride = gridDim.x * kChunkWarps;
+    const int mc = st.max_chunks;
+    for (int it = blockIdx.x * kChunkWarps + wid; it < total; it += stride) {
+        const int2 item = st.items[it];
+        const int64_t ray = item.x;
+        const int k = item.y;
+        if (!st.live[ray * mc + k]) continue;  // no positive density: no gradient anywhere in the chunk
+        const RaySetup rs = ray_setup(g, ro, rd, ray);
+        int s;
+        const int cnt = item_samples(g, rs, p, st, ray, k, s_buf[wid], lane, s);
+        if (cnt < 0) continue;
+        const bool valid = lane < cnt;
+        int32_t rr[8];
+        float ff[3];
+        float sig = 0.0f, pre[3] = {0.0f, 0.0f, 0.0f}, col[3] = {0.0f, 0.0f, 0.0f};
+        if (valid) {
+            DF gc[3];
+            sample_coords(g, rs, sample_t(rs, p, s), gc);
+            float acc[kNV];
+            gather_sample(g, FORM, gc, acc, rr, ff);
+            sig = fmaxf(acc[0], 0.0f);
+            colour_of(acc, rs.Y, pre, col);
+        }
+        const float4 q = st.part[ray * mc + k];  // (R_after, T_before)
+        const Composite cp = composite(sig, valid, q.w, p, lane);
+        const float w = cp.take ? cp.T * cp.alpha : 0.0f;
+        const float Ra[3] = {q.x, q.y, q.z};
+        float Rs[3];
+#pragma unroll
+        for (int ch = 0; ch < 3; ++ch) {
+            const float suf = warp_incl_suffix(w * col[ch], lane);
+            float suf_ex = __shfl_down_sync(kFull, suf, 1);
+            if (lane == 31) suf_ex = 0.0f;
+            Rs[ch] = Ra[ch] + suf_ex;
+        }
+        if (cp.take && sig > 0.0f) {
+            const float gr[3] = {__ldg(grad_rgb + 3 * ray), __ldg(grad_rgb + 3 * ray + 1),
+                                 __ldg(grad_rgb + 3 * ray + 2)};
+            scatter_sample(g, rr, ff, rs.Y, gr, pre, col, w, cp.Tn, Rs, p.delta, grad_rows);
+        }
+    }
+}
+
+// One resident wave: kGatherBlocks CTAs per SM, but no more warps than items can exist.
+unsigned chunk_grid(int64_t n, int max_chunks) {
+    const int64_t slots = n * (int64_t)max_chunks;
+    const int64_t need = (slots + kChunkWarps - 1) / kChunkWarps;
+    const int64_t wave = (int64_t)sm_count() * kGatherBlocks;
+    return (unsigned)std::max<int64_t>(1, std::min(need, wave));
+}
+
+}  // namespace
+
+cudaError_t launch_render_train(const GridView &g, const float *o, const float *d, int64_t n, const RenderParams &p,
+                                const MarchPtrs &st, const MarchHeader &hdr, float *rgb, float *T_end,
+                                cudaStream_t s) {
+    march_header_kernel<<<1, 1, 0, s>>>(st.hdr, hdr);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    if (hdr.mode == kMarchRecompute) return launch_render(g, o, d, n, p, rgb, T_end, s);
+    if (n == 0) return cudaSuccess;
+    march_plan_kernel<<<(unsigned)((n + kPlanWarps - 1) / kPlanWarps), kPlanWarps * 32, 0, s>>>(g, o, d, n, p, st);
+    const unsigned grid = chunk_grid(n, st.max_chunks);
+    if (g.form == PLX_SH_F32)
+        march_chunks_fwd_kernel<PLX_SH_F32><<<grid, kChunkWarps * 32, 0, s>>>(g, o, d, p, st);
+    else
+        march_chunks_fwd_kernel<PLX_SH_BF16><<<grid, kChunkWarps * 32, 0, s>>>(g, o, d, p, st);
+    march_combine_kernel<<<(unsigned)((n + kCombineWarps - 1) / kCombineWarps), kCombineWarps * 32, 0, s>>>(
+        n, p, st, rgb, T_end);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_render_backward_train(const GridView &g, const float *o, const float *d, int64_t n,
+                                         const RenderParams &p, const MarchPtrs &st, const MarchHeader &hdr,
+                                         const float *grad_rgb, float *grad_rows, cudaStream_t s) {
+    if (hdr.mode == kMarchRecompute) return launch_render_backward(g, o, d, n, p, grad_rgb, grad_rows, s);
+    if (n == 0) return cudaSuccess;
+    const unsigned grid = chunk_grid(n, st.max_chunks);
+    if (g.form == PLX_SH_F32)
+        march_chunks_bwd_kernel<PLX_SH_F32><<<grid, kChunkWarps * 32, 0, s>>>(g, o, d, p, st, hdr, grad_rgb, grad_rows);
+    else
+        march_chunks_bwd_kernel<PLX_SH_BF16><<<grid, kChunkWarps * 32, 0, s>>>(g, o, d, p, st, hdr, grad_rgb,
+                                                                               grad_rows);
+    return cudaGetLastError();
+}
+
+}  // namespace plx

@@ -113,6 +113,26 @@ class Grid:
         rows_t = torch.from_numpy(pad_rows(np.asarray(rows28, np.float32))).to(device)
         return cls(reso, idx_t, rows_t, sh_form, aabb)
 
+    @classmethod
+    def render_only_bf16(cls, reso: int, idx: np.ndarray, rows28: np.ndarray, device="cuda",
+                         aabb=((-1.0, -1.0, -1.0), (1.0, 1.0, 1.0))) -> "Grid":
+        """A BF16-SH grid that keeps only its 64-byte rows on the device (serving): the F32 rows are
+        packed by plx_pack_bf16 and then released."""
+        full = cls.from_host(reso, idx, rows28, sh_form=L.PLX_SH_BF16, device=device, aabb=aabb)
+        g = cls(reso, full.idx, None, L.PLX_SH_BF16, aabb, rows_h=full.rows_h, n_rows=full.M)
+        full.close()
+        del full
+        return g
+
+    def device_bytes(self) -> int:
+        """Device memory this grid holds (index volume, rows, workspace)."""
+        n = self.idx.numel() * 4 + self.workspace.numel()
+        if self.rows is not None:
+            n += self.rows.numel() * 4
+        if self.rows_h is not None:
+            n += self.rows_h.numel() * 2
+        return n
+
     def close(self):
         if getattr(self, "handle", None) is not None and self.handle.value:
             L.load().plx_grid_destroy(self.handle)
@@ -159,6 +179,42 @@ class Grid:
         _need(grad_rows, torch.float32, "grad_rows", (self.M, ROW))
         L.call("plx_render_backward", self.handle, _p(origins), _p(dirs), n, ctypes.byref(opts.c()), _p(grad_rgb),
                _p(grad_rows), _stream(stream))
+        return grad_rows
+
+    def march_state_bytes(self, n: int, opts: RenderOpts = RenderOpts()) -> int:
+        return int(L.load().plx_march_state_bytes(self.handle, int(n), ctypes.byref(opts.c())))
+
+    def new_march_state(self, n: int, opts: RenderOpts = RenderOpts()) -> torch.Tensor:
+        """A device buffer for the march state of n rays (plx_render_train / plx_render_backward_train)."""
+        nbytes = self.march_state_bytes(n, opts)
+        if nbytes == 0:
+            raise ValueError("invalid arguments for a march state")
+        return torch.empty(nbytes, dtype=torch.uint8, device=self.idx.device)
+
+    def render_train(self, origins: torch.Tensor, dirs: torch.Tensor, opts: RenderOpts, state: torch.Tensor,
+                     rgb: Optional[torch.Tensor] = None, T_end: Optional[torch.Tensor] = None, stream=None):
+        """plx_render_train: the forward of a training batch, leaving the march state in `state`."""
+        n = origins.shape[0]
+        _need(origins, torch.float32, "origins", (n, 3))
+        _need(dirs, torch.float32, "dirs", (n, 3))
+        _need(state, torch.uint8, "state")
+        if rgb is None:
+            rgb = torch.empty((n, 3), dtype=torch.float32, device=origins.device)
+        L.call("plx_render_train", self.handle, _p(origins), _p(dirs), n, ctypes.byref(opts.c()), _p(rgb), _p(T_end),
+               _p(state), state.numel(), _stream(stream))
+        return rgb
+
+    def render_backward_train(self, origins, dirs, grad_rgb, opts: RenderOpts, state: torch.Tensor,
+                              grad_rows: Optional[torch.Tensor] = None, stream=None):
+        """plx_render_backward_train: the adjoint of the last render_train on these rays, from its state."""
+        n = origins.shape[0]
+        _need(grad_rgb, torch.float32, "grad_rgb", (n, 3))
+        _need(state, torch.uint8, "state")
+        if grad_rows is None:
+            grad_rows = torch.zeros((self.M, ROW), dtype=torch.float32, device=origins.device)
+        _need(grad_rows, torch.float32, "grad_rows", (self.M, ROW))
+        L.call("plx_render_backward_train", self.handle, _p(origins), _p(dirs), n, ctypes.byref(opts.c()),
+               _p(grad_rgb), _p(state), state.numel(), _p(grad_rows), _stream(stream))
         return grad_rows
 
     def count_nodes(self, origins, dirs, opts: RenderOpts = RenderOpts(), stream=None) -> torch.Tensor:
@@ -220,6 +276,27 @@ def gen_rays(cams: torch.Tensor, pix: torch.Tensor, W: int, H: int, origins=None
     L.call("plx_gen_rays", _p(cams), cams.shape[0], int(W), int(H), _p(pix), n, _p(origins), _p(dirs),
            _stream(stream))
     return origins, dirs
+
+
+TILE_W = 16
+TILE_H = 16
+MAX_TILE_SCENES = 8
+# plx_tile: scene, camera, x0, y0, W, H (int32), d_rgb (device pointer)
+TILE_DTYPE = np.dtype([("scene", "<i4"), ("camera", "<i4"), ("x0", "<i4"), ("y0", "<i4"), ("W", "<i4"),
+                       ("H", "<i4"), ("d_rgb", "<u8")])
+assert TILE_DTYPE.itemsize == 32
+
+
+def render_tiles(grids: Sequence[Grid], cams: torch.Tensor, tiles: torch.Tensor, n_tiles: int,
+                 opts: RenderOpts = RenderOpts(), stream=None):
+    """plx_render_tiles: `tiles` is a device byte tensor holding n_tiles TILE_DTYPE records."""
+    _need(cams, torch.float32, "cams")
+    _need(tiles, torch.uint8, "tiles")
+    if tiles.numel() < n_tiles * TILE_DTYPE.itemsize:
+        raise ValueError("tiles holds fewer than n_tiles records")
+    handles = (ctypes.c_void_p * len(grids))(*[g.handle.value for g in grids])
+    L.call("plx_render_tiles", handles, len(grids), _p(cams), cams.shape[0], _p(tiles), int(n_tiles),
+           ctypes.byref(opts.c()), _stream(stream))
 
 
 def mse_grad(rgb: torch.Tensor, target: torch.Tensor, grad_rgb=None, loss=None, stream=None):

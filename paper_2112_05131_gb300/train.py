@@ -1,8 +1,11 @@
 """The optimisation step of Sec. 3.4 as a sequence of library calls, and the learning-rate schedules.
 
 One step (Supp. A.1: 5000-ray batches, RMSProp, stochastic TV on contiguous segments):
-  plx_gen_rays -> plx_render -> plx_mse_grad -> plx_render_backward -> plx_tv_grad -> plx_rmsprop_step
-All six are kernels of libplenoxel enqueued on one stream with no host synchronisation.
+  plx_gen_rays -> plx_render_train -> plx_mse_grad -> plx_render_backward_train -> plx_tv_grad
+  -> plx_rmsprop_step
+all libplenoxel calls enqueued on one stream with no host synchronisation.  The training march
+(plx_render_train: header, plan, chunks, combine; plx_render_backward_train: chunks) splits rays
+into chunk work items and hands the march state from the forward to the adjoint.
 """
 from __future__ import annotations
 
@@ -14,7 +17,9 @@ import torch
 
 from .grid import ROW, Grid, RenderOpts, gen_rays, mse_grad
 
-LAUNCHES_PER_STEP = 6
+# kernels one step enqueues with stop_thresh = 0: gen_rays, render_train (header, plan, chunks,
+# combine), mse, backward_train, tv, rmsprop
+LAUNCHES_PER_STEP = 10
 
 
 def lr_sigma(step: int, init: float = 30.0, final: float = 0.05, max_steps: int = 250000, delay_steps: int = 15000,
@@ -65,6 +70,7 @@ class Trainer:
         self.rgb = torch.empty((n, 3), dtype=torch.float32, device=dev)
         self.grad_rgb = torch.empty((n, 3), dtype=torch.float32, device=dev)
         self.loss = torch.zeros(1, dtype=torch.float32, device=dev)
+        self.state = grid.new_march_state(n, cfg.opts)  # fits every batch of up to n rays
 
     def step(self, pix: torch.Tensor, target: torch.Tensor, seg_start: Optional[torch.Tensor],
              seg_len: Optional[torch.Tensor], n_selected: int, lr_s: float, lr_h: float,
@@ -81,11 +87,11 @@ class Trainer:
         mark(0)
         gen_rays(self.cams, pix, self.W, self.H, o, d, stream=stream)
         mark(1)
-        g.render(o, d, c.opts, rgb, stream=stream)
+        g.render_train(o, d, c.opts, self.state, rgb, stream=stream)
         mark(2)
         mse_grad(rgb, target, grgb, self.loss, stream=stream)
         mark(3)
-        g.render_backward(o, d, grgb, c.opts, self.grad, stream=stream)
+        g.render_backward_train(o, d, grgb, c.opts, self.state, self.grad, stream=stream)
         mark(4)
         if seg_start is not None and n_selected > 0:
             g.tv_grad(seg_start, seg_len, n_selected, c.lambda_tv_sigma, c.lambda_tv_sh, self.grad, stream=stream)

@@ -112,3 +112,33 @@ def bf16_grid_rows(rows28):
     out = np.array(rows28, np.float32, copy=True)
     out[:, 1:] = oracle.round_bf16(out[:, 1:])
     return out
+
+
+def rmsprop_first_step_bound(g_ref, tol_g, x_ref, lr_sigma, lr_sh, beta, eps):
+    """Entrywise bound on |x_gpu - x_ref| after RMSProp's first step (v = 0) when the GPU gradient is
+    only known to lie in [g_ref - tol_g, g_ref + tol_g].  The update u(g) = lr g / (sqrt((1 - beta) g^2)
+    + eps) is monotone in g, so over that interval it moves by at most max |u(g_ref +- tol) - u(g_ref)|;
+    FP32 rounding of x adds a few ulp."""
+    lr = np.array([lr_sigma] + [lr_sh] * 27)[None, :]
+
+    def u(gg):
+        return lr * gg / (np.sqrt((1 - beta) * gg * gg) + eps)
+
+    du = np.maximum(np.abs(u(g_ref + tol_g) - u(g_ref)), np.abs(u(g_ref - tol_g) - u(g_ref)))
+    return du + 4 * np.finfo(np.float32).eps * (np.abs(x_ref) + np.abs(u(g_ref)))
+
+
+def grad_tolerance(g_ref, extra_abs=None):
+    """The per-entry gradient tolerance check_grads applies (without row selection)."""
+    g_ref = np.asarray(g_ref, np.float64)[:, :28]
+    gmax = float(np.max(np.abs(g_ref))) if g_ref.size else 0.0
+    tol = GRAD_RTOL * np.maximum(np.abs(g_ref), GRAD_FLOOR * gmax)
+    if extra_abs is not None:
+        tol = tol + np.asarray(extra_abs, np.float64)[:, :28]
+    return tol
+
+
+def psnr(x, y):
+    """Peak signal-to-noise ratio in dB for colours on a unit peak."""
+    mse = float(np.mean((np.asarray(x, np.float64) - np.asarray(y, np.float64)) ** 2))
+    return float("inf") if mse == 0.0 else -10.0 * math.log10(mse)

@@ -1,0 +1,169 @@
+"""Parity at full size, in the launch configuration the benchmark times.
+
+* 256^3 at 8% occupancy: one whole optimisation step of Trainer.step (5000-ray batch drawn from 100
+  800x800 views, TV on 1% of the nodes in 4096-node segments, sparse RMSProp), every output element
+  (colours, updated rows, RMSProp state) checked against the oracle.
+* 512^3 at 3% occupancy, FP32 and BF16-SH forms: the 5000-ray batch forward and adjoint, all rays and
+  all gradient rows checked.
+* 512^3 full frames: 25 held-out 800x800 views rendered one 640,000-ray launch each; 64 seeded pixels
+  per view (1600 rays) checked against the oracle, and the PSNR lost by storing SH in BF16 measured
+  against the ground truth on those rays (Sec. 3.1 grid, a BF16 storage form of this implementation).
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import synth
+from parity import (bf16_grid_rows, check_colours, check_grads, delta_of, grad_tolerance, psnr,
+                    rmsprop_first_step_bound)
+
+pytestmark = pytest.mark.gpu
+
+BETA, EPS = 0.95, 1e-8
+LAM_TV_SIGMA, LAM_TV_SH = 1e-5, 1e-3
+BG = (1.0, 1.0, 1.0)
+
+
+def _oracle_rays(cams, pix):
+    """The oracle's rays, held at the FP32 precision of the library's ray buffers."""
+    o, d = oracle.gen_rays(cams.astype(np.float64), pix)
+    return o.astype(np.float32), d.astype(np.float32)
+
+
+@pytest.fixture(scope="module")
+def scene256():
+    gt = synth.scene_config("sparse256")
+    return gt, synth.perturb(gt, 0.02, seed=1)
+
+
+@pytest.fixture(scope="module")
+def scene512():
+    gt = synth.scene_config("sparse512")
+    return gt, synth.perturb(gt, 0.02, seed=1)
+
+
+def test_full_step_sparse256(cuda_lib, scene256):
+    from paper_2112_05131_gb300.grid import Grid, RenderOpts
+    from paper_2112_05131_gb300.train import StepConfig, Trainer, lr_sh, lr_sigma
+
+    gt, sc = scene256
+    R, n = gt.R, 5000
+    cams = synth.cameras_config("hemi100_800")
+    pix = synth.pixel_batch(100, 800, 800, n, seed=1000)
+    ss, sl = synth.tv_segments(R, 0.01, 4096, seed=2000)
+    n_sel = int(sl.sum())
+    lrs, lrh = lr_sigma(0), lr_sh(0)
+    opts = RenderOpts(0.5, BG, 0.0)
+
+    # ---- oracle (FP64)
+    o32, d32 = _oracle_rays(cams, pix)
+    o64, d64 = o32.astype(np.float64), d32.astype(np.float64)
+    target = oracle.render(R, gt.idx, gt.rows, o64, d64, bg=BG)[0].astype(np.float32)
+    rgb_ref, aux = oracle.render(R, sc.idx, sc.rows, o64, d64, bg=BG)
+    L_ref, grgb_ref = oracle.mse(rgb_ref, target.astype(np.float64))
+    g_ref = oracle.render_backward(R, sc.idx, sc.rows, o64, d64, grgb_ref, bg=BG)
+    _, g_ref = oracle.tv(R, sc.idx, sc.rows, ss, sl, LAM_TV_SIGMA, LAM_TV_SH, grad_rows=g_ref)
+    x_ref, v_ref, _ = oracle.rmsprop(sc.rows, np.zeros_like(g_ref), g_ref, lrs, lrh, BETA, EPS)
+
+    # ---- the library: one Trainer.step, as timed by the benchmark
+    g = Grid.from_host(R, sc.idx, sc.rows)
+    tr = Trainer(g, torch.from_numpy(cams).cuda(), 800, 800, StepConfig(batch=n, opts=opts))
+    tr.step(torch.from_numpy(pix).cuda(), torch.from_numpy(target).cuda(), torch.from_numpy(ss).cuda(),
+            torch.from_numpy(sl).cuda(), n_sel, lrs, lrh)
+    torch.cuda.synchronize()
+    g.check()
+    assert np.array_equal(tr.d.cpu().numpy(), d32)  # the library's rays are the same FP32 roundings
+
+    worst_c, nflag = check_colours(tr.rgb.cpu().numpy(), rgb_ref, aux, sc.rows, delta_of(R, 0.5), BG)
+    assert abs(tr.loss.item() - L_ref) <= 1e-4 * L_ref
+    # colour tolerance carried through the MSE gradient into the adjoint (entrywise, by the oracle's
+    # absolute-value adjoint), then through RMSProp's monotone first update
+    dC = 1e-5 * np.maximum(np.abs(rgb_ref), 1e-3)
+    carried = oracle.render_backward_abs(R, sc.idx, sc.rows, o64, d64, 2.0 * dC / n, bg=BG)
+    tol_g = grad_tolerance(g_ref, carried)
+    x = g.rows[:, :28].cpu().numpy().astype(np.float64)
+    bound = rmsprop_first_step_bound(g_ref, tol_g, x_ref, lrs, lrh, BETA, EPS)
+    err = np.abs(x - x_ref)
+    assert np.all(err <= bound), f"rows: worst err/bound {float(np.max(err / bound)):.3f}"
+    # v = (1 - beta) g^2 after one step from zero
+    v = tr.v[:, :28].cpu().numpy().astype(np.float64)
+    vb = (1 - BETA) * (2 * np.abs(g_ref) * tol_g + tol_g ** 2) + 4 * np.finfo(np.float32).eps * v_ref
+    assert np.all(np.abs(v - v_ref) <= vb + 1e-45)
+    assert np.all(tr.grad.cpu().numpy() == 0.0)  # the step leaves the gradient cleared
+    touched = int((g_ref != 0).any(1).sum())
+    print(f"256^3 step: colour err/tol {worst_c:.3f} (flagged {nflag}), rows touched {touched} of {g.M}, "
+          f"rows err/bound {float(np.max(err / bound)):.3f}")
+
+
+@pytest.mark.parametrize("form", [0, 1])
+def test_batch_forward_backward_sparse512(cuda_lib, scene512, form):
+    from paper_2112_05131_gb300.grid import Grid, RenderOpts
+
+    gt, sc = scene512
+    R, n = gt.R, 5000
+    cams = synth.cameras_config("hemi100_800")
+    pix = synth.pixel_batch(100, 800, 800, n, seed=1001)
+    o32, d32 = _oracle_rays(cams, pix)
+    gw = (np.random.default_rng(77).normal(size=(n, 3)) * 1e-3).astype(np.float32)
+    rows = sc.rows if form == 0 else bf16_grid_rows(sc.rows)
+    ref, aux = oracle.render(R, sc.idx, rows, o32.astype(float), d32.astype(float), bg=BG)
+    gref = oracle.render_backward(R, sc.idx, rows, o32.astype(float), d32.astype(float), gw.astype(float), bg=BG)
+
+    g = Grid.from_host(R, sc.idx, sc.rows, sh_form=form)
+    ot, dt = torch.from_numpy(o32).cuda(), torch.from_numpy(d32).cuda()
+    opts = RenderOpts(0.5, BG, 0.0)
+    rgb = g.render(ot, dt, opts).cpu().numpy()
+    grad = g.render_backward(ot, dt, torch.from_numpy(gw).cuda(), opts).cpu().numpy()
+    g.check()
+    worst_c, nflag = check_colours(rgb, ref, aux, rows, delta_of(R, 0.5), BG)
+    worst_g = check_grads(grad, gref)
+    touched = (gref != 0).any(1)
+    assert np.all(grad[~touched] == 0.0)  # rows no ray reaches stay exactly zero
+    print(f"512^3 form {form}: colour err/tol {worst_c:.3f} (flagged {nflag}), grad err/tol {worst_g:.3f}, "
+          f"{int(touched.sum())} rows touched")
+
+
+def test_full_frames_sampled_and_bf16_psnr_sparse512(cuda_lib, scene512):
+    from paper_2112_05131_gb300.grid import Grid, RenderOpts, gen_rays
+
+    gt, sc = scene512
+    R, W, H = gt.R, 800, 800
+    cams = synth.cameras_config("hemi25_800_test")
+    V = cams.shape[0]
+    rng = np.random.default_rng(4242)
+    local = np.stack([rng.choice(W * H, 64, replace=False) for _ in range(V)])  # pixels within each view
+    pix = (local + (np.arange(V) * W * H)[:, None]).reshape(-1)
+    o32, d32 = _oracle_rays(cams, pix)
+    o64, d64 = o32.astype(np.float64), d32.astype(np.float64)
+    target, _ = oracle.render(R, gt.idx, gt.rows, o64, d64, bg=BG)
+    ref32, aux = oracle.render(R, sc.idx, sc.rows, o64, d64, bg=BG)
+    rows16 = bf16_grid_rows(sc.rows)
+    ref16, aux16 = oracle.render(R, sc.idx, rows16, o64, d64, bg=BG)
+
+    opts = RenderOpts(0.5, BG, 0.0)
+    cams_t = torch.from_numpy(cams).cuda()
+    out = {}
+    for form in (0, 1):
+        g = Grid.from_host(R, sc.idx, sc.rows, sh_form=form)
+        got = np.empty((V * 64, 3), np.float32)
+        rgb = torch.empty((W * H, 3), device="cuda")
+        for v in range(V):
+            o, d = gen_rays(cams_t, torch.arange(v * W * H, (v + 1) * W * H, device="cuda"), W, H)
+            # the sampled pixels carry the oracle's own rays (equal to the library's but for rays within
+            # ~1e-14 of an FP32 rounding midpoint); the frame is rendered in one launch as when timed
+            sel = torch.from_numpy(local[v]).cuda()
+            o[sel] = torch.from_numpy(o32[v * 64:(v + 1) * 64]).cuda()
+            d[sel] = torch.from_numpy(d32[v * 64:(v + 1) * 64]).cuda()
+            g.render(o, d, opts, rgb)
+            got[v * 64:(v + 1) * 64] = rgb[sel].cpu().numpy()
+        g.check()
+        out[form] = got
+        del g
+    w32, f32 = check_colours(out[0], ref32, aux, sc.rows, delta_of(R, 0.5), BG)
+    w16, f16 = check_colours(out[1], ref16, aux16, rows16, delta_of(R, 0.5), BG)
+    p32, p16 = psnr(out[0], target), psnr(out[1], target)
+    p16_vs_32 = psnr(out[1], ref32)
+    assert p32 - p16 <= 0.05, (p32, p16)
+    print(f"512^3 frames: err/tol f32 {w32:.3f} bf16 {w16:.3f}; PSNR vs ground truth f32 {p32:.3f} dB, "
+          f"bf16 {p16:.3f} dB (loss {p32 - p16:.4f} dB); bf16 vs oracle on the f32 grid {p16_vs_32:.2f} dB")

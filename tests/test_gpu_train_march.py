@@ -1,0 +1,200 @@
+"""The training march (plx_render_train / plx_render_backward_train, chunk work items and a march
+state handed from the forward to the adjoint) against the FP64 oracle, through the C ABI."""
+import ctypes
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import synth
+from parity import bf16_grid_rows, check_colours, check_grads, delta_of, tie_flags
+
+pytestmark = pytest.mark.gpu
+
+BG = (0.9, 0.6, 0.3)
+
+
+def _sparse_scene(R, frac_occ, seed, sigma=(0.0, 30.0), neg_frac=0.2):
+    rng = np.random.default_rng(seed)
+    occ = rng.uniform(size=R ** 3) < frac_occ
+    idx = np.full(R ** 3, -1, np.int32)
+    idx[occ] = np.arange(int(occ.sum()), dtype=np.int32)
+    M = int(occ.sum())
+    rows = np.empty((M, 28), np.float32)
+    rows[:, 0] = rng.uniform(*sigma, size=M)
+    neg = rng.uniform(size=M) < neg_frac
+    rows[neg, 0] = -rows[neg, 0]
+    rows[:, 1:] = rng.normal(0, 0.4, size=(M, 27))
+    return synth.Scene(R, idx, rows)
+
+
+def _both(sc, o, d, gw, opts, form=0):
+    """(rgb, T_end, grad) from the training march, and the oracle's (rgb, aux, grad), on the same rays."""
+    from paper_2112_05131_gb300.grid import Grid
+
+    g = Grid.from_host(sc.R, sc.idx, sc.rows, sh_form=form)
+    ot, dt = torch.from_numpy(o).cuda(), torch.from_numpy(d).cuda()
+    state = g.new_march_state(o.shape[0], opts)
+    T = torch.empty(o.shape[0], device="cuda")
+    rgb = g.render_train(ot, dt, opts, state, T_end=T)
+    grad = g.render_backward_train(ot, dt, torch.from_numpy(gw).cuda(), opts, state)
+    g.check()
+    rows = sc.rows if form == 0 else bf16_grid_rows(sc.rows)
+    kw = dict(step_vox=opts.step_vox, bg=opts.bg, stop_thresh=opts.stop_thresh)
+    ref, aux = oracle.render(sc.R, sc.idx, rows, o.astype(float), d.astype(float), **kw)
+    gref = oracle.render_backward(sc.R, sc.idx, rows, o.astype(float), d.astype(float), gw.astype(float), **kw)
+    return rgb.cpu().numpy(), T.cpu().numpy(), grad.cpu().numpy(), ref, aux, gref, rows
+
+
+@pytest.mark.parametrize("form", [0, 1])
+@pytest.mark.parametrize("stop", [0.0, 1e-4])
+def test_train_march_dense32(cuda_lib, form, stop):
+    from paper_2112_05131_gb300.grid import RenderOpts
+
+    sc = synth.scene_config("dense32")
+    o, d = synth.random_rays(2048, seed=41)
+    gw = (np.random.default_rng(42).normal(size=(2048, 3)) / 2048).astype(np.float32)
+    opts = RenderOpts(0.5, (1.0, 1.0, 1.0), stop)
+    rgb, T, grad, ref, aux, gref, rows = _both(sc, o, d, gw, opts, form)
+    wc, nflag = check_colours(rgb, ref, aux, rows, delta_of(sc.R, 0.5), opts.bg, stop)
+    assert np.allclose(T, aux[:, 0], rtol=1e-4, atol=1e-6 + stop)
+    wg = check_grads(grad, gref)
+    print(f"dense32 form={form} stop={stop}: colour err/tol {wc:.3f} (flagged {nflag}), grad err/tol {wg:.3f}")
+
+
+@pytest.mark.parametrize("form", [0, 1])
+@pytest.mark.parametrize("R,n", [(48, 1237), (67, 3001)])  # several CTAs, ragged tails of rays and chunks
+def test_train_march_sparse(cuda_lib, R, n, form):
+    from paper_2112_05131_gb300.grid import RenderOpts
+
+    sc = _sparse_scene(R, 0.15, 300 + R)
+    o, d = synth.random_rays(n, seed=R + 1, spread=0.9)
+    gw = (np.random.default_rng(R).normal(size=(n, 3)) * 1e-3).astype(np.float32)
+    opts = RenderOpts(0.5, BG, 0.0)
+    rgb, T, grad, ref, aux, gref, rows = _both(sc, o, d, gw, opts, form)
+    wc, nflag = check_colours(rgb, ref, aux, rows, delta_of(R, 0.5), BG)
+    wg = check_grads(grad, gref)
+    assert np.all(grad[:, 28:] == 0.0)
+    print(f"sparse R={R} form={form}: colour err/tol {wc:.3f} (flagged {nflag}), grad err/tol {wg:.3f}")
+
+
+# Unit roundoffs granted to FP32 where the adjoint subtracts nearly equal numbers: the density term
+# T_{s+1} c - R_s of a long ray whose colours resemble what lies behind it (and sums of gradient
+# terms of both signs).  Each operand is formed by fewer than 64 rounded operations along any path
+# of the warp scans, the per-ray chunk scan and the interpolation and SH sums.
+FP32_CANCEL_U = 64 * 2.0 ** -24
+
+
+def test_train_march_long_rays_many_chunks(cuda_lib):
+    """A dense 64^3 grid marched at 0.05 voxel: rays of 1300-2200 samples, more than 32 chunks each,
+    so the per-ray combine runs its multi-group prefix and suffix passes.  Thin density and colours
+    close to the background make T_{s+1} c - R_s cancel by up to ~400x on some rows; the gradient
+    tolerance there adds FP32_CANCEL_U times the oracle's magnitude adjoint (the size of the
+    operands), the rounding bound of any FP32 evaluation of the same formula."""
+    from paper_2112_05131_gb300.grid import RenderOpts
+
+    R = 64
+    rng = np.random.default_rng(5)
+    idx = np.arange(R ** 3, dtype=np.int32)
+    rows = np.empty((R ** 3, 28), np.float32)
+    rows[:, 0] = rng.uniform(0.0, 0.6, size=R ** 3)  # thin enough that light crosses the whole box
+    rows[:, 1:] = rng.normal(0, 0.3, size=(R ** 3, 27))
+    rows[:, [1, 10, 19]] += 2.0
+    sc = synth.Scene(R, idx, rows)
+    o, d = synth.random_rays(300, seed=6, spread=0.3)
+    gw = (rng.normal(size=(300, 3)) * 1e-3).astype(np.float32)
+    opts = RenderOpts(0.05, BG, 0.0)
+    rgb, T, grad, ref, aux, gref, rows_ = _both(sc, o, d, gw, opts)
+    assert aux[:, 1].max() > 32 * 32, aux[:, 1].max()  # some ray has more than 32 chunks
+    wc, _ = check_colours(rgb, ref, aux, rows_, delta_of(R, 0.05), BG)
+    mag = oracle.render_backward_mag(R, sc.idx, rows_, o.astype(float), d.astype(float), gw.astype(float),
+                                     step_vox=0.05, bg=BG)
+    wg = check_grads(grad, gref, extra_abs=FP32_CANCEL_U * mag)
+    print(f"long rays (max {int(aux[:, 1].max())} samples): colour err/tol {wc:.3f}, grad err/tol {wg:.3f}")
+
+
+def test_train_march_matches_render_and_is_deterministic(cuda_lib):
+    from paper_2112_05131_gb300.grid import Grid, RenderOpts
+
+    sc = _sparse_scene(40, 0.2, 21)
+    g = Grid.from_host(sc.R, sc.idx, sc.rows)
+    o, d = synth.random_rays(5000, seed=22)
+    ot, dt = torch.from_numpy(o).cuda(), torch.from_numpy(d).cuda()
+    opts = RenderOpts(0.5, BG, 0.0)
+    state = g.new_march_state(5000, opts)
+    a = g.render_train(ot, dt, opts, state).cpu().numpy()
+    b = g.render_train(ot, dt, opts, state).cpu().numpy()
+    assert np.array_equal(a.view(np.uint32), b.view(np.uint32))  # item order varies, results do not
+    ref = g.render(ot, dt, opts).cpu().numpy()
+    assert np.allclose(a, ref, rtol=1e-5, atol=1e-7)
+
+
+def test_train_march_edge_cases(cuda_lib):
+    from paper_2112_05131_gb300.grid import Grid, RenderOpts
+
+    opts = RenderOpts(0.5, BG, 0.0)
+    sc = _sparse_scene(16, 0.3, 9)
+    g = Grid.from_host(sc.R, sc.idx, sc.rows)
+    # zero rays
+    empty = torch.empty((0, 3), device="cuda")
+    st0 = g.new_march_state(0, opts)
+    assert g.render_train(empty, empty, opts, st0).shape == (0, 3)
+    grad0 = g.render_backward_train(empty, empty, torch.empty((0, 3), device="cuda"), opts, st0)
+    assert torch.count_nonzero(grad0) == 0
+    # misses, rays starting inside, rays along faces
+    o = np.float32([[3, 3, 3], [0.1, -0.2, 0.3], [-3, 0.5, 0.25], [-3, 1.0, 0.0], [0.0, 0.0, 5.0], [-3, -1, -1]])
+    d = np.float32([[1, 0, 0], [0.6, 0.0, 0.8], [1, 0, 0], [1, 0, 0], [0, 0, -1], [1, 0, 0]])
+    gw = np.full((6, 3), 0.01, np.float32)
+    # rays 2-5 run along a box axis from outside: (t_far - t_near) / delta is exactly 30, a tie
+    # that FP32 and FP64 may resolve differently (one sample more or less).  Their colours are checked
+    # with the one-sample bound; their gradients are left out (g = 0 on both sides).
+    _, aux0 = oracle.render(sc.R, sc.idx, sc.rows, o.astype(float), d.astype(float), bg=BG)
+    ties = tie_flags(aux0, delta_of(16, 0.5))
+    assert ties.sum() >= 3
+    gw[ties] = 0.0
+    rgb, T, grad, ref, aux, gref, rows = _both(sc, o, d, gw, opts)
+    check_colours(rgb, ref, aux, rows, delta_of(16, 0.5), BG)
+    check_grads(grad, gref)
+    assert np.any(gref != 0)
+    assert np.all(rgb[0] == np.float32(BG))
+    # an all-empty grid: background, no gradient
+    ge = Grid.from_host(16, np.full(16 ** 3, -1, np.int32), np.zeros((0, 28), np.float32))
+    o2, d2 = synth.random_rays(100, seed=3)
+    ot, dt = torch.from_numpy(o2).cuda(), torch.from_numpy(d2).cuda()
+    st = ge.new_march_state(100, opts)
+    rgb2 = ge.render_train(ot, dt, opts, st).cpu().numpy()
+    assert np.all(rgb2 == np.float32(BG)[None, :])
+
+
+def test_train_march_rejects_a_foreign_state(cuda_lib):
+    from paper_2112_05131_gb300._lib import PlxError
+    from paper_2112_05131_gb300.grid import Grid, RenderOpts
+
+    opts = RenderOpts(0.5, BG, 0.0)
+    sc = _sparse_scene(24, 0.3, 10)
+    g = Grid.from_host(sc.R, sc.idx, sc.rows)
+    o, d = synth.random_rays(500, seed=12)
+    ot, dt = torch.from_numpy(o).cuda(), torch.from_numpy(d).cuda()
+    st = g.new_march_state(500, opts)
+    g.render_train(ot, dt, opts, st)
+    # other ray buffers than the forward's: the device check refuses, adds nothing, flags the grid
+    ot2, dt2 = ot.clone(), dt.clone()
+    grad = g.render_backward_train(ot2, dt2, torch.ones((500, 3), device="cuda"), opts, st)
+    torch.cuda.synchronize()
+    assert torch.count_nonzero(grad) == 0
+    with pytest.raises(PlxError, match="PLX_EDEVICE"):
+        g.check()
+    g.check()  # the status word was cleared by the previous check
+    # other options than the forward's: refused the same way
+    grad = g.render_backward_train(ot, dt, torch.ones((500, 3), device="cuda"), RenderOpts(0.7, BG, 0.0), st)
+    assert torch.count_nonzero(grad) == 0
+    with pytest.raises(PlxError, match="PLX_EDEVICE"):
+        g.check()
+    # a state buffer that is too small is refused on the host, before any launch
+    with pytest.raises(PlxError, match="PLX_EINVAL"):
+        g.render_train(ot, dt, opts, st[: st.numel() // 2])
+    # a matching state still works afterwards
+    grad = g.render_backward_train(ot, dt, torch.ones((500, 3), device="cuda"), opts, st)
+    g.check()
+    assert torch.count_nonzero(grad) > 0
