@@ -57,6 +57,10 @@ def parse_args():
     ap.add_argument("--render-reps", type=int, default=20)
     ap.add_argument("--no-extras", action="store_true", help="only the headline step timing")
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="budget of the CPU oracle baseline")
+    ap.add_argument("--skip-serving", action="store_true", help="leave out the serving measurement")
+    ap.add_argument("--skip-c2f", action="store_true", help="leave out the coarse-to-fine run")
+    ap.add_argument("--c2f-steps", type=int, default=12800)
+    ap.add_argument("--skip-large-batch", action="store_true", help="leave out the 2^18-ray batch measurement")
     return ap.parse_args()
 
 
@@ -407,6 +411,21 @@ def extras(args, wl, dev_batches, cams_t, gt_grid, opts, timed_loop, st32, ms32)
         del frames
         torch.cuda.empty_cache()
 
+    # ---- fwd+bwd at 2^18-ray batches (a 5000-ray batch underfills the GPU)
+    if not args.skip_large_batch:
+        res["batch_262144"] = large_batch(args, wl, cams_t, gt_grid, opts)
+        torch.cuda.empty_cache()
+
+    # ---- serving: 4 resident BF16 scenes, continuous batching, Poisson arrivals
+    if not args.skip_serving:
+        res["serving"] = serving(args, opts)
+        torch.cuda.empty_cache()
+
+    # ---- the coarse-to-fine optimisation loop, 128^3 -> 256^3 -> 512^3, against this workload's ground truth
+    if not args.skip_c2f and wl["test_cams"]:
+        res["coarse_to_fine"] = coarse_to_fine(args, wl, cams_t, gt_grid, opts)
+        torch.cuda.empty_cache()
+
     # ---- coarse-to-fine grid operations on this workload's grid
     g = Grid.from_host(R, wl["train"].idx, wl["train"].rows)
     t = []
@@ -441,6 +460,120 @@ def extras(args, wl, dev_batches, cams_t, gt_grid, opts, timed_loop, st32, ms32)
     # ---- CPU oracle baseline on a bounded sample of the same workload
     res["cpu_baseline"] = cpu_baseline(args, wl, budget_s=args.cpu_seconds)
     return res
+
+
+def large_batch(args, wl, cams_t, gt_grid, opts, n=1 << 18, steps=8, warmup=3):
+    """The same optimisation step on 2^18-ray batches of the workload (FP32 rows)."""
+    import torch
+
+    import synth
+    from paper_2112_05131_gb300.grid import Grid, gen_rays
+    from paper_2112_05131_gb300.train import StepConfig, Trainer, lr_sh, lr_sigma
+
+    R, W, H = wl["R"], wl["W"], wl["H"]
+    dev = cams_t.device
+    batches = []
+    for b in range(4):
+        pix = torch.from_numpy(synth.pixel_batch(wl["n_views"], W, H, n, seed=5000 + b)).to(dev)
+        o, d = gen_rays(cams_t, pix, W, H)
+        ss, sl = synth.tv_segments(R, 0.01, 4096 if R >= 128 else 256, seed=6000 + b)
+        batches.append((pix, gt_grid.render(o, d, opts), torch.from_numpy(ss).to(dev), torch.from_numpy(sl).to(dev),
+                        int(sl.sum())))
+        del o, d
+    g = Grid.from_host(R, wl["train"].idx, wl["train"].rows)
+    tr = Trainer(g, cams_t, W, H, StepConfig(batch=n, opts=opts))
+    for s in range(warmup):
+        b = batches[s % 4]
+        tr.step(b[0], b[1], b[2], b[3], b[4], lr_sigma(s), lr_sh(s))
+    stream = torch.cuda.current_stream()
+    a, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    a.record(stream)
+    for s in range(steps):
+        b = batches[s % 4]
+        tr.step(b[0], b[1], b[2], b[3], b[4], lr_sigma(warmup + s), lr_sh(warmup + s))
+    e.record(stream)
+    torch.cuda.synchronize()
+    ms = a.elapsed_time(e)
+    g.check()
+    del tr, g, batches
+    return {"value": steps * n / (ms / 1e3), "unit": "rays/s", "batch": n, "steps": steps,
+            "ms_per_step": ms / steps, "rows": "f32"}
+
+
+def coarse_to_fine(args, wl, cams_t, gt_grid, opts):
+    """Training images = the ground truth rendered for the 100 training views; a dense 128^3 start (sigma 0.1,
+    SH 0); prune (sigma < 5, dilated) and upsample at steps 4266 and 8533 of 12800; TV 5e-4 / 1e-3 on 1% of the
+    nodes; PSNR on the 25 held-out views against the ground truth's renders."""
+    import torch
+
+    import synth
+    from paper_2112_05131_gb300.coarse_to_fine import C2FConfig, psnr, render_views, train
+
+    W, H = wl["W"], wl["H"]
+    t0 = time.perf_counter()
+    images = render_views(gt_grid, cams_t, W, H, opts)
+    test_t = torch.from_numpy(synth.cameras_config(wl["test_cams"])).to(cams_t.device)
+    truth = render_views(gt_grid, test_t, W, H, opts)
+    prep = time.perf_counter() - t0
+    cfg = C2FConfig(steps=args.c2f_steps, upsample_at=(args.c2f_steps // 3, 2 * args.c2f_steps // 3))
+    log = []
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    g = train(images, cams_t, W, H, cfg, log)
+    wall = time.perf_counter() - t0
+    final = render_views(g, test_t, W, H, opts)
+    out = {"steps": cfg.steps, "batch": cfg.batch, "wall_s": wall, "steps_per_s": cfg.steps / wall,
+           "stages": log, "final_reso": g.reso, "final_rows": g.M,
+           "psnr_test_db": psnr(final, truth), "views": {"train": images.shape[0], "test": truth.shape[0]},
+           "images_render_s": prep}
+    del g, images, truth, final
+    return out
+
+
+def serving(args, opts, n_requests=240, loads=(0.5, 0.8, 0.95)):
+    """Four resident BF16-SH scenes (128^3, 256^3, 384^3, 512^3 at 8% occupancy, blobs and shell); requests of
+    256^2, 800^2, 1280x720 or 1920x1080 pixels from cameras on the upper hemisphere r = 4.  Capacity is the
+    closed-loop throughput (all requests queued at once); then Poisson arrivals at 50/80/95% of it.  Latency
+    runs from arrival to the image in pinned host memory."""
+    import torch
+
+    import synth
+    from paper_2112_05131_gb300.grid import Grid
+    from paper_2112_05131_gb300.serve import TileServer, latency_stats, requests_from, scene_device_bytes
+
+    t0 = time.time()
+    grids = []
+    sizes = (128, 256, 384, 512)
+    for R in sizes:
+        sc = synth.scene_config(f"sparse{R}_0.08", seed=7)
+        free, _ = torch.cuda.mem_get_info()
+        need = scene_device_bytes(R, sc.M, 1) + sc.M * 128  # the F32 rows are held while packing
+        if need > free - (8 << 30):  # keep 8 GB for request images and launches
+            raise RuntimeError(f"scene {R}^3 does not fit in free HBM ({free >> 20} MiB)")
+        grids.append(Grid.render_only_bf16(R, sc.idx, sc.rows))
+        del sc
+    gen_s = time.time() - t0
+    srv = TileServer(grids, opts, max_rays_per_launch=1 << 19, max_inflight=2, max_active=48)
+    srv.run(requests_from(synth.serving_requests(24, 4, seed=100)))  # warm-up: pools, caches
+    closed = requests_from(synth.serving_requests(n_requests, 4, seed=101))
+    t = time.perf_counter()
+    done = srv.run(closed)
+    wall = time.perf_counter() - t
+    cap = latency_stats(done, wall)
+    capacity_rps = len(done) / wall
+    out = {"scenes": [f"{R}^3 ({g.M} rows, BF16 SH)" for R, g in zip(sizes, grids)],
+           "capacity": {"requests_per_s": capacity_rps, **cap}, "scene_gen_s": gen_s,
+           "max_rays_per_launch": 1 << 19, "tile": "16x16"}
+    for load in loads:
+        rate = load * capacity_rps
+        reqs = requests_from(synth.serving_requests(n_requests, 4, seed=200 + int(100 * load), rate=rate))
+        t = time.perf_counter()
+        done = srv.run(reqs)
+        wall = time.perf_counter() - t
+        out[f"load_{int(100 * load)}"] = {"rate_per_s": rate, **latency_stats(done, wall)}
+    del srv, grids
+    return out
 
 
 # --------------------------------------------------------------------------- CPU oracle

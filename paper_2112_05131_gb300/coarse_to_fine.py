@@ -1,0 +1,130 @@
+"""The coarse-to-fine optimisation loop (Sec. 3.4 "Coarse to Fine", Supp. A.1) on libplenoxel.
+
+Training starts from a dense low-resolution grid; at fixed steps the grid is pruned (nodes whose
+density, and whose 3x3x3 neighbourhood's density, fall below a threshold are dropped) and then
+upsampled to twice the resolution by trilinear interpolation, and optimisation continues on the
+new grid with fresh RMSProp state.  Every step is Trainer.step (ray generation, training march,
+MSE gradient, adjoint, TV on a random 1% of the nodes in contiguous segments, sparse RMSProp);
+prune and upsample are plx_grid_prune_* / plx_grid_upsample_*.
+
+The training images are the ground-truth grid rendered by plx_render for every training view and
+held in host memory; each step's 5000 pixels are drawn on the host with a seeded generator, their
+target colours gathered there, and both copied to the device (the role a data loader plays).
+The paper does not give the steps at which it upsamples; `upsample_at` defaults to thirds of the run.
+"""
+from __future__ import annotations
+
+import time
+from dataclasses import dataclass, field
+from typing import List, Optional, Sequence
+
+import numpy as np
+import torch
+
+from .grid import Grid, RenderOpts, gen_rays
+from .train import StepConfig, Trainer, lr_sh, lr_sigma
+
+
+@dataclass
+class C2FConfig:
+    steps: int = 12800
+    start_reso: int = 128
+    upsample_at: Sequence[int] = (4266, 8533)
+    prune_tau: float = 5.0
+    batch: int = 5000
+    lambda_tv_sigma: float = 5e-4
+    lambda_tv_sh: float = 1e-3
+    tv_fraction: float = 0.01
+    tv_segment: int = 4096
+    init_sigma: float = 0.1
+    opts: RenderOpts = field(default_factory=lambda: RenderOpts(0.5, (1.0, 1.0, 1.0), 0.0))
+    chunk: int = 256  # steps whose pixel batches are prepared and uploaded together
+    seed: int = 0
+
+
+def dense_grid(R: int, sigma: float, device="cuda") -> Grid:
+    """Every node occupied, density `sigma`, SH zero."""
+    idx = torch.arange(R ** 3, dtype=torch.int32, device=device)
+    rows = torch.zeros((R ** 3, 32), dtype=torch.float32, device=device)
+    rows[:, 0] = sigma
+    return Grid(R, idx, rows)
+
+
+def render_views(grid: Grid, cams: torch.Tensor, W: int, H: int, opts: RenderOpts) -> np.ndarray:
+    """All views of `cams` rendered by plx_render, float32 [V, H, W, 3] on the host."""
+    V = cams.shape[0]
+    out = np.empty((V, H, W, 3), np.float32)
+    rgb = torch.empty((W * H, 3), dtype=torch.float32, device=cams.device)
+    for v in range(V):
+        pix = torch.arange(v * W * H, (v + 1) * W * H, dtype=torch.int64, device=cams.device)
+        o, d = gen_rays(cams, pix, W, H)
+        grid.render(o, d, opts, rgb)
+        out[v] = rgb.view(H, W, 3).cpu().numpy()
+    return out
+
+
+def psnr(a: np.ndarray, b: np.ndarray) -> float:
+    mse = float(np.mean((a.astype(np.float64) - b.astype(np.float64)) ** 2))
+    return float("inf") if mse == 0 else -10.0 * np.log10(mse)
+
+
+class _Batches:
+    """Pixel ids, targets and TV segments for `chunk` steps at a time, uploaded in one copy each."""
+
+    def __init__(self, images: np.ndarray, cfg: C2FConfig, device):
+        self.flat = images.reshape(-1, 3)
+        self.n_pix = self.flat.shape[0]
+        self.cfg = cfg
+        self.dev = device
+        self.rng = np.random.default_rng(cfg.seed)
+        self.step0 = -1
+        self.pix = self.tgt = None
+
+    def get(self, step: int, R: int):
+        import synth
+
+        c = self.cfg
+        if self.pix is None or step >= self.step0 + c.chunk or step < self.step0:
+            self.step0 = step
+            pix = self.rng.integers(0, self.n_pix, size=(c.chunk, c.batch), dtype=np.int64)
+            self.pix = torch.from_numpy(pix).pin_memory().to(self.dev, non_blocking=True)
+            self.tgt = torch.from_numpy(self.flat[pix]).pin_memory().to(self.dev, non_blocking=True)
+        k = step - self.step0
+        ss, sl = synth.tv_segments(R, c.tv_fraction, min(c.tv_segment, R ** 3), seed=int(self.rng.integers(2 ** 31)))
+        return (self.pix[k], self.tgt[k], torch.from_numpy(ss).to(self.dev, non_blocking=True),
+                torch.from_numpy(sl).to(self.dev, non_blocking=True), int(sl.sum()))
+
+
+def train(train_images: np.ndarray, cams: torch.Tensor, W: int, H: int, cfg: C2FConfig = C2FConfig(),
+          log: Optional[List[dict]] = None) -> Grid:
+    """Runs the coarse-to-fine schedule and returns the final grid.  `log` receives one record per stage."""
+    dev = cams.device
+    grid = dense_grid(cfg.start_reso, cfg.init_sigma, dev)
+    sc = StepConfig(batch=cfg.batch, opts=cfg.opts, lambda_tv_sigma=cfg.lambda_tv_sigma,
+                    lambda_tv_sh=cfg.lambda_tv_sh)
+    tr = Trainer(grid, cams, W, H, sc)
+    batches = _Batches(train_images, cfg, dev)
+    ups = sorted(int(s) for s in cfg.upsample_at)
+    t_stage = time.perf_counter()
+    for step in range(cfg.steps):
+        if ups and step == ups[0]:
+            ups.pop(0)
+            torch.cuda.synchronize()
+            before = (grid.reso, grid.M)
+            pruned = grid.prune(cfg.prune_tau, True)
+            grid = pruned.upsample(2 * grid.reso)
+            del pruned, tr
+            torch.cuda.empty_cache()
+            tr = Trainer(grid, cams, W, H, sc)
+            torch.cuda.synchronize()
+            if log is not None:
+                log.append({"step": step, "from": before, "to": (grid.reso, grid.M),
+                            "stage_s": time.perf_counter() - t_stage})
+            t_stage = time.perf_counter()
+        pix, tgt, ss, sl, nsel = batches.get(step, grid.reso)
+        tr.step(pix, tgt, ss, sl, nsel, lr_sigma(step), lr_sh(step))
+    torch.cuda.synchronize()
+    grid.check()
+    if log is not None:
+        log.append({"step": cfg.steps, "final": (grid.reso, grid.M), "stage_s": time.perf_counter() - t_stage})
+    return grid

@@ -239,3 +239,27 @@ def random_rays(n: int, seed: int, radius: float = 2.5, spread: float = 0.6):
     d = target - eye
     d /= np.linalg.norm(d, axis=1, keepdims=True)
     return eye.astype(np.float32), d.astype(np.float32)
+
+
+SERVING_RESOLUTIONS = ((256, 256), (800, 800), (1280, 720), (1920, 1080))
+
+
+def serving_requests(n: int, n_scenes: int, seed: int, rate=None, fov_deg: float = 40.0, radius: float = 4.0):
+    """n image requests as (scene, cam float32 [18], W, H, arrival s): scene uniform over n_scenes,
+    resolution uniform over SERVING_RESOLUTIONS, a camera at a uniform point of the upper hemisphere
+    of radius `radius` looking at the origin, Poisson arrivals at `rate` per second (all 0 if None)."""
+    rng = np.random.default_rng(seed)
+    out = []
+    t = 0.0
+    for _ in range(n):
+        W, H = SERVING_RESOLUTIONS[int(rng.integers(len(SERVING_RESOLUTIONS)))]
+        z = rng.uniform(0.05, 1.0)
+        phi = rng.uniform(0.0, 2.0 * math.pi)
+        r = math.sqrt(1.0 - z * z)
+        c2w = look_at(radius * np.array([r * math.cos(phi), r * math.sin(phi), z]))
+        f = 0.5 * W / math.tan(0.5 * math.radians(fov_deg))
+        cam = np.concatenate([c2w.reshape(-1), [f, f, 0.5 * W, 0.5 * H, W, H]]).astype(np.float32)
+        if rate is not None:
+            t += rng.exponential(1.0 / rate)
+        out.append((int(rng.integers(n_scenes)), cam, W, H, t))
+    return out
