@@ -151,6 +151,8 @@ plx_status plx_grid_create(const plx_grid_desc *desc, const int32_t *d_idx, floa
     v.rows_h = d_rows_bf16;
     v.occ = reinterpret_cast<const uint32_t *>(g->ws + g->layout.occ_off);
     v.touched = reinterpret_cast<uint32_t *>(g->ws + g->layout.touched_off);
+    v.tlist = reinterpret_cast<int32_t *>(g->ws + g->layout.list_off);
+    v.tcount = reinterpret_cast<int *>(g->ws + g->layout.status_off + plx::WorkspaceLayout::kListCountOff);
     v.status = reinterpret_cast<int *>(g->ws + g->layout.status_off);
     v.R = desc->reso;
     v.form = desc->sh_form;
@@ -168,7 +170,7 @@ plx_status plx_grid_create(const plx_grid_desc *desc, const int32_t *d_idx, floa
     // status block and touched bits start at zero; occupancy is rebuilt from the index volume
     cudaError_t e = cudaMemsetAsync(g->ws + g->layout.status_off, 0, 256, s);
     if (e == cudaSuccess)
-        e = cudaMemsetAsync(g->ws + g->layout.touched_off, 0, g->layout.total - g->layout.touched_off, s);
+        e = cudaMemsetAsync(g->ws + g->layout.touched_off, 0, g->layout.list_off - g->layout.touched_off, s);
     if (e == cudaSuccess) e = plx::launch_build_occupancy(v, reinterpret_cast<uint32_t *>(g->ws + g->layout.occ_off), s);
     if (e != cudaSuccess) {
         delete g;
@@ -283,10 +285,11 @@ plx_status march_state(const plx_grid *grid, const float *d_origins, const float
     char *b = static_cast<char *>(d_state);
     ptrs->hdr = reinterpret_cast<plx::MarchHeader *>(b + L.hdr_off);
     ptrs->n_occ = reinterpret_cast<int32_t *>(b + L.nocc_off);
-    ptrs->first = reinterpret_cast<int32_t *>(b + L.first_off);
+    ptrs->range = reinterpret_cast<int2 *>(b + L.first_off);
     ptrs->items = reinterpret_cast<int2 *>(b + L.items_off);
     ptrs->part = reinterpret_cast<float4 *>(b + L.part_off);
     ptrs->live = reinterpret_cast<uint8_t *>(b + L.live_off);
+    ptrs->samp = plx::MarchLayout::store_samples(p.max_chunks) ? reinterpret_cast<uint16_t *>(b + L.samp_off) : nullptr;
     ptrs->max_chunks = p.max_chunks;
     std::memset(hdr, 0, sizeof(*hdr));
     hdr->magic = plx::kMarchMagic;

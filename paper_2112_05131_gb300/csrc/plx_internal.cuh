@@ -23,9 +23,11 @@ constexpr unsigned kFull = 0xffffffffu;
 // device status codes (stored in the grid workspace's first word)
 enum : int { kDevOk = 0, kDevBadRow = 1, kDevTooManySamples = 2, kDevCountMismatch = 3, kDevStateMismatch = 4, kDevBadTile = 5 };
 
-// Workspace layout of a grid: [status block 256 B][occupancy bits][touched bits]
+// Workspace layout of a grid: [status block 256 B][occupancy bits][touched bits][touched-row list].
+// The status block holds the device status word at byte 0 and the touched-list length at byte 64.
 struct WorkspaceLayout {
-    size_t status_off, occ_off, touched_off, total;
+    size_t status_off, occ_off, touched_off, list_off, total;
+    static constexpr size_t kListCountOff = 64;
     static size_t round256(size_t b) { return (b + 255) & ~size_t(255); }
     static WorkspaceLayout make(int64_t R, int64_t M) {
         WorkspaceLayout L;
@@ -33,7 +35,8 @@ struct WorkspaceLayout {
         L.status_off = 0;
         L.occ_off = 256;
         L.touched_off = L.occ_off + round256(size_t((nodes + 31) / 32) * 4);
-        L.total = L.touched_off + round256(size_t((M + 31) / 32 + 1) * 4);
+        L.list_off = L.touched_off + round256(size_t((M + 31) / 32 + 1) * 4);
+        L.total = L.list_off + round256(size_t(M) * 4);
         return L;
     }
 };
@@ -44,6 +47,8 @@ struct GridView {
     const uint16_t *rows_h;     // BF16-SH rows (null for the F32 form)
     const uint32_t *occ;        // bit per base node: 1 if any of the cell's 8 nodes is occupied
     uint32_t *touched;          // bit per row: set when a gradient lands on the row
+    int32_t *tlist;             // the touched rows as a list (built by the sparse RMSProp step)
+    int *tcount;                // its length
     int *status;
     int R;
     int form;
@@ -307,11 +312,12 @@ struct RenderParams {
 
 // March state written by plx_render_train and read by plx_render_backward_train.
 // Per ray: the number of compacted (occupied-cell) samples and, per chunk of 32
-// of them, the index of its first sample (plus one past the last sample); per
+// of them, the sample-index range [first, last + 1) that holds them; per
 // chunk a float4 that first holds the chunk's local colour and transmittance
 // product (C_loc, P) and, after the per-ray combine, the remaining colour after
 // the chunk and the transmittance before it (R_after, T_before); a flag for
-// chunks with positive density; and the flat list of (ray, chunk) work items.
+// chunks with positive density; the flat list of (ray, chunk) work items; and,
+// when sample indices fit in 16 bits, each chunk's 32 sample indices.
 struct MarchHeader {
     uint32_t magic;
     int32_t max_chunks;
@@ -328,7 +334,9 @@ constexpr uint32_t kMarchMagic = 0x53584c50u;
 enum : int32_t { kMarchChunked = 1, kMarchRecompute = 2 };
 
 struct MarchLayout {
-    size_t hdr_off, nocc_off, first_off, items_off, part_off, live_off, total;
+    size_t hdr_off, nocc_off, first_off, items_off, part_off, live_off, samp_off, total;
+    // the plan stores each chunk's sample indices (uint16) when every index fits
+    static bool store_samples(int max_chunks) { return (int64_t)max_chunks * 32 <= 65536; }
     static size_t round256(size_t b) { return (b + 255) & ~size_t(255); }
     static MarchLayout make(int64_t n, int max_chunks) {
         MarchLayout L;
@@ -336,10 +344,11 @@ struct MarchLayout {
         L.hdr_off = 0;
         L.nocc_off = 256;
         L.first_off = L.nocc_off + round256(size_t(n) * 4);
-        L.items_off = L.first_off + round256(size_t(n) * size_t(max_chunks + 1) * 4);
+        L.items_off = L.first_off + round256(slots * 8);
         L.part_off = L.items_off + round256(slots * 8);
         L.live_off = L.part_off + round256(slots * 16);
-        L.total = L.live_off + round256(slots);
+        L.samp_off = L.live_off + round256(slots);
+        L.total = L.samp_off + (store_samples(max_chunks) ? round256(slots * 64) : 0);
         return L;
     }
 };
@@ -347,10 +356,11 @@ struct MarchLayout {
 struct MarchPtrs {
     MarchHeader *hdr;
     int32_t *n_occ;   // [n] compacted samples per ray
-    int32_t *first;   // [n][max_chunks + 1] first sample of each chunk, then one past the last sample
+    int2 *range;      // [n][max_chunks] the sample-index range [first, last + 1) of each chunk
     int2 *items;      // [total_items] (ray, chunk)
     float4 *part;     // [n][max_chunks] (C_loc, P), then (R_after, T_before)
     uint8_t *live;    // [n][max_chunks] 1 if any sample of the chunk has positive density
+    uint16_t *samp;   // [n][max_chunks][32] the chunk's sample indices, or null (then chunks rescan)
     int max_chunks;
 };
 

@@ -1,6 +1,8 @@
 // plx_optim.cu -- the kernels around the renderer: the cell-occupancy mask
 // used for empty-space skipping, BF16-SH packing, the total-variation gradient
 // (Sec. 3.4, Supp. A.1) and the RMSProp update (Sec. 3.4).
+#include <algorithm>
+
 #include "plx_internal.cuh"
 
 namespace plx {
@@ -76,58 +78,59 @@ cudaError_t launch_pack_bf16(const GridView &g, uint16_t *rows_h, cudaStream_t s
 //   missing neighbour (NULL or outside): density 0, SH = V_d(v).
 // Each segment is split over kTvParts CTAs so short and long runs both fill the GPU.
 constexpr int kTvThreads = 256;
-constexpr int kTvParts = 8;
+constexpr int kTvParts = 16;
 
 __device__ __forceinline__ float4 ld4(const float *p) { return __ldg(reinterpret_cast<const float4 *>(p)); }
 
 __device__ __forceinline__ float comp(const float4 &v, int c) { return c == 0 ? v.x : c == 1 ? v.y : c == 2 ? v.z : v.w; }
 
-__device__ __forceinline__ void tv_node(const GridView &g, int32_t rs, const int32_t rn[3], float scale, float lam_sigma,
-                                        float lam_sh, float *__restrict__ grad, float &loss_acc) {
-#pragma unroll 1
-    for (int q = 0; q < 7; ++q) {
-        const float4 z4 = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
-        const float4 self4 = rs >= 0 ? ld4(g.rows + (int64_t)rs * kRowF + 4 * q) : z4;
-        float4 nb4[3];
+// TV (Sec. 3.4; Supp. A.1) of one float4 quarter q (< 7) of one node: per value d of the quarter,
+// D_a = (V_d(n + e_a) - V_d(n)) R/256, t = sqrt(sum_a D_a^2), loss += lam_d t, and the gradient
+// lam_d (R/256) D_a / t to the +a neighbour and minus its sum to the node (0 when t = 0).  A missing
+// neighbour (NULL or outside) has density 0 and SH equal to the node's own (no gradient for it).
+__device__ __forceinline__ void tv_quarter(const GridView &g, int32_t rs, const int32_t rn[3], int q, float scale,
+                                           float lam_sigma, float lam_sh, float *__restrict__ grad,
+                                           float &loss_acc) {
+    const float4 z4 = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+    const float4 self4 = rs >= 0 ? ld4(g.rows + (int64_t)rs * kRowF + 4 * q) : z4;
+    float4 nb4[3];
 #pragma unroll
-        for (int a = 0; a < 3; ++a) nb4[a] = rn[a] >= 0 ? ld4(g.rows + (int64_t)rn[a] * kRowF + 4 * q) : z4;
-        float gs[4], gn[3][4];
+    for (int a = 0; a < 3; ++a) nb4[a] = rn[a] >= 0 ? ld4(g.rows + (int64_t)rn[a] * kRowF + 4 * q) : z4;
+    float gs[4], gn[3][4];
 #pragma unroll
-        for (int c = 0; c < 4; ++c) {
-            const int d = 4 * q + c;
-            const float lam = d == 0 ? lam_sigma : lam_sh;
-            const float self = comp(self4, c);
-            float D[3];
+    for (int c = 0; c < 4; ++c) {
+        const int d = 4 * q + c;
+        const float lam = d == 0 ? lam_sigma : lam_sh;
+        const float self = comp(self4, c);
+        float D[3];
 #pragma unroll
-            for (int a = 0; a < 3; ++a) {
-                const float nv = rn[a] >= 0 ? comp(nb4[a], c) : (d == 0 ? 0.0f : self);
-                D[a] = (nv - self) * scale;
-            }
-            const float t = sqrtf(D[0] * D[0] + D[1] * D[1] + D[2] * D[2]);
-            loss_acc = fmaf(lam, t, loss_acc);
-            const float k = t > 0.0f ? lam * scale / t : 0.0f;
-            float acc = 0.0f;
-#pragma unroll
-            for (int a = 0; a < 3; ++a) {
-                gn[a][c] = D[a] * k;
-                if (rn[a] >= 0 || d == 0) acc -= D[a];
-            }
-            gs[c] = acc * k;
+        for (int a = 0; a < 3; ++a) {
+            const float nv = rn[a] >= 0 ? comp(nb4[a], c) : (d == 0 ? 0.0f : self);
+            D[a] = (nv - self) * scale;
         }
+        const float t = sqrtf(D[0] * D[0] + D[1] * D[1] + D[2] * D[2]);
+        loss_acc = fmaf(lam, t, loss_acc);
+        const float k = t > 0.0f ? lam * scale / t : 0.0f;
+        float acc = 0.0f;
 #pragma unroll
-        for (int a = 0; a < 3; ++a)
-            if (rn[a] >= 0)
-                atomicAdd(reinterpret_cast<float4 *>(grad + (int64_t)rn[a] * kRowF + 4 * q),
-                          make_float4(gn[a][0], gn[a][1], gn[a][2], gn[a][3]));
-        if (rs >= 0)
-            atomicAdd(reinterpret_cast<float4 *>(grad + (int64_t)rs * kRowF + 4 * q), make_float4(gs[0], gs[1], gs[2], gs[3]));
+        for (int a = 0; a < 3; ++a) {
+            gn[a][c] = D[a] * k;
+            if (rn[a] >= 0 || d == 0) acc -= D[a];
+        }
+        gs[c] = acc * k;
     }
-    if (rs >= 0) mark_touched(g, rs);
 #pragma unroll
     for (int a = 0; a < 3; ++a)
-        if (rn[a] >= 0) mark_touched(g, rn[a]);
+        if (rn[a] >= 0)
+            atomicAdd(reinterpret_cast<float4 *>(grad + (int64_t)rn[a] * kRowF + 4 * q),
+                      make_float4(gn[a][0], gn[a][1], gn[a][2], gn[a][3]));
+    if (rs >= 0)
+        atomicAdd(reinterpret_cast<float4 *>(grad + (int64_t)rs * kRowF + 4 * q), make_float4(gs[0], gs[1], gs[2], gs[3]));
 }
 
+// A warp takes 32 consecutive selected nodes: lane l reads the index of node l and of its +x, +y, +z
+// neighbours; nodes with no occupied row among the four are skipped; the others are processed four
+// at a time with 8 lanes each (one float4 quarter per lane), so a node's rows take one round trip.
 __global__ void __launch_bounds__(kTvThreads) tv_kernel(GridView g, const int64_t *__restrict__ seg_start,
                                                         const int64_t *__restrict__ seg_len, int64_t n_seg,
                                                         float lam_sigma, float lam_sh, float *__restrict__ grad,
@@ -135,28 +138,68 @@ __global__ void __launch_bounds__(kTvThreads) tv_kernel(GridView g, const int64_
     const int64_t R = g.R;
     const int64_t N = R * R * R;
     const float scale = (float)R / 256.0f;
+    const int lane = threadIdx.x & 31;
+    const int q = lane & 7;
+    const int grp = lane >> 3;
+    const int wid = threadIdx.x >> 5;
+    constexpr int kWarps = kTvThreads / 32;
     float loss_acc = 0.0f;
     for (int64_t item = blockIdx.x; item < n_seg * kTvParts; item += gridDim.x) {
         const int64_t sg = item / kTvParts;
         const int part = (int)(item % kTvParts);
         const int64_t start = seg_start[sg];
         const int64_t len = seg_len[sg];
-        for (int64_t off = (int64_t)part * kTvThreads + threadIdx.x; off < len; off += (int64_t)kTvParts * kTvThreads) {
+        for (int64_t off0 = ((int64_t)part * kWarps + wid) * 32; off0 < len; off0 += (int64_t)kTvParts * kWarps * 32) {
+            const int64_t off = off0 + lane;
             const int64_t n = start + off;
-            if (n < 0 || n >= N) continue;
-            const int64_t i = n / (R * R), j = (n / R) % R, k = n % R;
-            const int32_t rs = row_of(g, n);
-            int32_t rn[3];
-            rn[0] = i + 1 < R ? row_of(g, n + R * R) : -1;
-            rn[1] = j + 1 < R ? row_of(g, n + R) : -1;
-            rn[2] = k + 1 < R ? row_of(g, n + 1) : -1;
-            if (rs < 0 && rn[0] < 0 && rn[1] < 0 && rn[2] < 0) continue;
-            tv_node(g, rs, rn, scale, lam_sigma, lam_sh, grad, loss_acc);
+            // (i, j, k) of the warp's first node by one division, then carried lane by lane
+            const int64_t n0 = start + off0;
+            int64_t i = 0, j = 0, k = 0;
+            if (n0 >= 0 && n0 < N) {
+                i = n0 / (R * R);
+                const int64_t rem = n0 - i * R * R;
+                j = rem / R;
+                k = rem - j * R + lane;
+                while (k >= R) {
+                    k -= R;
+                    if (++j == R) {
+                        j = 0;
+                        ++i;
+                    }
+                }
+            }
+            int32_t rs = -1, rn[3] = {-1, -1, -1};
+            if (off < len && n0 >= 0 && n >= 0 && n < N) {
+                rs = row_of(g, n);
+                rn[0] = i + 1 < R ? row_of(g, n + R * R) : -1;
+                rn[1] = j + 1 < R ? row_of(g, n + R) : -1;
+                rn[2] = k + 1 < R ? row_of(g, n + 1) : -1;
+            }
+            unsigned mask = __ballot_sync(kFull, rs >= 0 || rn[0] >= 0 || rn[1] >= 0 || rn[2] >= 0);
+            while (mask) {  // uniform
+                const int cnt = __popc(mask);
+                const bool active = grp < cnt;
+                const int src = active ? __fns(mask, 0, grp + 1) : 0;
+                const int32_t ms = __shfl_sync(kFull, rs, src);
+                int32_t mn[3];
+#pragma unroll
+                for (int a = 0; a < 3; ++a) mn[a] = __shfl_sync(kFull, rn[a], src);
+                if (active && q < 7) {
+                    tv_quarter(g, ms, mn, q, scale, lam_sigma, lam_sh, grad, loss_acc);
+                    if (q == 0) {
+                        if (ms >= 0) mark_touched(g, ms);
+#pragma unroll
+                        for (int a = 0; a < 3; ++a)
+                            if (mn[a] >= 0) mark_touched(g, mn[a]);
+                    }
+                }
+                for (int k = 0; k < 4 && mask; ++k) mask &= mask - 1u;
+            }
         }
     }
     if (loss) {
         loss_acc = warp_sum(loss_acc);
-        if ((threadIdx.x & 31) == 0 && loss_acc != 0.0f) atomicAdd(loss, loss_acc);
+        if (lane == 0 && loss_acc != 0.0f) atomicAdd(loss, loss_acc);
     }
 }
 
@@ -177,19 +220,15 @@ cudaError_t launch_tv(const GridView &g, const int64_t *seg_start, const int64_t
 // which the scattered rows need to reach DRAM efficiently.  Entries with a zero
 // gradient keep x and v; a row with any update is re-packed into its BF16-SH
 // form when the grid has one.
-__device__ __forceinline__ void rms_quarter(int64_t r, int q, float *__restrict__ rows, uint16_t *__restrict__ rows_h,
-                                            float *__restrict__ grad, float *__restrict__ v, float lr_sigma, float lr_sh,
-                                            float beta, float eps, bool active) {
-    float4 g4 = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
-    if (active && q < 7) g4 = reinterpret_cast<const float4 *>(grad + r * kRowF)[q];
+// RMSProp (Sec. 3.4) on one float4 quarter q (< 7) of a row: for every entry with g != 0,
+// v <- beta v + (1 - beta) g^2, x <- x - lr g / (sqrt(v) + eps), then g <- 0; the BF16-SH
+// shadow of the quarter is refreshed.  g4, x4, v4 were loaded by the caller.
+__device__ __forceinline__ void rms_update(int64_t r, int q, float4 g4, float4 x4, float4 v4, float *__restrict__ rows,
+                                           uint16_t *__restrict__ rows_h, float *__restrict__ grad,
+                                           float *__restrict__ v, float lr_sigma, float lr_sh, float beta,
+                                           float eps) {
     const bool nz = g4.x != 0.0f || g4.y != 0.0f || g4.z != 0.0f || g4.w != 0.0f;
-    const unsigned grp = __ballot_sync(kFull, nz);
-    const int lane = threadIdx.x & 31;
-    const bool row_any = (grp >> (lane & ~7)) & 0xffu;
-    if (!active || !row_any || q == 7) return;
-    float4 *xp = reinterpret_cast<float4 *>(rows + r * kRowF) + q;
-    float4 *vp = reinterpret_cast<float4 *>(v + r * kRowF) + q;
-    float4 x4 = *xp, v4 = *vp;
+    if (!nz) return;
     float *xe = &x4.x, *ve = &v4.x;
     const float *ge = &g4.x;
 #pragma unroll
@@ -202,9 +241,9 @@ __device__ __forceinline__ void rms_quarter(int64_t r, int q, float *__restrict_
             xe[c] = xe[c] - lr * gg / (sqrtf(vv) + eps);
         }
     }
-    *xp = x4;
-    *vp = v4;
-    if (nz) reinterpret_cast<float4 *>(grad + r * kRowF)[q] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+    reinterpret_cast<float4 *>(rows + r * kRowF)[q] = x4;
+    reinterpret_cast<float4 *>(v + r * kRowF)[q] = v4;
+    reinterpret_cast<float4 *>(grad + r * kRowF)[q] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
     if (rows_h) {
         // column col sits in BF16 slot col + 1 (SH), density bits in slots 0-1
         uint16_t *hp = rows_h + r * kRowH;
@@ -219,27 +258,75 @@ __device__ __forceinline__ void rms_quarter(int64_t r, int q, float *__restrict_
     }
 }
 
-__global__ void __launch_bounds__(256) rmsprop_kernel(GridView g, float *__restrict__ rows, uint16_t *__restrict__ rows_h,
-                                                      float *__restrict__ grad, float *__restrict__ v, float lr_sigma,
-                                                      float lr_sh, float beta, float eps, int sparse, int64_t n_words) {
+// Sparse mode, pass 1: the rows marked in the touched bitmask, as a list, and the mask cleared.  A
+// warp takes 32 mask words at a time; the order of the list does not matter (rows update independently).
+__global__ void __launch_bounds__(256) rms_compact_kernel(GridView g, int64_t n_words) {
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t n_warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t w0 = warp * 32; w0 < n_words; w0 += n_warps * 32) {
+        const int64_t w = w0 + lane;
+        uint32_t word = 0u;
+        if (w < n_words) {
+            word = g.touched[w];
+            if (word) g.touched[w] = 0u;
+            const int64_t left = g.M - w * 32;  // >= 1
+            if (left < 32) word &= (1u << left) - 1u;
+        }
+        const int c = __popc(word);
+        int incl = c;
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+            const int t = __shfl_up_sync(kFull, incl, off);
+            if (lane >= off) incl += t;
+        }
+        const int total = __shfl_sync(kFull, incl, 31);
+        int base = 0;
+        if (lane == 0 && total) base = atomicAdd(g.tcount, total);
+        base = __shfl_sync(kFull, base, 0) + incl - c;
+        while (word) {
+            const int b = __ffs(word) - 1;
+            word &= word - 1u;
+            g.tlist[base++] = (int32_t)(w * 32 + b);
+        }
+    }
+}
+
+// Pass 2: rows from the list (sparse) or all rows (dense).  A warp takes 32 rows at a time, 8 lanes per
+// row (quarters 0..6, lane 7 idle), two groups of 4 rows per round so six float4 loads are in flight.
+template <bool SPARSE>
+__global__ void __launch_bounds__(256) rms_apply_kernel(GridView g, float *__restrict__ rows,
+                                                        uint16_t *__restrict__ rows_h, float *__restrict__ grad,
+                                                        float *__restrict__ v, float lr_sigma, float lr_sh, float beta,
+                                                        float eps) {
     const int lane = threadIdx.x & 31;
     const int q = lane & 7;
     const int grp = lane >> 3;
-    for (int64_t w = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); w < n_words;
-         w += (int64_t)gridDim.x * (blockDim.x >> 5)) {
-        const uint32_t word = g.touched[w];
-        uint32_t mask = sparse ? word : 0xffffffffu;
-        const int64_t left = g.M - w * 32;  // rows beyond M in the last word
-        if (left < 32) mask &= (1u << left) - 1u;
-        __syncwarp();
-        if (lane == 0 && word) g.touched[w] = 0u;  // both modes leave the mask clear
-        while (mask) {  // uniform
-            const int n = __popc(mask);
-            const bool active = grp < n;
-            const int bit = active ? __fns(mask, 0, grp + 1) : 0;
-            rms_quarter(w * 32 + bit, q, rows, rows_h, grad, v, lr_sigma, lr_sh, beta, eps, active);
-            // drop the (up to) four rows just handled
-            for (int k = 0; k < 4 && mask; ++k) mask &= mask - 1;
+    const int64_t total = SPARSE ? (int64_t)*g.tcount : g.M;
+    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t n_warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t base = warp * 32; base < total; base += n_warps * 32) {
+        const int64_t li = base + lane;
+        const int32_t mine = li < total ? (SPARSE ? g.tlist[li] : (int32_t)li) : -1;
+#pragma unroll 1
+        for (int sub = 0; sub < 8; sub += 2) {
+            const int32_t r0 = __shfl_sync(kFull, mine, 4 * sub + grp);
+            const int32_t r1 = __shfl_sync(kFull, mine, 4 * (sub + 1) + grp);
+            if (q == 7) continue;
+            const float4 z = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+            float4 g0 = z, x0 = z, v0 = z, g1 = z, x1 = z, v1 = z;
+            if (r0 >= 0) {
+                g0 = reinterpret_cast<const float4 *>(grad + (int64_t)r0 * kRowF)[q];
+                x0 = reinterpret_cast<const float4 *>(rows + (int64_t)r0 * kRowF)[q];
+                v0 = reinterpret_cast<const float4 *>(v + (int64_t)r0 * kRowF)[q];
+            }
+            if (r1 >= 0) {
+                g1 = reinterpret_cast<const float4 *>(grad + (int64_t)r1 * kRowF)[q];
+                x1 = reinterpret_cast<const float4 *>(rows + (int64_t)r1 * kRowF)[q];
+                v1 = reinterpret_cast<const float4 *>(v + (int64_t)r1 * kRowF)[q];
+            }
+            if (r0 >= 0) rms_update(r0, q, g0, x0, v0, rows, rows_h, grad, v, lr_sigma, lr_sh, beta, eps);
+            if (r1 >= 0) rms_update(r1, q, g1, x1, v1, rows, rows_h, grad, v, lr_sigma, lr_sh, beta, eps);
         }
     }
 }
@@ -248,10 +335,25 @@ cudaError_t launch_rmsprop(const GridView &g, float *rows, uint16_t *rows_h, flo
                            float lr_sh, float beta, float eps, int sparse, cudaStream_t s) {
     const int64_t n_words = (g.M + 31) / 32;
     if (n_words == 0) return cudaSuccess;
-    int64_t blocks = (n_words + 7) / 8;
-    if (blocks > 152 * 64) blocks = 152 * 64;
-    rmsprop_kernel<<<(unsigned)blocks, 256, 0, s>>>(g, rows, rows_h, grad, v, lr_sigma, lr_sh, beta, eps, sparse,
-                                                    n_words);
+    int sms = 152;
+    {
+        int dev = 0;
+        if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    }
+    const int64_t apply_blocks = std::min<int64_t>((g.M + 255) / 256, (int64_t)sms * 8);
+    if (sparse) {
+        cudaError_t e = cudaMemsetAsync(g.tcount, 0, sizeof(int), s);
+        if (e != cudaSuccess) return e;
+        const int64_t blocks = std::min<int64_t>((n_words + 255) / 256, (int64_t)sms * 8);
+        rms_compact_kernel<<<(unsigned)blocks, 256, 0, s>>>(g, n_words);
+        rms_apply_kernel<true><<<(unsigned)apply_blocks, 256, 0, s>>>(g, rows, rows_h, grad, v, lr_sigma, lr_sh,
+                                                                      beta, eps);
+    } else {
+        rms_apply_kernel<false><<<(unsigned)apply_blocks, 256, 0, s>>>(g, rows, rows_h, grad, v, lr_sigma, lr_sh,
+                                                                       beta, eps);
+        cudaError_t e = cudaMemsetAsync(g.touched, 0, (size_t)n_words * 4, s);
+        if (e != cudaSuccess) return e;
+    }
     return cudaGetLastError();
 }
 

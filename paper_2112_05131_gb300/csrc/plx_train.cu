@@ -7,9 +7,9 @@
 // rays set the kernel time while most SMs idle.  Here every chunk of 32
 // compacted samples of every ray is one work item of equal cost:
 //
-//   plan     (warp per ray)    compacts the ray's samples against the
-//                              occupancy mask, records where each chunk of 32
-//                              starts, and appends its (ray, chunk) items;
+//   plan     (CTA per ray)     compacts the ray's samples against the
+//                              occupancy mask, records the sample range of each
+//                              chunk of 32, and appends its (ray, chunk) items;
 //   chunks   (one resident wave, warps stride over the items)
 //                              gathers a chunk and composites it from T = 1:
 //                              local colour C_loc and transmittance product P;
@@ -58,55 +58,124 @@ int sm_count() {
 __global__ void march_header_kernel(MarchHeader *dst, MarchHeader v) { *dst = v; }
 
 // ---------------------------------------------------------------------------- plan
+// One CTA per ray: its kPlanWarps warps test interleaved spans of 256 candidates (span q by warp
+// q mod kPlanWarps, candidate q 256 + 32 j + lane as in the other marches), keeping each span's
+// ballot masks in shared memory; a prefix over the spans' counts then gives every occupied sample its
+// rank, so a long ray is planned by four warps at once.  Spans are handled kPlanMaxSpans at a time.
+constexpr int kPlanMaxSpans = 64;
+constexpr int kSpan = 32 * kCand;  // candidates tested by one warp at a time
+
 __global__ void __launch_bounds__(kPlanWarps * 32) march_plan_kernel(GridView g, const float *__restrict__ ro,
                                                                      const float *__restrict__ rd, int64_t n,
                                                                      RenderParams p, MarchPtrs st) {
+    __shared__ uint32_t s_mask[kPlanMaxSpans * kCand];
+    __shared__ int s_cnt[kPlanMaxSpans + 1];
+    __shared__ int s_last;
     const int lane = threadIdx.x & 31;
-    const int64_t ray = (int64_t)blockIdx.x * kPlanWarps + (threadIdx.x >> 5);
-    if (ray >= n) return;  // uniform per warp
+    const int wid = threadIdx.x >> 5;
+    const unsigned lt = (1u << lane) - 1u;
+    const int64_t ray = blockIdx.x;
     const RaySetup rs = ray_setup(g, ro, rd, ray);
     const int mc = st.max_chunks;
-    int32_t *first = st.first + ray * (mc + 1);
-    const unsigned lt = (1u << lane) - 1u;
-    int n_occ = 0, last = -1;
-    if (rs.hit) {
-        // test_candidate admits at most max_chunks * 32 samples, so rank / 32 < max_chunks
-        for (int next = 0;; next += 32 * kCand) {
+    int2 *range = st.range + ray * mc;
+    uint16_t *samp = st.samp ? st.samp + ray * mc * 32 : nullptr;  // chunk k's samples at [32 k, 32 k + 32)
+    // candidates beyond (t_far - t_near) / delta + 2 are invalid, and test_candidate admits fewer than
+    // max_chunks * 32 (so every rank / 32 < max_chunks)
+    int L = 0;
+    if (rs.hit) L = (int)fminf((float)(mc * 32), ceilf((rs.tf.hi - rs.tn.hi) / p.delta) + 2.0f);
+    const int n_spans = (L + kSpan - 1) / kSpan;
+    if (threadIdx.x == 0) s_last = -1;
+    int n_occ = 0;
+    for (int w0 = 0; w0 < n_spans; w0 += kPlanMaxSpans) {
+        const int nw = min(kPlanMaxSpans, n_spans - w0);
+        // phase 1: masks and counts of this window's spans
+        for (int q = wid; q < nw; q += kPlanWarps) {
+            const int base = (w0 + q) * kSpan;
             Cand c[kCand];
 #pragma unroll
-            for (int j = 0; j < kCand; ++j) c[j] = test_candidate(g, rs, p, next + 32 * j + lane);
+            for (int j = 0; j < kCand; ++j) c[j] = test_candidate(g, rs, p, base + 32 * j + lane);
+            int cnt = 0;
 #pragma unroll
             for (int j = 0; j < kCand; ++j) {
                 const unsigned m = __ballot_sync(kFull, c[j].occ);
-                if (c[j].occ) {
-                    const int rank = n_occ + __popc(m & lt);
-                    if ((rank & 31) == 0) first[rank >> 5] = next + 32 * j + lane;
-                }
-                if (m) last = next + 32 * j + 31 - __clz((int)m);
-                n_occ += __popc(m);
+                if (lane == 0) s_mask[q * kCand + j] = m;
+                cnt += __popc(m);
             }
-            // valid candidates form a prefix of the sample indices
-            if (__ballot_sync(kFull, c[kCand - 1].valid) != kFull) break;
+            if (lane == 0) s_cnt[q] = cnt;
         }
+        __syncthreads();
+        // phase 2: exclusive prefix of the counts (from the ranks already given), and the last sample
+        if (wid == 0) {
+            int carry = n_occ;
+            for (int q0 = 0; q0 < nw; q0 += 32) {
+                const int q = q0 + lane;
+                const int c = q < nw ? s_cnt[q] : 0;
+                int incl = c;
+#pragma unroll
+                for (int off = 1; off < 32; off <<= 1) {
+                    const int v = __shfl_up_sync(kFull, incl, off);
+                    if (lane >= off) incl += v;
+                }
+                if (q < nw) s_cnt[q] = carry + incl - c;
+                const unsigned nz = __ballot_sync(kFull, c > 0);
+                if (nz && lane == 0) {
+                    const int ql = q0 + 31 - __clz((int)nz);  // last span with an occupied sample so far
+                    for (int j = kCand - 1; j >= 0; --j) {
+                        const unsigned m = s_mask[ql * kCand + j];
+                        if (m) {
+                            s_last = (w0 + ql) * kSpan + 32 * j + 31 - __clz((int)m);
+                            break;
+                        }
+                    }
+                }
+                carry += __shfl_sync(kFull, incl, 31);
+            }
+            if (lane == 0) s_cnt[nw] = carry;
+        }
+        __syncthreads();
+        // phase 3: every occupied sample of the window writes its chunk boundary and list entry
+        for (int q = wid; q < nw; q += kPlanWarps) {
+            const int base = (w0 + q) * kSpan;
+            int rank0 = s_cnt[q];
+#pragma unroll
+            for (int j = 0; j < kCand; ++j) {
+                const unsigned m = s_mask[q * kCand + j];
+                if ((m >> lane) & 1u) {
+                    const int rank = rank0 + __popc(m & lt);
+                    const int sidx = base + 32 * j + lane;
+                    if ((rank & 31) == 0) range[rank >> 5].x = sidx;
+                    if ((rank & 31) == 31) range[rank >> 5].y = sidx + 1;
+                    if (samp) samp[rank] = (uint16_t)sidx;
+                }
+                rank0 += __popc(m);
+            }
+        }
+        n_occ = s_cnt[nw];
+        __syncthreads();  // the next window reuses the shared arrays
     }
-    const int nch = (n_occ + 31) >> 5;
-    int base = 0;
-    if (lane == 0) {
-        first[nch] = last + 1;
+    if (threadIdx.x == 0) {
+        const int nch = (n_occ + 31) >> 5;
+        if (nch > 0) {
+            range[nch - 1].y = s_last + 1;
+            const int base = atomicAdd(&st.hdr->total_items, nch);
+            for (int k = 0; k < nch; ++k) st.items[base + k] = make_int2((int)ray, k);
+        }
         st.n_occ[ray] = n_occ;
-        if (nch > 0) base = atomicAdd(&st.hdr->total_items, nch);
     }
-    base = __shfl_sync(kFull, base, 0);
-    for (int k = lane; k < nch; k += 32) st.items[base + k] = make_int2((int)ray, k);
 }
 
-// The samples of item (ray, k): returns the count (lane i gets sample s if i < count), or -1 when
-// the rescan disagrees with the plan (reported; cannot happen for a deterministic occupancy test).
+// The samples of item (ray, k): returns the count (lane i gets sample s if i < count), read from the
+// plan's list when it stored one, else rescanned from the chunk's range; -1 when the rescan disagrees
+// with the plan (reported; cannot happen for a deterministic occupancy test).
 __device__ __forceinline__ int item_samples(const GridView &g, const RaySetup &rs, const RenderParams &p,
                                             const MarchPtrs &st, int64_t ray, int k, int *buf, int lane, int &s) {
-    const int32_t *first = st.first + ray * (st.max_chunks + 1);
     const int expect = min(32, st.n_occ[ray] - 32 * k);
-    const int cnt = scan_range(g, rs, p, first[k], first[k + 1], buf, lane);
+    if (st.samp) {  // the plan's own list
+        s = lane < expect ? (int)st.samp[(ray * st.max_chunks + k) * 32 + lane] : 0;
+        return expect;
+    }
+    const int2 r = st.range[ray * st.max_chunks + k];
+    const int cnt = scan_range(g, rs, p, r.x, r.y, buf, lane);
     s = lane < cnt ? buf[lane] : 0;
     __syncwarp();
     if (cnt != expect) {
@@ -299,7 +368,7 @@ cudaError_t launch_render_train(const GridView &g, const float *o, const float *
     if (e != cudaSuccess) return e;
     if (hdr.mode == kMarchRecompute) return launch_render(g, o, d, n, p, rgb, T_end, s);
     if (n == 0) return cudaSuccess;
-    march_plan_kernel<<<(unsigned)((n + kPlanWarps - 1) / kPlanWarps), kPlanWarps * 32, 0, s>>>(g, o, d, n, p, st);
+    march_plan_kernel<<<(unsigned)n, kPlanWarps * 32, 0, s>>>(g, o, d, n, p, st);
     const unsigned grid = chunk_grid(n, st.max_chunks);
     if (g.form == PLX_SH_F32)
         march_chunks_fwd_kernel<PLX_SH_F32><<<grid, kChunkWarps * 32, 0, s>>>(g, o, d, p, st);

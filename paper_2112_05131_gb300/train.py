@@ -18,8 +18,8 @@ import torch
 from .grid import ROW, Grid, RenderOpts, gen_rays, mse_grad
 
 # kernels one step enqueues with stop_thresh = 0: gen_rays, render_train (header, plan, chunks,
-# combine), mse, backward_train, tv, rmsprop
-LAUNCHES_PER_STEP = 10
+# combine), mse, backward_train, tv, rmsprop (compact, apply; sparse mode)
+LAUNCHES_PER_STEP = 11
 
 
 def lr_sigma(step: int, init: float = 30.0, final: float = 0.05, max_steps: int = 250000, delay_steps: int = 15000,

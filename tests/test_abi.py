@@ -63,8 +63,12 @@ def test_workspace_sizes(lib):
     d.n_rows = 4_000_000
     d.sh_form = 0
     ws = lib.plx_grid_workspace_bytes(ctypes.byref(d))
-    # status block + one bit per node + one bit per row, each rounded to 256 bytes
-    assert ws == 256 + 512 ** 3 // 8 + ((4_000_000 + 31) // 32 + 1) * 4 + (256 - ((4_000_000 + 31) // 32 + 1) * 4 % 256) % 256
+    # status block + one bit per node + one bit per row + a 4-byte list entry per row, each rounded to 256 bytes
+
+    def up(b):
+        return (b + 255) // 256 * 256
+
+    assert ws == 256 + up(512 ** 3 // 8) + up(((4_000_000 + 31) // 32 + 1) * 4) + up(4_000_000 * 4)
     assert ws % 256 == 0
     d.reso = 1
     assert lib.plx_grid_workspace_bytes(ctypes.byref(d)) == 0
