@@ -21,6 +21,7 @@ struct RaySetup {
     float og[3];   // FP32 grid-coordinate origin and direction, for the cheap candidate test
     float dg[3];
     float Y[9];    // SH basis at the direction
+    float feps;    // bound on |FP32 - exact| grid coordinate of any sample of the ray (see test_candidate)
     bool hit;
 };
 
@@ -36,6 +37,18 @@ __device__ __forceinline__ RaySetup ray_setup_od(const GridView &g, const float 
         rs.dg[a] = rs.d[a] * g.inv_h[a];
     }
     sh_basis(rs.d, rs.Y);
+    // The cheap test's coordinate x32 = fma(t32, dg, og) with t32 = fma(s, delta, t_near.hi) differs from
+    // the exact (o - lo + t d) / h by at most u (inv_h (3 |o - lo| + 5 t) + |x|), u = 2^-24: og carries
+    // 3 roundings, dg 2, t32 3 (t_near.lo, delta_lo, the fma), and the final fma 1.  Over the ray
+    // t <= t_far and |x| <= R; the margin is that bound plus a quarter.
+    float om = 0.0f, ih = 0.0f;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        om = fmaxf(om, fabsf(o[a] - g.lo[a]));
+        ih = fmaxf(ih, g.inv_h[a]);
+    }
+    const float tmax = rs.hit ? fabsf(rs.tf.hi) : 0.0f;
+    rs.feps = 1.25f * 5.9604645e-8f * (ih * (3.0f * om + 5.0f * tmax) + (float)g.R);
     return rs;
 }
 
@@ -232,12 +245,11 @@ struct Cand {
 
 // Is sample s inside the clipped ray (valid), and is its cell non-empty (occ)?
 // The answer must equal the double-float one exactly (it decides which samples
-// are marched).  Plain FP32 coordinates are within ~3e-4 of a cell of the
-// double-float ones (rounding of t_near, delta, the direction and the grid
-// scale, for R <= 2048); a candidate whose FP32 coordinate lies within kFaceEps
-// of a cell face on any axis, or whose t lies within kTEps of t_far, is
-// re-evaluated in double-float, so the cheap path is taken only where both agree.
-constexpr float kFaceEps = 2e-3f;
+// are marched).  Plain FP32 coordinates are within rs.feps of the exact ones
+// (the bound derived in ray_setup_od); a candidate whose FP32 coordinate lies
+// within rs.feps of a cell face or of the box on any axis, or whose t lies
+// within kTEps of t_far, is re-evaluated in double-float, so the cheap path is
+// taken only where both agree.
 
 __device__ __forceinline__ Cand test_candidate(const GridView &g, const RaySetup &rs, const RenderParams &p, int s) {
     Cand c;
@@ -249,12 +261,13 @@ __device__ __forceinline__ Cand test_candidate(const GridView &g, const RaySetup
     bool exact = fabsf(t32 - rs.tf.hi) <= kTEps;
     if (!exact && t32 > rs.tf.hi) return c;  // clearly past t_far
     int b[3];
-    const float rm1 = (float)(g.R - 1);
+    // near a cell face: the fraction within feps of 0 or 1; near the box: x within feps of 0 or R-1
+    const float half = 0.5f * (float)(g.R - 1);
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
         const float x = fmaf(t32, rs.dg[a], rs.og[a]);
         const float fl = floorf(x);
-        exact = exact || (x - fl) < kFaceEps || (fl + 1.0f - x) < kFaceEps || x < kFaceEps || x > rm1 - kFaceEps;
+        exact = exact || fabsf((x - fl) - 0.5f) > 0.5f - rs.feps || fabsf(x - half) > half - rs.feps;
         b[a] = (int)fl;
     }
     if (exact) {
@@ -268,7 +281,10 @@ __device__ __forceinline__ Cand test_candidate(const GridView &g, const RaySetup
         return c;
     }
     c.valid = true;
-    c.occ = cell_occupied(g, ((int64_t)b[0] * g.R + b[1]) * g.R + b[2]);
+    // here 0 <= b < R - 1 on every axis; the linear id fits 32 bits below R = 1291
+    const int64_t base = g.R <= 1290 ? (int64_t)((b[0] * g.R + b[1]) * g.R + b[2])
+                                     : ((int64_t)b[0] * g.R + b[1]) * g.R + b[2];
+    c.occ = cell_occupied(g, base);
     return c;
 }
 

@@ -71,110 +71,161 @@ __global__ void __launch_bounds__(kPlanWarps * 32) march_plan_kernel(GridView g,
     __shared__ uint32_t s_mask[kPlanMaxSpans * kCand];
     __shared__ int s_cnt[kPlanMaxSpans + 1];
     __shared__ int s_last;
+    __shared__ RaySetup s_rs;
     const int lane = threadIdx.x & 31;
     const int wid = threadIdx.x >> 5;
     const unsigned lt = (1u << lane) - 1u;
-    const int64_t ray = blockIdx.x;
-    const RaySetup rs = ray_setup(g, ro, rd, ray);
-    const int mc = st.max_chunks;
-    int2 *range = st.range + ray * mc;
-    uint16_t *samp = st.samp ? st.samp + ray * mc * 32 : nullptr;  // chunk k's samples at [32 k, 32 k + 32)
-    // candidates beyond (t_far - t_near) / delta + 2 are invalid, and test_candidate admits fewer than
-    // max_chunks * 32 (so every rank / 32 < max_chunks)
-    int L = 0;
-    if (rs.hit) L = (int)fminf((float)(mc * 32), ceilf((rs.tf.hi - rs.tn.hi) / p.delta) + 2.0f);
-    const int n_spans = (L + kSpan - 1) / kSpan;
-    if (threadIdx.x == 0) s_last = -1;
-    int n_occ = 0;
-    for (int w0 = 0; w0 < n_spans; w0 += kPlanMaxSpans) {
-        const int nw = min(kPlanMaxSpans, n_spans - w0);
-        // phase 1: masks and counts of this window's spans
-        for (int q = wid; q < nw; q += kPlanWarps) {
-            const int base = (w0 + q) * kSpan;
-            Cand c[kCand];
-#pragma unroll
-            for (int j = 0; j < kCand; ++j) c[j] = test_candidate(g, rs, p, base + 32 * j + lane);
-            int cnt = 0;
-#pragma unroll
-            for (int j = 0; j < kCand; ++j) {
-                const unsigned m = __ballot_sync(kFull, c[j].occ);
-                if (lane == 0) s_mask[q * kCand + j] = m;
-                cnt += __popc(m);
-            }
-            if (lane == 0) s_cnt[q] = cnt;
+    for (int64_t ray = blockIdx.x; ray < n; ray += gridDim.x) {  // uniform over the CTA
+        if (threadIdx.x == 0) {  // the ray's setup, once for the CTA
+            s_rs = ray_setup(g, ro, rd, ray);
+            s_last = -1;
         }
         __syncthreads();
-        // phase 2: exclusive prefix of the counts (from the ranks already given), and the last sample
-        if (wid == 0) {
-            int carry = n_occ;
-            for (int q0 = 0; q0 < nw; q0 += 32) {
-                const int q = q0 + lane;
-                const int c = q < nw ? s_cnt[q] : 0;
-                int incl = c;
+        const RaySetup rs = s_rs;
+        const int mc = st.max_chunks;
+        int2 *range = st.range + ray * mc;
+        uint16_t *samp = st.samp ? st.samp + ray * mc * 32 : nullptr;  // chunk k's samples at [32 k, 32 k + 32)
+        // candidates beyond (t_far - t_near) / delta + 2 are invalid, and test_candidate admits fewer than
+        // max_chunks * 32 (so every rank / 32 < max_chunks)
+        int L = 0;
+        if (rs.hit) L = (int)fminf((float)(mc * 32), ceilf((rs.tf.hi - rs.tn.hi) / p.delta) + 2.0f);
+        const int n_spans = (L + kSpan - 1) / kSpan;
+        int n_occ = 0;
+        for (int w0 = 0; w0 < n_spans; w0 += kPlanMaxSpans) {
+            const int nw = min(kPlanMaxSpans, n_spans - w0);
+            // phase 1: masks and counts of this window's spans
+            for (int q = wid; q < nw; q += kPlanWarps) {
+                const int base = (w0 + q) * kSpan;
+                Cand c[kCand];
 #pragma unroll
-                for (int off = 1; off < 32; off <<= 1) {
-                    const int v = __shfl_up_sync(kFull, incl, off);
-                    if (lane >= off) incl += v;
-                }
-                if (q < nw) s_cnt[q] = carry + incl - c;
-                const unsigned nz = __ballot_sync(kFull, c > 0);
-                if (nz && lane == 0) {
-                    const int ql = q0 + 31 - __clz((int)nz);  // last span with an occupied sample so far
-                    for (int j = kCand - 1; j >= 0; --j) {
-                        const unsigned m = s_mask[ql * kCand + j];
-                        if (m) {
-                            s_last = (w0 + ql) * kSpan + 32 * j + 31 - __clz((int)m);
-                            break;
-                        }
+                for (int j = 0; j < kCand; ++j) {
+                    const int sidx = base + 32 * j + lane;
+                    if (sidx < L) {
+                        c[j] = test_candidate(g, rs, p, sidx);
+                    } else {
+                        c[j].valid = c[j].occ = false;
                     }
                 }
-                carry += __shfl_sync(kFull, incl, 31);
-            }
-            if (lane == 0) s_cnt[nw] = carry;
-        }
-        __syncthreads();
-        // phase 3: every occupied sample of the window writes its chunk boundary and list entry
-        for (int q = wid; q < nw; q += kPlanWarps) {
-            const int base = (w0 + q) * kSpan;
-            int rank0 = s_cnt[q];
+                int cnt = 0;
 #pragma unroll
-            for (int j = 0; j < kCand; ++j) {
-                const unsigned m = s_mask[q * kCand + j];
-                if ((m >> lane) & 1u) {
-                    const int rank = rank0 + __popc(m & lt);
-                    const int sidx = base + 32 * j + lane;
-                    if ((rank & 31) == 0) range[rank >> 5].x = sidx;
-                    if ((rank & 31) == 31) range[rank >> 5].y = sidx + 1;
-                    if (samp) samp[rank] = (uint16_t)sidx;
+                for (int j = 0; j < kCand; ++j) {
+                    const unsigned m = __ballot_sync(kFull, c[j].occ);
+                    if (lane == 0) s_mask[q * kCand + j] = m;
+                    cnt += __popc(m);
                 }
-                rank0 += __popc(m);
+                if (lane == 0) s_cnt[q] = cnt;
             }
+            __syncthreads();
+            // phase 2: exclusive prefix of the counts (from the ranks already given), and the last sample
+            if (wid == 0) {
+                int carry = n_occ;
+                for (int q0 = 0; q0 < nw; q0 += 32) {
+                    const int q = q0 + lane;
+                    const int c = q < nw ? s_cnt[q] : 0;
+                    int incl = c;
+#pragma unroll
+                    for (int off = 1; off < 32; off <<= 1) {
+                        const int v = __shfl_up_sync(kFull, incl, off);
+                        if (lane >= off) incl += v;
+                    }
+                    if (q < nw) s_cnt[q] = carry + incl - c;
+                    const unsigned nz = __ballot_sync(kFull, c > 0);
+                    if (nz && lane == 0) {
+                        const int ql = q0 + 31 - __clz((int)nz);  // last span with an occupied sample so far
+                        for (int j = kCand - 1; j >= 0; --j) {
+                            const unsigned m = s_mask[ql * kCand + j];
+                            if (m) {
+                                s_last = (w0 + ql) * kSpan + 32 * j + 31 - __clz((int)m);
+                                break;
+                            }
+                        }
+                    }
+                    carry += __shfl_sync(kFull, incl, 31);
+                }
+                if (lane == 0) s_cnt[nw] = carry;
+            }
+            __syncthreads();
+            // phase 3: every occupied sample of the window writes its chunk boundary and list entry
+            for (int q = wid; q < nw; q += kPlanWarps) {
+                const int base = (w0 + q) * kSpan;
+                int rank0 = s_cnt[q];
+#pragma unroll
+                for (int j = 0; j < kCand; ++j) {
+                    const unsigned m = s_mask[q * kCand + j];
+                    if ((m >> lane) & 1u) {
+                        const int rank = rank0 + __popc(m & lt);
+                        const int sidx = base + 32 * j + lane;
+                        if ((rank & 31) == 0) range[rank >> 5].x = sidx;
+                        if ((rank & 31) == 31) range[rank >> 5].y = sidx + 1;
+                        if (samp) samp[rank] = (uint16_t)sidx;
+                    }
+                    rank0 += __popc(m);
+                }
+            }
+            n_occ = s_cnt[nw];
+            __syncthreads();  // the next window reuses the shared arrays
         }
-        n_occ = s_cnt[nw];
-        __syncthreads();  // the next window reuses the shared arrays
-    }
-    if (threadIdx.x == 0) {
-        const int nch = (n_occ + 31) >> 5;
-        if (nch > 0) {
-            range[nch - 1].y = s_last + 1;
-            const int base = atomicAdd(&st.hdr->total_items, nch);
-            for (int k = 0; k < nch; ++k) st.items[base + k] = make_int2((int)ray, k);
+        if (threadIdx.x == 0) {
+            const int nch = (n_occ + 31) >> 5;
+            if (nch > 0) {
+                range[nch - 1].y = s_last + 1;
+                const int base = atomicAdd(&st.hdr->total_items, nch);
+                for (int k = 0; k < nch; ++k) st.items[base + k] = make_int2((int)ray, k);
+            }
+            st.n_occ[ray] = n_occ;
         }
-        st.n_occ[ray] = n_occ;
+        __syncthreads();  // the next ray reuses the shared setup
     }
 }
 
-// The samples of item (ray, k): returns the count (lane i gets sample s if i < count), read from the
-// plan's list when it stored one, else rescanned from the chunk's range; -1 when the rescan disagrees
-// with the plan (reported; cannot happen for a deterministic occupancy test).
+// The inputs of one work item, loaded one item ahead so that their round trips overlap the
+// previous item's gather: the ray, its compacted-sample count, and this lane's sample index when
+// the plan stored the chunk's list.
+struct ItemIn {
+    int ray, k;  // ray -1: past the end of the list
+    float o[3], d[3];
+    int n_occ;
+    int s;
+};
+
+__device__ __forceinline__ int2 item_at(const MarchPtrs &st, int it, int total) {
+    return it < total ? st.items[it] : make_int2(-1, 0);
+}
+
+__device__ __forceinline__ ItemIn load_item(const MarchPtrs &st, const float *__restrict__ ro,
+                                            const float *__restrict__ rd, int2 id, int lane) {
+    ItemIn r;
+    r.ray = id.x;
+    r.k = id.y;
+    r.n_occ = 0;
+    r.s = 0;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) r.o[a] = r.d[a] = 0.0f;
+    if (id.x >= 0) {
+        const int64_t ray = id.x;
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            r.o[a] = __ldg(ro + 3 * ray + a);
+            r.d[a] = __ldg(rd + 3 * ray + a);
+        }
+        r.n_occ = st.n_occ[ray];
+        // lanes past the chunk's count read unused slots of the list; their value is never used
+        if (st.samp) r.s = st.samp[(ray * st.max_chunks + id.y) * 32 + lane];
+    }
+    return r;
+}
+
+// The samples of the item: returns the count (lane i gets sample s if i < count), from the plan's list
+// when it stored one, else rescanned from the chunk's range; -1 when the rescan disagrees with the plan
+// (reported; cannot happen for a deterministic occupancy test).
 __device__ __forceinline__ int item_samples(const GridView &g, const RaySetup &rs, const RenderParams &p,
-                                            const MarchPtrs &st, int64_t ray, int k, int *buf, int lane, int &s) {
-    const int expect = min(32, st.n_occ[ray] - 32 * k);
-    if (st.samp) {  // the plan's own list
-        s = lane < expect ? (int)st.samp[(ray * st.max_chunks + k) * 32 + lane] : 0;
+                                            const MarchPtrs &st, const ItemIn &in, int *buf, int lane, int &s) {
+    const int expect = min(32, in.n_occ - 32 * in.k);
+    if (st.samp) {
+        s = lane < expect ? in.s : 0;
         return expect;
     }
-    const int2 r = st.range[ray * st.max_chunks + k];
+    const int2 r = st.range[(int64_t)in.ray * st.max_chunks + in.k];
     const int cnt = scan_range(g, rs, p, r.x, r.y, buf, lane);
     s = lane < cnt ? buf[lane] : 0;
     __syncwarp();
@@ -195,13 +246,18 @@ __global__ void __launch_bounds__(kChunkWarps * 32, kGatherBlocks) march_chunks_
     const int total = st.hdr->total_items;
     const int stride = gridDim.x * kChunkWarps;
     const int mc = st.max_chunks;
-    for (int it = blockIdx.x * kChunkWarps + wid; it < total; it += stride) {
-        const int2 item = st.items[it];
-        const int64_t ray = item.x;
-        const int k = item.y;
-        const RaySetup rs = ray_setup(g, ro, rd, ray);
+    int it = blockIdx.x * kChunkWarps + wid;
+    ItemIn cur = load_item(st, ro, rd, item_at(st, it, total), lane);
+    int2 id_next = item_at(st, it + stride, total);
+    for (; it < total; it += stride) {
+        const ItemIn nxt = load_item(st, ro, rd, id_next, lane);
+        id_next = item_at(st, it + 2 * stride, total);
+        const int64_t ray = cur.ray;
+        const int k = cur.k;
+        const RaySetup rs = ray_setup_od(g, cur.o, cur.d);
         int s;
-        const int cnt = item_samples(g, rs, p, st, ray, k, s_buf[wid], lane, s);
+        const int cnt = item_samples(g, rs, p, st, cur, s_buf[wid], lane, s);
+        cur = nxt;
         if (cnt < 0) continue;
         const bool valid = lane < cnt;
         float sig = 0.0f, col[3] = {0.0f, 0.0f, 0.0f};
@@ -309,14 +365,32 @@ __global__ void __launch_bounds__(kChunkWarps * 32, kGatherBlocks) march_chunks_
     const int total = h.total_items;
     const int stride = gridDim.x * kChunkWarps;
     const int mc = st.max_chunks;
-    for (int it = blockIdx.x * kChunkWarps + wid; it < total; it += stride) {
-        const int2 item = st.items[it];
-        const int64_t ray = item.x;
-        const int k = item.y;
-        if (!st.live[ray * mc + k]) continue;  // no positive density: no gradient anywhere in the chunk
-        const RaySetup rs = ray_setup(g, ro, rd, ray);
+    int it = blockIdx.x * kChunkWarps + wid;
+    // the items whose chunk has no positive density add nothing: skip them when fetching
+    auto next_live = [&](int from) {
+        int2 id = item_at(st, from, total);
+        while (id.x >= 0 && !st.live[(int64_t)id.x * mc + id.y]) {
+            from += stride;
+            id = item_at(st, from, total);
+        }
+        it = from;
+        return id;
+    };
+    int2 id = next_live(it);
+    int it_cur = it;
+    ItemIn cur = load_item(st, ro, rd, id, lane);
+    int2 id_next = next_live(it_cur + stride);
+    while (cur.ray >= 0) {
+        const ItemIn nxt = load_item(st, ro, rd, id_next, lane);
+        id_next = next_live(it + stride);
+        const int64_t ray = cur.ray;
+        const int k = cur.k;
+        const float4 q = st.part[ray * mc + k];  // (R_after, T_before)
+        const float gr[3] = {__ldg(grad_rgb + 3 * ray), __ldg(grad_rgb + 3 * ray + 1), __ldg(grad_rgb + 3 * ray + 2)};
+        const RaySetup rs = ray_setup_od(g, cur.o, cur.d);
         int s;
-        const int cnt = item_samples(g, rs, p, st, ray, k, s_buf[wid], lane, s);
+        const int cnt = item_samples(g, rs, p, st, cur, s_buf[wid], lane, s);
+        cur = nxt;
         if (cnt < 0) continue;
         const bool valid = lane < cnt;
         int32_t rr[8];
@@ -330,7 +404,6 @@ __global__ void __launch_bounds__(kChunkWarps * 32, kGatherBlocks) march_chunks_
             sig = fmaxf(acc[0], 0.0f);
             colour_of(acc, rs.Y, pre, col);
         }
-        const float4 q = st.part[ray * mc + k];  // (R_after, T_before)
         const Composite cp = composite(sig, valid, q.w, p, lane);
         const float w = cp.take ? cp.T * cp.alpha : 0.0f;
         const float Ra[3] = {q.x, q.y, q.z};
@@ -342,11 +415,7 @@ __global__ void __launch_bounds__(kChunkWarps * 32, kGatherBlocks) march_chunks_
             if (lane == 31) suf_ex = 0.0f;
             Rs[ch] = Ra[ch] + suf_ex;
         }
-        if (cp.take && sig > 0.0f) {
-            const float gr[3] = {__ldg(grad_rgb + 3 * ray), __ldg(grad_rgb + 3 * ray + 1),
-                                 __ldg(grad_rgb + 3 * ray + 2)};
-            scatter_sample(g, rr, ff, rs.Y, gr, pre, col, w, cp.Tn, Rs, p.delta, grad_rows);
-        }
+        if (cp.take && sig > 0.0f) scatter_sample(g, rr, ff, rs.Y, gr, pre, col, w, cp.Tn, Rs, p.delta, grad_rows);
     }
 }
 

@@ -51,6 +51,9 @@ class StepConfig:
     beta: float = 0.95
     eps: float = 1e-8
     sparse_rmsprop: bool = True
+    # TV on a second stream, concurrent with ray generation, forward, MSE and adjoint: it reads only
+    # rows (unchanged until RMSProp) and adds to the gradient with atomics; RMSProp waits for both
+    overlap_tv: bool = True
 
 
 class Trainer:
@@ -71,32 +74,46 @@ class Trainer:
         self.grad_rgb = torch.empty((n, 3), dtype=torch.float32, device=dev)
         self.loss = torch.zeros(1, dtype=torch.float32, device=dev)
         self.state = grid.new_march_state(n, cfg.opts)  # fits every batch of up to n rays
+        self.side = torch.cuda.Stream(device=dev) if cfg.overlap_tv else None
+        self._ev_start = torch.cuda.Event()
+        self._ev_tv = torch.cuda.Event()
 
     def step(self, pix: torch.Tensor, target: torch.Tensor, seg_start: Optional[torch.Tensor],
              seg_len: Optional[torch.Tensor], n_selected: int, lr_s: float, lr_h: float,
              events: Optional[List[torch.cuda.Event]] = None, stream=None):
-        """One optimisation step; `events`, if given, must hold 7 events recorded at the stage boundaries."""
+        """One optimisation step; `events`, if given, must hold 7 events recorded at the stage boundaries of
+        the main stream (with overlap_tv the TV stage there is only the wait for the side stream)."""
         g, c = self.grid, self.cfg
         n = pix.shape[0]
         o, d, rgb, grgb = self.o[:n], self.d[:n], self.rgb[:n], self.grad_rgb[:n]
+        main = stream if stream is not None else torch.cuda.current_stream()
+        do_tv = seg_start is not None and n_selected > 0
+        side = self.side if (do_tv and self.side is not None) else None
 
         def mark(i):
             if events is not None:
-                events[i].record(stream if stream is not None else torch.cuda.current_stream())
+                events[i].record(main)
 
+        if side is not None:  # TV starts after everything enqueued so far (the last RMSProp, the inputs)
+            self._ev_start.record(main)
+            side.wait_event(self._ev_start)
+            g.tv_grad(seg_start, seg_len, n_selected, c.lambda_tv_sigma, c.lambda_tv_sh, self.grad, stream=side)
+            self._ev_tv.record(side)
         mark(0)
-        gen_rays(self.cams, pix, self.W, self.H, o, d, stream=stream)
+        gen_rays(self.cams, pix, self.W, self.H, o, d, stream=main)
         mark(1)
-        g.render_train(o, d, c.opts, self.state, rgb, stream=stream)
+        g.render_train(o, d, c.opts, self.state, rgb, stream=main)
         mark(2)
-        mse_grad(rgb, target, grgb, self.loss, stream=stream)
+        mse_grad(rgb, target, grgb, self.loss, stream=main)
         mark(3)
-        g.render_backward_train(o, d, grgb, c.opts, self.state, self.grad, stream=stream)
+        g.render_backward_train(o, d, grgb, c.opts, self.state, self.grad, stream=main)
         mark(4)
-        if seg_start is not None and n_selected > 0:
-            g.tv_grad(seg_start, seg_len, n_selected, c.lambda_tv_sigma, c.lambda_tv_sh, self.grad, stream=stream)
+        if side is not None:
+            main.wait_event(self._ev_tv)
+        elif do_tv:
+            g.tv_grad(seg_start, seg_len, n_selected, c.lambda_tv_sigma, c.lambda_tv_sh, self.grad, stream=main)
         mark(5)
-        g.rmsprop_step(self.grad, self.v, lr_s, lr_h, c.beta, c.eps, sparse=c.sparse_rmsprop, stream=stream)
+        g.rmsprop_step(self.grad, self.v, lr_s, lr_h, c.beta, c.eps, sparse=c.sparse_rmsprop, stream=main)
         mark(6)
         return rgb
 
