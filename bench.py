@@ -215,14 +215,15 @@ def run_ours(args, world, rank, local):
                             int(sl.sum())))
     torch.cuda.synchronize()
 
-    def timed_loop(grid, K, Wm, per_stage=True):
-        tr = Trainer(grid, cams_t, W, H, StepConfig(batch=args.batch, opts=opts))
+    def timed_loop(grid, K, Wm, per_stage=True, overlap=True):
+        tr = Trainer(grid, cams_t, W, H, StepConfig(batch=args.batch, opts=opts, overlap=overlap))
         nb = len(dev_batches)
         for s in range(Wm):
             b = dev_batches[s % nb]
             tr.step(b[0], b[1], b[2], b[3], b[4], lr_sigma(s), lr_sh(s))
+        tr.finish()
         torch.cuda.synchronize()
-        evs = [[torch.cuda.Event(enable_timing=True) for _ in range(7)] for _ in range(K)] if per_stage else None
+        evs = [[torch.cuda.Event(enable_timing=True) for _ in range(8)] for _ in range(K)] if per_stage else None
         start, stop = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         barrier(world)
         torch.cuda.synchronize()
@@ -233,21 +234,27 @@ def run_ours(args, world, rank, local):
             b = dev_batches[(Wm + s) % nb]
             tr.step(b[0], b[1], b[2], b[3], b[4], lr_sigma(Wm + s), lr_sh(Wm + s),
                     events=evs[s] if per_stage else None)
+        tr.finish()  # the last step's update is inside the timed region
         stop.record(stream)
         torch.cuda.synchronize()
         clocks = clk.stop()
         barrier(world)
         ms = start.elapsed_time(stop)
         stages = None
-        if per_stage:
+        if per_stage:  # stage names: "serial|overlapped"; "-" marks an empty interval
+            names = [nm.split("|")[-1 if overlap else 0] for nm in Trainer.STAGES]
             stages = {name: statistics.mean(e[i].elapsed_time(e[i + 1]) for e in evs)
-                      for i, name in enumerate(Trainer.STAGES)}
+                      for i, name in enumerate(names) if name != "-"}
         grid.check()
         return ms, stages, clocks, tr
 
-    # ---- headline: FP32 rows
+    # ---- headline: FP32 rows, the overlapped step (three streams, deferred update)
     train32 = Grid.from_host(R, wl["train"].idx, wl["train"].rows)
-    ms32, st32, clocks, _ = timed_loop(train32, args.steps, args.warmup)
+    ms32, st_overlap, clocks, _ = timed_loop(train32, args.steps, args.warmup)
+    # the same steps in one stream, in order: per-stage times of the kernels alone
+    train_s = Grid.from_host(R, wl["train"].idx, wl["train"].rows)
+    ms_serial, st32, _, _ = timed_loop(train_s, args.steps, args.warmup, overlap=False)
+    del train_s
     ms32 = max_over_ranks(ms32, world)
     rays_total = sum_over_ranks(float(args.steps * args.batch), world)
     value = rays_total / (ms32 / 1e3)
@@ -264,7 +271,7 @@ def run_ours(args, world, rank, local):
                    "l2": "grid exceeds the 129 MB L2 and every step uses a new batch; no flush"},
         "gpu_launches": LAUNCHES_PER_STEP * args.steps,
         "clocks": clocks,
-        "stage_ms": st32,
+        "stage_ms": {"overlapped": st_overlap, "serial": st32, "serial_ms_per_step": ms_serial / args.steps},
     }
     del train32
     torch.cuda.empty_cache()
@@ -295,10 +302,11 @@ def extras(args, wl, dev_batches, cams_t, gt_grid, opts, timed_loop, st32, ms32)
     del train16
     torch.cuda.empty_cache()
 
-    # ---- roofline of the dominant kernel (algorithmic bytes from the node counts of the timed batches)
+    # ---- roofline of the dominant kernel, from the serial per-stage times and the algorithmic bytes of the
+    # timed batches (node and sample counts from plx_count_nodes, TV rows from the index volume)
     peak, peak_kind = load_peaks()
     train32 = Grid.from_host(R, wl["train"].idx, wl["train"].rows)
-    nodes = occ = 0
+    nodes = occ = samples = 0
     nb = len(dev_batches)
     K, Wm = args.steps, args.warmup
     for s in range(K):
@@ -307,13 +315,19 @@ def extras(args, wl, dev_batches, cams_t, gt_grid, opts, timed_loop, st32, ms32)
         c = train32.count_nodes(o, d, opts).sum(0).cpu().numpy()
         nodes += int(c[0])
         occ += int(c[1])
+        samples += int(c[2])
     nodes /= K
     occ /= K
+    samples /= K
     n = args.batch
-    fwd_bytes = n * (24 + 12) + 4 * nodes + 112 * occ
-    bwd_bytes = 2 * (4 * nodes + 112 * occ) + n * (24 + 12) + 2 * 112 * occ
-    # RMSProp: every touched row is read (gradient, value, state) and written back (112 bytes each),
-    # plus one bit per row of the touched mask; touched rows counted on the timed batches
+    # forward (chunks + combine): rays, colours, one index read per distinct node, one 112-byte row per
+    # distinct occupied node, and each sample's stored (sigma, pre) (16 B) and index (2 B)
+    fwd_bytes = n * (24 + 12) + 4 * nodes + 112 * occ + 18 * samples
+    # adjoint: rays and dL/dC, the stored per-sample values and indices, one index read per distinct node,
+    # and a read-modify-write of each distinct occupied row's 112-byte gradient
+    bwd_bytes = n * (24 + 12) + 18 * samples + 4 * nodes + 2 * 112 * occ
+    # RMSProp: every touched row's gradient, value and state read and written (6 x 112 B), the touched
+    # mask (1 bit per row) and the row list (4 B written, 4 B read per touched row)
     tr_count = Trainer(train32, cams_t, W, H, StepConfig(batch=args.batch, opts=opts))
     touched = []
     for s in range(min(K, 8)):
@@ -325,17 +339,39 @@ def extras(args, wl, dev_batches, cams_t, gt_grid, opts, timed_loop, st32, ms32)
         touched.append(int((tr_count.grad[:, :28] != 0).any(1).sum()))
         train32.rmsprop_step(tr_count.grad, tr_count.v, 0.0, 0.0, sparse=True)  # clears gradient and marks
     del tr_count
-    rms_bytes = float(np.mean(touched)) * 6 * 112 + train32.M / 8
-    per_launch = {"render": fwd_bytes, "render_backward": bwd_bytes, "rmsprop_step": rms_bytes}
+    rms_bytes = float(np.mean(touched)) * (6 * 112 + 8) + train32.M / 8
+    # TV: three index streams per selected node (self/+z, +y, +x), and for every distinct occupied row
+    # among the active nodes' self and +x/+y/+z, its 112 bytes read and its gradient read and written
+    idx_np = wl["train"].idx
+    tv_b = []
+    for s in range(min(K, 4)):
+        ss, sl = wl["batches"][(Wm + s) % nb][1], wl["batches"][(Wm + s) % nb][2]
+        sel = np.concatenate([np.arange(a0, a0 + l0) for a0, l0 in zip(ss, sl)])
+        i, j, k = sel // (R * R), (sel // R) % R, sel % R
+        rows = [idx_np[sel]]
+        rows.append(np.where(i + 1 < R, idx_np[np.minimum(sel + R * R, R ** 3 - 1)], -1))
+        rows.append(np.where(j + 1 < R, idx_np[np.minimum(sel + R, R ** 3 - 1)], -1))
+        rows.append(np.where(k + 1 < R, idx_np[np.minimum(sel + 1, R ** 3 - 1)], -1))
+        rows = np.stack(rows)
+        distinct = np.unique(rows[rows >= 0]).size
+        tv_b.append(12 * sel.size + 3 * 112 * distinct)
+    tv_bytes = float(np.mean(tv_b))
+    per_launch = {"render": fwd_bytes, "render_backward": bwd_bytes, "rmsprop_step": rms_bytes, "tv_grad": tv_bytes}
+    launches = {"render": "march_chunks_fwd + march_combine", "render_backward": "march_chunks_bwd",
+                "rmsprop_step": "rms_compact + rms_apply", "tv_grad": "tv_kernel"}
     dom = max(per_launch, key=lambda k: st32[k])
     ach = per_launch[dom] / (st32[dom] / 1e3) / 1e9
-    res["roofline"] = {"kernel": dom, "bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s",
-                       "frac": ach / peak, "peak_source": f"{peak_kind} hbm_gbs (STREAM-style copy)",
+    res["roofline"] = {"kernel": f"{dom} ({launches[dom]})", "bound": "hbm", "achieved": ach, "peak": peak,
+                       "unit": "GB/s", "frac": ach / peak,
+                       "peak_source": f"{peak_kind} hbm_gbs (STREAM-style copy), burst",
+                       "timing": "CUDA events around the stage on the launching stream, serial run",
                        "algorithmic_bytes_per_launch": per_launch[dom], "traffic": None}
     res["algorithmic"] = {"distinct_nodes_per_ray": nodes / n, "occupied_nodes_per_ray": occ / n,
+                          "marched_samples_per_ray": samples / n,
                           "touched_rows_per_step": float(np.mean(touched)),
                           "bytes_per_launch": per_launch,
-                          "GBps": {k: per_launch[k] / (st32[k] / 1e3) / 1e9 for k in per_launch}}
+                          "GBps": {k: per_launch[k] / (st32[k] / 1e3) / 1e9 for k in per_launch},
+                          "frac_of_peak": {k: per_launch[k] / (st32[k] / 1e3) / 1e9 / peak for k in per_launch}}
 
     # ---- end to end through the public API with host buffers (pinned), copies inside the timed region
     tr = Trainer(train32, cams_t, W, H, StepConfig(batch=args.batch, opts=opts))
@@ -365,11 +401,13 @@ def extras(args, wl, dev_batches, cams_t, gt_grid, opts, timed_loop, st32, ms32)
 
     for s in range(args.warmup):
         e2e_step(s)
+    tr.finish()
     torch.cuda.synchronize()
     a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     a.record(stream)
     for s in range(K):
         e2e_step(Wm + s)
+    tr.finish()
     b.record(stream)
     torch.cuda.synchronize()
     ms_e2e = a.elapsed_time(b)
@@ -485,6 +523,7 @@ def large_batch(args, wl, cams_t, gt_grid, opts, n=1 << 18, steps=8, warmup=3):
     for s in range(warmup):
         b = batches[s % 4]
         tr.step(b[0], b[1], b[2], b[3], b[4], lr_sigma(s), lr_sh(s))
+    tr.finish()
     stream = torch.cuda.current_stream()
     a, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     torch.cuda.synchronize()
@@ -492,6 +531,7 @@ def large_batch(args, wl, cams_t, gt_grid, opts, n=1 << 18, steps=8, warmup=3):
     for s in range(steps):
         b = batches[s % 4]
         tr.step(b[0], b[1], b[2], b[3], b[4], lr_sigma(warmup + s), lr_sh(warmup + s))
+    tr.finish()
     e.record(stream)
     torch.cuda.synchronize()
     ms = a.elapsed_time(e)

@@ -211,9 +211,22 @@ plx_status plx_render_train(const plx_grid *grid, const float *d_origins, const 
                             const plx_render_opts *opts, float *d_rgb, float *d_T_end, void *d_state,
                             size_t state_bytes, void *stream);
 
+/* plx_render_train in two calls: plx_march_plan writes the plan of these rays
+ * into d_state (reading only the index volume and the occupancy mask, never
+ * the rows, so it may run concurrently with calls that change rows, such as
+ * plx_rmsprop_step); plx_render_planned then marches the planned chunks and
+ * writes the colours.  plx_render_planned checks on the device that d_state
+ * holds a plan of these rays, this grid and these options; otherwise it writes
+ * nothing and plx_check then returns PLX_EDEVICE. */
+plx_status plx_march_plan(const plx_grid *grid, const float *d_origins, const float *d_dirs, int64_t n,
+                          const plx_render_opts *opts, void *d_state, size_t state_bytes, void *stream);
+plx_status plx_render_planned(const plx_grid *grid, const float *d_origins, const float *d_dirs, int64_t n,
+                              const plx_render_opts *opts, float *d_rgb, float *d_T_end, void *d_state,
+                              size_t state_bytes, void *stream);
+
 /* As plx_render_backward, for the rays, grid and options of the last
- * plx_render_train that wrote d_state, enqueued after it, before the grid's
- * rows change.  The kernel checks the state's header (ray buffers, grid rows,
+ * plx_render_train (or plx_render_planned) that used d_state, enqueued after
+ * it, before the grid's rows change.  The kernel checks the state's header (ray buffers, grid rows,
  * sizes, options) on the device; on a mismatch it adds nothing and plx_check
  * then returns PLX_EDEVICE. */
 plx_status plx_render_backward_train(const plx_grid *grid, const float *d_origins, const float *d_dirs, int64_t n,
@@ -250,11 +263,12 @@ plx_status plx_render_tiles(const plx_grid *const *grids, int32_t n_grids, const
                             const plx_tile *d_tiles, int64_t n_tiles, const plx_render_opts *opts, void *stream);
 
 /* Traffic accounting (a measurement aid, not part of the method): for each
- * ray, d_counts int64 [n][2] receives (a) the number of distinct lattice
+ * ray, d_counts int64 [n][3] receives (a) the number of distinct lattice
  * nodes that are corners of the ray's sampled cells having at least one
- * occupied corner, and (b) how many of those nodes are occupied, following the
- * same samples and early termination as plx_render.  (a) x 4 bytes of index
- * reads plus (b) x row bytes is the least a forward march must move. */
+ * occupied corner, (b) how many of those nodes are occupied, and (c) how many
+ * samples are marched (those in such cells), following the same samples and
+ * early termination as plx_render.  (a) x 4 bytes of index reads plus (b) x
+ * row bytes is the least a forward march must move. */
 plx_status plx_count_nodes(const plx_grid *grid, const float *d_origins, const float *d_dirs, int64_t n,
                            const plx_render_opts *opts, int64_t *d_counts, void *stream);
 

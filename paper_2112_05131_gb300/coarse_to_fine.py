@@ -109,6 +109,7 @@ def train(train_images: np.ndarray, cams: torch.Tensor, W: int, H: int, cfg: C2F
     for step in range(cfg.steps):
         if ups and step == ups[0]:
             ups.pop(0)
+            tr.finish()
             torch.cuda.synchronize()
             before = (grid.reso, grid.M)
             pruned = grid.prune(cfg.prune_tau, True)
@@ -123,6 +124,7 @@ def train(train_images: np.ndarray, cams: torch.Tensor, W: int, H: int, cfg: C2F
             t_stage = time.perf_counter()
         pix, tgt, ss, sl, nsel = batches.get(step, grid.reso)
         tr.step(pix, tgt, ss, sl, nsel, lr_sigma(step), lr_sh(step))
+    tr.finish()
     torch.cuda.synchronize()
     grid.check()
     if log is not None:

@@ -217,8 +217,8 @@ plx_status plx_check(const plx_grid *grid, void *stream) {
     if (code == plx::kDevBadTile)
         return fail(PLX_EDEVICE, "plx_render_tiles skipped a tile with an out-of-range scene or camera or a NULL image");
     if (code == plx::kDevStateMismatch)
-        return fail(PLX_EDEVICE, "plx_render_backward_train was given a march state that plx_render_train did not "
-                                 "write for these rays, this grid and these options; no gradient was added");
+        return fail(PLX_EDEVICE, "a training march was given a state that holds no plan of these rays, this grid and "
+                                 "these options; it wrote and added nothing");
     if (code != 0) return fail(PLX_EDEVICE, "device status %d", code);
     return PLX_OK;
 }
@@ -290,6 +290,7 @@ plx_status march_state(const plx_grid *grid, const float *d_origins, const float
     ptrs->part = reinterpret_cast<float4 *>(b + L.part_off);
     ptrs->live = reinterpret_cast<uint8_t *>(b + L.live_off);
     ptrs->samp = plx::MarchLayout::store_samples(p.max_chunks) ? reinterpret_cast<uint16_t *>(b + L.samp_off) : nullptr;
+    ptrs->vals = plx::MarchLayout::store_samples(p.max_chunks) ? reinterpret_cast<float4 *>(b + L.vals_off) : nullptr;
     ptrs->max_chunks = p.max_chunks;
     std::memset(hdr, 0, sizeof(*hdr));
     hdr->magic = plx::kMarchMagic;
@@ -326,6 +327,40 @@ plx_status plx_render_train(const plx_grid *grid, const float *d_origins, const 
     if (st != PLX_OK) return st;
     return cuda_status(plx::launch_render_train(grid->view, d_origins, d_dirs, n, p, ptrs, hdr, d_rgb, d_T_end,
                                                 static_cast<cudaStream_t>(stream)), "plx_render_train");
+}
+
+plx_status plx_march_plan(const plx_grid *grid, const float *d_origins, const float *d_dirs, int64_t n,
+                          const plx_render_opts *opts, void *d_state, size_t state_bytes, void *stream) {
+    plx_status st = check_grid(grid);
+    if (st == PLX_OK) st = check_opts(opts);
+    if (st != PLX_OK) return st;
+    if (n < 0 || n >= (int64_t(1) << 31)) return fail(PLX_EINVAL, "n out of range");
+    if (n > 0 && (!d_origins || !d_dirs)) return fail(PLX_EINVAL, "NULL ray buffer");
+    const plx::RenderParams p = make_params(grid, opts);
+    plx::MarchPtrs ptrs;
+    plx::MarchHeader hdr;
+    st = march_state(grid, d_origins, d_dirs, n, opts, p, d_state, state_bytes, &ptrs, &hdr);
+    if (st != PLX_OK) return st;
+    return cuda_status(plx::launch_march_plan(grid->view, d_origins, d_dirs, n, p, ptrs, hdr,
+                                              static_cast<cudaStream_t>(stream)), "plx_march_plan");
+}
+
+plx_status plx_render_planned(const plx_grid *grid, const float *d_origins, const float *d_dirs, int64_t n,
+                              const plx_render_opts *opts, float *d_rgb, float *d_T_end, void *d_state,
+                              size_t state_bytes, void *stream) {
+    plx_status st = check_grid(grid);
+    if (st == PLX_OK) st = check_opts(opts);
+    if (st != PLX_OK) return st;
+    if (n < 0 || n >= (int64_t(1) << 31)) return fail(PLX_EINVAL, "n out of range");
+    if (n > 0 && (!d_origins || !d_dirs || !d_rgb)) return fail(PLX_EINVAL, "NULL ray or output buffer");
+    if (grid->desc.sh_form == PLX_SH_F32 && grid->desc.n_rows > 0 && !grid->rows) return fail(PLX_EINVAL, "grid has no F32 rows");
+    const plx::RenderParams p = make_params(grid, opts);
+    plx::MarchPtrs ptrs;
+    plx::MarchHeader hdr;
+    st = march_state(grid, d_origins, d_dirs, n, opts, p, d_state, state_bytes, &ptrs, &hdr);
+    if (st != PLX_OK) return st;
+    return cuda_status(plx::launch_render_planned(grid->view, d_origins, d_dirs, n, p, ptrs, hdr, d_rgb, d_T_end,
+                                                  static_cast<cudaStream_t>(stream)), "plx_render_planned");
 }
 
 plx_status plx_render_backward_train(const plx_grid *grid, const float *d_origins, const float *d_dirs, int64_t n,

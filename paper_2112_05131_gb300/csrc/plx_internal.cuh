@@ -317,7 +317,9 @@ struct RenderParams {
 // product (C_loc, P) and, after the per-ray combine, the remaining colour after
 // the chunk and the transmittance before it (R_after, T_before); a flag for
 // chunks with positive density; the flat list of (ray, chunk) work items; and,
-// when sample indices fit in 16 bits, each chunk's 32 sample indices.
+// when sample indices fit in 16 bits, each chunk's 32 sample indices and the
+// forward's interpolated density and colour pre-activations of each sample
+// (so the adjoint needs the corner indices and weights only, not the rows).
 struct MarchHeader {
     uint32_t magic;
     int32_t max_chunks;
@@ -334,7 +336,7 @@ constexpr uint32_t kMarchMagic = 0x53584c50u;
 enum : int32_t { kMarchChunked = 1, kMarchRecompute = 2 };
 
 struct MarchLayout {
-    size_t hdr_off, nocc_off, first_off, items_off, part_off, live_off, samp_off, total;
+    size_t hdr_off, nocc_off, first_off, items_off, part_off, live_off, samp_off, vals_off, total;
     // the plan stores each chunk's sample indices (uint16) when every index fits
     static bool store_samples(int max_chunks) { return (int64_t)max_chunks * 32 <= 65536; }
     static size_t round256(size_t b) { return (b + 255) & ~size_t(255); }
@@ -348,7 +350,8 @@ struct MarchLayout {
         L.part_off = L.items_off + round256(slots * 8);
         L.live_off = L.part_off + round256(slots * 16);
         L.samp_off = L.live_off + round256(slots);
-        L.total = L.samp_off + (store_samples(max_chunks) ? round256(slots * 64) : 0);
+        L.vals_off = L.samp_off + (store_samples(max_chunks) ? round256(slots * 64) : 0);
+        L.total = L.vals_off + (store_samples(max_chunks) ? round256(slots * 32 * 16) : 0);
         return L;
     }
 };
@@ -361,6 +364,7 @@ struct MarchPtrs {
     float4 *part;     // [n][max_chunks] (C_loc, P), then (R_after, T_before)
     uint8_t *live;    // [n][max_chunks] 1 if any sample of the chunk has positive density
     uint16_t *samp;   // [n][max_chunks][32] the chunk's sample indices, or null (then chunks rescan)
+    float4 *vals;     // [n][max_chunks][32] each sample's (sigma, pre_R, pre_G, pre_B) from the forward, or null
     int max_chunks;
 };
 
@@ -371,6 +375,11 @@ cudaError_t launch_render(const GridView &g, const float *o, const float *d, int
 cudaError_t launch_render_backward(const GridView &g, const float *o, const float *d, int64_t n,
                                    const RenderParams &p, const float *grad_rgb, float *grad_rows,
                                    cudaStream_t s);
+cudaError_t launch_march_plan(const GridView &g, const float *o, const float *d, int64_t n, const RenderParams &p,
+                              const MarchPtrs &st, const MarchHeader &hdr, cudaStream_t s);
+cudaError_t launch_render_planned(const GridView &g, const float *o, const float *d, int64_t n,
+                                  const RenderParams &p, const MarchPtrs &st, const MarchHeader &hdr, float *rgb,
+                                  float *T_end, cudaStream_t s);
 cudaError_t launch_render_train(const GridView &g, const float *o, const float *d, int64_t n, const RenderParams &p,
                                 const MarchPtrs &st, const MarchHeader &hdr, float *rgb, float *T_end, cudaStream_t s);
 cudaError_t launch_render_backward_train(const GridView &g, const float *o, const float *d, int64_t n,

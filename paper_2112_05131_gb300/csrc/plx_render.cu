@@ -375,8 +375,8 @@ cudaError_t launch_render_backward(const GridView &g, const float *o, const floa
 // --------------------------------------------------------------------------- node counting
 // Algorithmic-traffic accounting for the forward march: per ray, the number of
 // distinct lattice nodes that are corners of sampled cells with at least one
-// occupied corner (each costs an index read) and how many of them are
-// occupied (each costs a row read).  The cells sharing a node form a
+// occupied corner (each costs an index read), how many of them are occupied
+// (each costs a row read), and how many samples are marched.  The cells sharing a node form a
 // contiguous run along the ray, so a node is counted at the first such cell,
 // i.e. unless it is also a corner of the previous non-empty sampled cell.
 // Exact for occupied nodes (every cell around one is non-empty); an empty node
@@ -397,7 +397,7 @@ __global__ void __launch_bounds__(kFwdWarps * 32) count_nodes_kernel(GridView g,
     const int64_t ray = (int64_t)blockIdx.x * kFwdWarps + wid;
     if (ray >= n) return;
     const RaySetup rs = ray_setup(g, ro, rd, ray);
-    int64_t nodes = 0, occ_nodes = 0;
+    int64_t nodes = 0, occ_nodes = 0, samples = 0;  // samples: uniform over the warp
     if (rs.hit) {
         int *ring = s_ring[wid];
         Stream st = {0, 0, 0, false};
@@ -430,6 +430,7 @@ __global__ void __launch_bounds__(kFwdWarps * 32) count_nodes_kernel(GridView g,
             }
             const int k = __popc(cp.tmask);
             if (k > 0) carry = __shfl_sync(kFull, cell, k - 1);
+            samples += k;
             Tc *= cp.chunk_prod;
             if (cp.tmask != __ballot_sync(kFull, valid)) break;
         }
@@ -440,8 +441,9 @@ __global__ void __launch_bounds__(kFwdWarps * 32) count_nodes_kernel(GridView g,
         occ_nodes += __shfl_xor_sync(kFull, occ_nodes, off);
     }
     if (lane == 0) {
-        out[2 * ray] = nodes;
-        out[2 * ray + 1] = occ_nodes;
+        out[3 * ray] = nodes;
+        out[3 * ray + 1] = occ_nodes;
+        out[3 * ray + 2] = samples;
     }
 }
 

@@ -19,9 +19,11 @@
 //                              C_loc(j) + T_end bg (a suffix sum of
 //                              non-negative terms: no cancellation);
 //   adjoint  (one resident wave over the same items)
-//                              recomputes a chunk's samples with T_s =
-//                              T_before(k) x (in-chunk prefix) and R_s =
-//                              R_after(k) + (in-chunk suffix), and scatters.
+//                              takes each sample's density and colour
+//                              pre-activations from the forward, recomputes
+//                              T_s = T_before(k) x (in-chunk prefix) and R_s =
+//                              R_after(k) + (in-chunk suffix), looks up the
+//                              corner rows and scatters.
 //
 // The state between the calls lives in a caller buffer (MarchLayout).  The
 // results equal plx_render / plx_render_backward up to FP32 summation order.
@@ -178,6 +180,15 @@ __global__ void __launch_bounds__(kPlanWarps * 32) march_plan_kernel(GridView g,
     }
 }
 
+// Does the state's header describe a plan of these rays, this grid and these options?
+__device__ __forceinline__ bool header_matches(const MarchHeader &h, const MarchHeader &e) {
+    return h.magic == kMarchMagic && h.mode == kMarchChunked && h.n == e.n && h.max_chunks == e.max_chunks &&
+           h.R == e.R && h.M == e.M && __float_as_uint(h.delta) == __float_as_uint(e.delta) &&
+           __float_as_uint(h.delta_lo) == __float_as_uint(e.delta_lo) &&
+           __float_as_uint(h.stop) == __float_as_uint(e.stop) && h.ro == e.ro && h.rd == e.rd &&
+           h.rows == e.rows && h.total_items >= 0 && (int64_t)h.total_items <= e.n * (int64_t)e.max_chunks;
+}
+
 // The inputs of one work item, loaded one item ahead so that their round trips overlap the
 // previous item's gather: the ray, its compacted-sample count, and this lane's sample index when
 // the plan stored the chunk's list.
@@ -239,11 +250,16 @@ __device__ __forceinline__ int item_samples(const GridView &g, const RaySetup &r
 // ---------------------------------------------------------------------------- chunks (forward)
 template <int FORM>
 __global__ void __launch_bounds__(kChunkWarps * 32, kGatherBlocks) march_chunks_fwd_kernel(
-    GridView g, const float *__restrict__ ro, const float *__restrict__ rd, RenderParams p, MarchPtrs st) {
+    GridView g, const float *__restrict__ ro, const float *__restrict__ rd, RenderParams p, MarchPtrs st,
+    MarchHeader expect) {
     __shared__ int s_buf[kChunkWarps][32];
     const int lane = threadIdx.x & 31;
     const int wid = threadIdx.x >> 5;
-    const int total = st.hdr->total_items;
+    const MarchHeader h = *st.hdr;
+    if (!header_matches(h, expect)) {  // no plan of these rays: nothing to march (reported by the combine)
+        return;
+    }
+    const int total = h.total_items;
     const int stride = gridDim.x * kChunkWarps;
     const int mc = st.max_chunks;
     int it = blockIdx.x * kChunkWarps + wid;
@@ -271,6 +287,7 @@ __global__ void __launch_bounds__(kChunkWarps * 32, kGatherBlocks) march_chunks_
             sig = fmaxf(acc[0], 0.0f);
             float pre[3];
             colour_of(acc, rs.Y, pre, col);
+            if (st.vals) st.vals[(ray * mc + k) * 32 + lane] = make_float4(sig, pre[0], pre[1], pre[2]);
         }
         const Composite cp = composite(sig, valid, 1.0f, p, lane);  // stop_thresh is 0 on this path
         const float w = cp.take ? cp.T * cp.alpha : 0.0f;
@@ -286,12 +303,17 @@ __global__ void __launch_bounds__(kChunkWarps * 32, kGatherBlocks) march_chunks_
 }
 
 // ---------------------------------------------------------------------------- combine
-__global__ void __launch_bounds__(kCombineWarps * 32) march_combine_kernel(int64_t n, RenderParams p, MarchPtrs st,
+__global__ void __launch_bounds__(kCombineWarps * 32) march_combine_kernel(GridView g, int64_t n, RenderParams p,
+                                                                           MarchPtrs st, MarchHeader expect,
                                                                            float *__restrict__ rgb,
                                                                            float *__restrict__ T_out) {
     const int lane = threadIdx.x & 31;
     const int64_t ray = (int64_t)blockIdx.x * kCombineWarps + (threadIdx.x >> 5);
     if (ray >= n) return;
+    if (!header_matches(*st.hdr, expect)) {  // uniform over the grid: the state holds no plan of these rays
+        if (ray == 0 && lane == 0) report(g.status, kDevStateMismatch);
+        return;
+    }
     const int mc = st.max_chunks;
     const int nch = (st.n_occ[ray] + 31) >> 5;
     float4 *part = st.part + ray * mc;
@@ -342,16 +364,13 @@ __global__ void __launch_bounds__(kCombineWarps * 32) march_combine_kernel(int64
 }
 
 // ---------------------------------------------------------------------------- adjoint
-__device__ __forceinline__ bool header_matches(const MarchHeader &h, const MarchHeader &e) {
-    return h.magic == kMarchMagic && h.mode == kMarchChunked && h.n == e.n && h.max_chunks == e.max_chunks &&
-           h.R == e.R && h.M == e.M && __float_as_uint(h.delta) == __float_as_uint(e.delta) &&
-           __float_as_uint(h.delta_lo) == __float_as_uint(e.delta_lo) &&
-           __float_as_uint(h.stop) == __float_as_uint(e.stop) && h.ro == e.ro && h.rd == e.rd &&
-           h.rows == e.rows && h.total_items >= 0 && (int64_t)h.total_items <= e.n * (int64_t)e.max_chunks;
-}
 
-template <int FORM>
-__global__ void __launch_bounds__(kChunkWarps * 32, kGatherBlocks) march_chunks_bwd_kernel(
+// With the forward's stored values (VALS) the adjoint gathers no rows: half the registers, twice the
+// resident warps to hide the index loads and atomics.
+constexpr int kBwdValsBlocks = 5;
+
+template <int FORM, bool VALS>
+__global__ void __launch_bounds__(kChunkWarps * 32, VALS ? kBwdValsBlocks : kGatherBlocks) march_chunks_bwd_kernel(
     GridView g, const float *__restrict__ ro, const float *__restrict__ rd, RenderParams p, MarchPtrs st,
     MarchHeader expect, const float *__restrict__ grad_rgb, float *__restrict__ grad_rows) {
     __shared__ int s_buf[kChunkWarps][32];
@@ -399,10 +418,25 @@ __global__ void __launch_bounds__(kChunkWarps * 32, kGatherBlocks) march_chunks_
         if (valid) {
             DF gc[3];
             sample_coords(g, rs, sample_t(rs, p, s), gc);
-            float acc[kNV];
-            gather_sample(g, FORM, gc, acc, rr, ff);
-            sig = fmaxf(acc[0], 0.0f);
-            colour_of(acc, rs.Y, pre, col);
+            if (VALS) {  // the forward's values; only the corners are looked up again
+                const float4 v = st.vals[(ray * mc + k) * 32 + lane];
+                const Cell c = locate(g, gc);
+#pragma unroll
+                for (int a = 0; a < 3; ++a) ff[a] = c.f[a];
+#pragma unroll
+                for (int kc = 0; kc < 8; ++kc) rr[kc] = row_of(g, corner_node(g, c.base, kc));
+                sig = v.x;
+                pre[0] = v.y;
+                pre[1] = v.z;
+                pre[2] = v.w;
+#pragma unroll
+                for (int ch = 0; ch < 3; ++ch) col[ch] = fmaxf(pre[ch], 0.0f);
+            } else {
+                float acc[kNV];
+                gather_sample(g, FORM, gc, acc, rr, ff);
+                sig = fmaxf(acc[0], 0.0f);
+                colour_of(acc, rs.Y, pre, col);
+            }
         }
         const Composite cp = composite(sig, valid, q.w, p, lane);
         const float w = cp.take ? cp.T * cp.alpha : 0.0f;
@@ -419,33 +453,44 @@ __global__ void __launch_bounds__(kChunkWarps * 32, kGatherBlocks) march_chunks_
     }
 }
 
-// One resident wave: kGatherBlocks CTAs per SM, but no more warps than items can exist.
-unsigned chunk_grid(int64_t n, int max_chunks) {
+// One resident wave: blocks_per_sm CTAs per SM, but no more warps than items can exist.
+unsigned chunk_grid(int64_t n, int max_chunks, int blocks_per_sm = kGatherBlocks) {
     const int64_t slots = n * (int64_t)max_chunks;
     const int64_t need = (slots + kChunkWarps - 1) / kChunkWarps;
-    const int64_t wave = (int64_t)sm_count() * kGatherBlocks;
+    const int64_t wave = (int64_t)sm_count() * blocks_per_sm;
     return (unsigned)std::max<int64_t>(1, std::min(need, wave));
 }
 
 }  // namespace
 
+cudaError_t launch_march_plan(const GridView &g, const float *o, const float *d, int64_t n, const RenderParams &p,
+                              const MarchPtrs &st, const MarchHeader &hdr, cudaStream_t s) {
+    march_header_kernel<<<1, 1, 0, s>>>(st.hdr, hdr);
+    if (hdr.mode == kMarchChunked && n > 0) march_plan_kernel<<<(unsigned)n, kPlanWarps * 32, 0, s>>>(g, o, d, n, p, st);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_render_planned(const GridView &g, const float *o, const float *d, int64_t n,
+                                  const RenderParams &p, const MarchPtrs &st, const MarchHeader &hdr, float *rgb,
+                                  float *T_end, cudaStream_t s) {
+    if (hdr.mode == kMarchRecompute) return launch_render(g, o, d, n, p, rgb, T_end, s);
+    if (n == 0) return cudaSuccess;
+    const unsigned grid = chunk_grid(n, st.max_chunks);
+    if (g.form == PLX_SH_F32)
+        march_chunks_fwd_kernel<PLX_SH_F32><<<grid, kChunkWarps * 32, 0, s>>>(g, o, d, p, st, hdr);
+    else
+        march_chunks_fwd_kernel<PLX_SH_BF16><<<grid, kChunkWarps * 32, 0, s>>>(g, o, d, p, st, hdr);
+    march_combine_kernel<<<(unsigned)((n + kCombineWarps - 1) / kCombineWarps), kCombineWarps * 32, 0, s>>>(
+        g, n, p, st, hdr, rgb, T_end);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_render_train(const GridView &g, const float *o, const float *d, int64_t n, const RenderParams &p,
                                 const MarchPtrs &st, const MarchHeader &hdr, float *rgb, float *T_end,
                                 cudaStream_t s) {
-    march_header_kernel<<<1, 1, 0, s>>>(st.hdr, hdr);
-    cudaError_t e = cudaGetLastError();
+    cudaError_t e = launch_march_plan(g, o, d, n, p, st, hdr, s);
     if (e != cudaSuccess) return e;
-    if (hdr.mode == kMarchRecompute) return launch_render(g, o, d, n, p, rgb, T_end, s);
-    if (n == 0) return cudaSuccess;
-    march_plan_kernel<<<(unsigned)n, kPlanWarps * 32, 0, s>>>(g, o, d, n, p, st);
-    const unsigned grid = chunk_grid(n, st.max_chunks);
-    if (g.form == PLX_SH_F32)
-        march_chunks_fwd_kernel<PLX_SH_F32><<<grid, kChunkWarps * 32, 0, s>>>(g, o, d, p, st);
-    else
-        march_chunks_fwd_kernel<PLX_SH_BF16><<<grid, kChunkWarps * 32, 0, s>>>(g, o, d, p, st);
-    march_combine_kernel<<<(unsigned)((n + kCombineWarps - 1) / kCombineWarps), kCombineWarps * 32, 0, s>>>(
-        n, p, st, rgb, T_end);
-    return cudaGetLastError();
+    return launch_render_planned(g, o, d, n, p, st, hdr, rgb, T_end, s);
 }
 
 cudaError_t launch_render_backward_train(const GridView &g, const float *o, const float *d, int64_t n,
@@ -453,12 +498,23 @@ cudaError_t launch_render_backward_train(const GridView &g, const float *o, cons
                                          const float *grad_rgb, float *grad_rows, cudaStream_t s) {
     if (hdr.mode == kMarchRecompute) return launch_render_backward(g, o, d, n, p, grad_rgb, grad_rows, s);
     if (n == 0) return cudaSuccess;
-    const unsigned grid = chunk_grid(n, st.max_chunks);
-    if (g.form == PLX_SH_F32)
-        march_chunks_bwd_kernel<PLX_SH_F32><<<grid, kChunkWarps * 32, 0, s>>>(g, o, d, p, st, hdr, grad_rgb, grad_rows);
-    else
-        march_chunks_bwd_kernel<PLX_SH_BF16><<<grid, kChunkWarps * 32, 0, s>>>(g, o, d, p, st, hdr, grad_rgb,
-                                                                               grad_rows);
+    if (st.vals) {
+        const unsigned grid = chunk_grid(n, st.max_chunks, kBwdValsBlocks);
+        if (g.form == PLX_SH_F32)
+            march_chunks_bwd_kernel<PLX_SH_F32, true><<<grid, kChunkWarps * 32, 0, s>>>(g, o, d, p, st, hdr, grad_rgb,
+                                                                                      grad_rows);
+        else
+            march_chunks_bwd_kernel<PLX_SH_BF16, true><<<grid, kChunkWarps * 32, 0, s>>>(g, o, d, p, st, hdr,
+                                                                                       grad_rgb, grad_rows);
+    } else {
+        const unsigned grid = chunk_grid(n, st.max_chunks);
+        if (g.form == PLX_SH_F32)
+            march_chunks_bwd_kernel<PLX_SH_F32, false><<<grid, kChunkWarps * 32, 0, s>>>(g, o, d, p, st, hdr,
+                                                                                       grad_rgb, grad_rows);
+        else
+            march_chunks_bwd_kernel<PLX_SH_BF16, false><<<grid, kChunkWarps * 32, 0, s>>>(g, o, d, p, st, hdr,
+                                                                                        grad_rgb, grad_rows);
+    }
     return cudaGetLastError();
 }
 

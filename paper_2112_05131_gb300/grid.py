@@ -204,6 +204,29 @@ class Grid:
                _p(state), state.numel(), _stream(stream))
         return rgb
 
+    def march_plan(self, origins: torch.Tensor, dirs: torch.Tensor, opts: RenderOpts, state: torch.Tensor,
+                   stream=None):
+        """plx_march_plan: the plan of a training batch (reads no rows)."""
+        n = origins.shape[0]
+        _need(origins, torch.float32, "origins", (n, 3))
+        _need(dirs, torch.float32, "dirs", (n, 3))
+        _need(state, torch.uint8, "state")
+        L.call("plx_march_plan", self.handle, _p(origins), _p(dirs), n, ctypes.byref(opts.c()), _p(state),
+               state.numel(), _stream(stream))
+
+    def render_planned(self, origins: torch.Tensor, dirs: torch.Tensor, opts: RenderOpts, state: torch.Tensor,
+                       rgb: Optional[torch.Tensor] = None, T_end: Optional[torch.Tensor] = None, stream=None):
+        """plx_render_planned: the forward of a planned training batch."""
+        n = origins.shape[0]
+        _need(origins, torch.float32, "origins", (n, 3))
+        _need(dirs, torch.float32, "dirs", (n, 3))
+        _need(state, torch.uint8, "state")
+        if rgb is None:
+            rgb = torch.empty((n, 3), dtype=torch.float32, device=origins.device)
+        L.call("plx_render_planned", self.handle, _p(origins), _p(dirs), n, ctypes.byref(opts.c()), _p(rgb),
+               _p(T_end), _p(state), state.numel(), _stream(stream))
+        return rgb
+
     def render_backward_train(self, origins, dirs, grad_rgb, opts: RenderOpts, state: torch.Tensor,
                               grad_rows: Optional[torch.Tensor] = None, stream=None):
         """plx_render_backward_train: the adjoint of the last render_train on these rays, from its state."""
@@ -218,9 +241,10 @@ class Grid:
         return grad_rows
 
     def count_nodes(self, origins, dirs, opts: RenderOpts = RenderOpts(), stream=None) -> torch.Tensor:
-        """Per ray (distinct nodes of sampled non-empty cells, occupied ones among them), int64 [n, 2]."""
+        """Per ray (distinct nodes of sampled non-empty cells, occupied ones among them, marched samples),
+        int64 [n, 3]."""
         n = origins.shape[0]
-        out = torch.empty((n, 2), dtype=torch.int64, device=origins.device)
+        out = torch.empty((n, 3), dtype=torch.int64, device=origins.device)
         L.call("plx_count_nodes", self.handle, _p(origins), _p(dirs), n, ctypes.byref(opts.c()), _p(out),
                _stream(stream))
         return out

@@ -1,11 +1,15 @@
 """The optimisation step of Sec. 3.4 as a sequence of library calls, and the learning-rate schedules.
 
 One step (Supp. A.1: 5000-ray batches, RMSProp, stochastic TV on contiguous segments):
-  plx_gen_rays -> plx_render_train -> plx_mse_grad -> plx_render_backward_train -> plx_tv_grad
-  -> plx_rmsprop_step
-all libplenoxel calls enqueued on one stream with no host synchronisation.  The training march
-(plx_render_train: header, plan, chunks, combine; plx_render_backward_train: chunks) splits rays
-into chunk work items and hands the march state from the forward to the adjoint.
+  plx_gen_rays -> plx_march_plan -> plx_render_planned -> plx_mse_grad -> plx_render_backward_train
+  -> plx_tv_grad -> plx_rmsprop_step
+all libplenoxel calls with no host synchronisation.  The training march splits rays into chunk work
+items and hands the march state from the forward to the adjoint.
+
+With overlap (the default) the calls use three streams and RMSProp is deferred to the start of the next
+step (or to finish()): ray generation and the plan read no rows, so the next batch's are computed while
+the previous update runs; TV reads rows only and adds to the gradient with atomics, so it runs beside
+the forward and adjoint.  Every step computes exactly what the serial order computes.
 """
 from __future__ import annotations
 
@@ -17,8 +21,8 @@ import torch
 
 from .grid import ROW, Grid, RenderOpts, gen_rays, mse_grad
 
-# kernels one step enqueues with stop_thresh = 0: gen_rays, render_train (header, plan, chunks,
-# combine), mse, backward_train, tv, rmsprop (compact, apply; sparse mode)
+# kernels one step enqueues with stop_thresh = 0: gen_rays, march_plan (header, plan), render_planned
+# (chunks, combine), mse, backward_train, tv, rmsprop (compact, apply; sparse mode)
 LAUNCHES_PER_STEP = 11
 
 
@@ -51,9 +55,8 @@ class StepConfig:
     beta: float = 0.95
     eps: float = 1e-8
     sparse_rmsprop: bool = True
-    # TV on a second stream, concurrent with ray generation, forward, MSE and adjoint: it reads only
-    # rows (unchanged until RMSProp) and adds to the gradient with atomics; RMSProp waits for both
-    overlap_tv: bool = True
+    # three streams and a deferred RMSProp (see the module docstring); False: one stream, in order
+    overlap: bool = True
 
 
 class Trainer:
@@ -74,47 +77,100 @@ class Trainer:
         self.grad_rgb = torch.empty((n, 3), dtype=torch.float32, device=dev)
         self.loss = torch.zeros(1, dtype=torch.float32, device=dev)
         self.state = grid.new_march_state(n, cfg.opts)  # fits every batch of up to n rays
-        self.side = torch.cuda.Stream(device=dev) if cfg.overlap_tv else None
-        self._ev_start = torch.cuda.Event()
-        self._ev_tv = torch.cuda.Event()
+        if cfg.overlap:
+            self.plan_stream = torch.cuda.Stream(device=dev)
+            self.tv_stream = torch.cuda.Stream(device=dev)
+        self._ev = {k: torch.cuda.Event() for k in ("start", "plan", "rms", "tv", "bwd")}
+        self._bwd_recorded = False
+        self.pending = None  # (lr_sigma, lr_sh) of an update not yet applied
+
+    def _update(self, main, lrs):
+        c = self.cfg
+        self.grid.rmsprop_step(self.grad, self.v, lrs[0], lrs[1], c.beta, c.eps, sparse=c.sparse_rmsprop, stream=main)
+
+    def finish(self, stream=None):
+        """Applies the pending RMSProp update (overlap mode defers each step's update to the next call)."""
+        if self.pending is not None:
+            main = stream if stream is not None else torch.cuda.current_stream()
+            self._update(main, self.pending)
+            self.pending = None
 
     def step(self, pix: torch.Tensor, target: torch.Tensor, seg_start: Optional[torch.Tensor],
              seg_len: Optional[torch.Tensor], n_selected: int, lr_s: float, lr_h: float,
              events: Optional[List[torch.cuda.Event]] = None, stream=None):
-        """One optimisation step; `events`, if given, must hold 7 events recorded at the stage boundaries of
-        the main stream (with overlap_tv the TV stage there is only the wait for the side stream)."""
+        """One optimisation step.  `events`, if given, holds 8 events recorded on the main stream; the 7
+        intervals between them are the stages named in STAGES (serial mode: rays and plan, -, forward, MSE,
+        adjoint, TV, update; overlap mode: the previous step's update, the wait for this step's plan,
+        forward, MSE, adjoint, the wait for TV, -).  In overlap mode call finish() after the last step."""
         g, c = self.grid, self.cfg
         n = pix.shape[0]
         o, d, rgb, grgb = self.o[:n], self.d[:n], self.rgb[:n], self.grad_rgb[:n]
         main = stream if stream is not None else torch.cuda.current_stream()
         do_tv = seg_start is not None and n_selected > 0
-        side = self.side if (do_tv and self.side is not None) else None
+        ev = self._ev
 
         def mark(i):
             if events is not None:
                 events[i].record(main)
 
-        if side is not None:  # TV starts after everything enqueued so far (the last RMSProp, the inputs)
-            self._ev_start.record(main)
-            side.wait_event(self._ev_start)
-            g.tv_grad(seg_start, seg_len, n_selected, c.lambda_tv_sigma, c.lambda_tv_sh, self.grad, stream=side)
-            self._ev_tv.record(side)
+        if not c.overlap:
+            mark(0)
+            gen_rays(self.cams, pix, self.W, self.H, o, d, stream=main)
+            g.march_plan(o, d, c.opts, self.state, stream=main)
+            mark(1)
+            mark(2)
+            g.render_planned(o, d, c.opts, self.state, rgb, stream=main)
+            mark(3)
+            mse_grad(rgb, target, grgb, self.loss, stream=main)
+            mark(4)
+            g.render_backward_train(o, d, grgb, c.opts, self.state, self.grad, stream=main)
+            mark(5)
+            if do_tv:
+                g.tv_grad(seg_start, seg_len, n_selected, c.lambda_tv_sigma, c.lambda_tv_sh, self.grad, stream=main)
+            mark(6)
+            self._update(main, (lr_s, lr_h))
+            mark(7)
+            return rgb
+
+        # rays and plan of this batch on the plan stream, once the last adjoint is done with rays and state
+        ev["start"].record(main)
+        ps = self.plan_stream
+        ps.wait_event(ev["start"])
+        if self._bwd_recorded:
+            ps.wait_event(ev["bwd"])
+        gen_rays(self.cams, pix, self.W, self.H, o, d, stream=ps)
+        g.march_plan(o, d, c.opts, self.state, stream=ps)
+        ev["plan"].record(ps)
+        # the previous step's update, concurrently
         mark(0)
-        gen_rays(self.cams, pix, self.W, self.H, o, d, stream=main)
+        if self.pending is not None:
+            self._update(main, self.pending)
+            self.pending = None
         mark(1)
-        g.render_train(o, d, c.opts, self.state, rgb, stream=main)
+        # TV of this step after that update, beside the march
+        if do_tv:
+            ev["rms"].record(main)
+            self.tv_stream.wait_event(ev["rms"])
+            g.tv_grad(seg_start, seg_len, n_selected, c.lambda_tv_sigma, c.lambda_tv_sh, self.grad,
+                      stream=self.tv_stream)
+            ev["tv"].record(self.tv_stream)
+        main.wait_event(ev["plan"])
         mark(2)
-        mse_grad(rgb, target, grgb, self.loss, stream=main)
+        g.render_planned(o, d, c.opts, self.state, rgb, stream=main)
         mark(3)
-        g.render_backward_train(o, d, grgb, c.opts, self.state, self.grad, stream=main)
+        mse_grad(rgb, target, grgb, self.loss, stream=main)
         mark(4)
-        if side is not None:
-            main.wait_event(self._ev_tv)
-        elif do_tv:
-            g.tv_grad(seg_start, seg_len, n_selected, c.lambda_tv_sigma, c.lambda_tv_sh, self.grad, stream=main)
+        g.render_backward_train(o, d, grgb, c.opts, self.state, self.grad, stream=main)
+        ev["bwd"].record(main)
+        self._bwd_recorded = True
         mark(5)
-        g.rmsprop_step(self.grad, self.v, lr_s, lr_h, c.beta, c.eps, sparse=c.sparse_rmsprop, stream=main)
+        if do_tv:
+            main.wait_event(ev["tv"])
+        self.pending = (lr_s, lr_h)
         mark(6)
+        mark(7)
         return rgb
 
-    STAGES = ("gen_rays", "render", "mse_grad", "render_backward", "tv_grad", "rmsprop_step")
+    # the 7 intervals between step()'s 8 events: serial mode | overlap mode
+    STAGES = ("rays_plan|prev_update", "-|plan_wait", "render", "mse_grad", "render_backward", "tv_grad|tv_wait",
+              "rmsprop_step|-")

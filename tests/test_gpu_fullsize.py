@@ -3,8 +3,8 @@
 * 256^3 at 8% occupancy: one whole optimisation step of Trainer.step (5000-ray batch drawn from 100
   800x800 views, TV on 1% of the nodes in 4096-node segments, sparse RMSProp), every output element
   (colours, updated rows, RMSProp state) checked against the oracle.
-* 512^3 at 3% occupancy, FP32 and BF16-SH forms: the 5000-ray batch forward and adjoint, all rays and
-  all gradient rows checked.
+* 512^3 at 3% occupancy, FP32 and BF16-SH forms: the 5000-ray batch forward and adjoint (the training
+  march the benchmark times, and the one-warp-per-ray kernels), all rays and all gradient rows checked.
 * 512^3 full frames: 25 held-out 800x800 views rendered one 640,000-ray launch each; 64 seeded pixels
   per view (1600 rays) checked against the oracle, and the PSNR lost by storing SH in BF16 measured
   against the ground truth on those rays (Sec. 3.1 grid, a BF16 storage form of this implementation).
@@ -71,6 +71,7 @@ def test_full_step_sparse256(cuda_lib, scene256):
     tr = Trainer(g, torch.from_numpy(cams).cuda(), 800, 800, StepConfig(batch=n, opts=opts))
     tr.step(torch.from_numpy(pix).cuda(), torch.from_numpy(target).cuda(), torch.from_numpy(ss).cuda(),
             torch.from_numpy(sl).cuda(), n_sel, lrs, lrh)
+    tr.finish()  # the overlapped step defers its update
     torch.cuda.synchronize()
     g.check()
     assert np.array_equal(tr.d.cpu().numpy(), d32)  # the library's rays are the same FP32 roundings
@@ -112,14 +113,24 @@ def test_batch_forward_backward_sparse512(cuda_lib, scene512, form):
 
     g = Grid.from_host(R, sc.idx, sc.rows, sh_form=form)
     ot, dt = torch.from_numpy(o32).cuda(), torch.from_numpy(d32).cuda()
+    gw_t = torch.from_numpy(gw).cuda()
     opts = RenderOpts(0.5, BG, 0.0)
-    rgb = g.render(ot, dt, opts).cpu().numpy()
-    grad = g.render_backward(ot, dt, torch.from_numpy(gw).cuda(), opts).cpu().numpy()
+    touched = (gref != 0).any(1)
+    # the training march the benchmark times (plan, planned forward, adjoint from the state) ...
+    state = g.new_march_state(n, opts)
+    g.march_plan(ot, dt, opts, state)
+    rgb = g.render_planned(ot, dt, opts, state).cpu().numpy()
+    grad = g.render_backward_train(ot, dt, gw_t, opts, state).cpu().numpy()
     g.check()
     worst_c, nflag = check_colours(rgb, ref, aux, rows, delta_of(R, 0.5), BG)
     worst_g = check_grads(grad, gref)
-    touched = (gref != 0).any(1)
     assert np.all(grad[~touched] == 0.0)  # rows no ray reaches stay exactly zero
+    # ... and the one-warp-per-ray forward and adjoint
+    rgb1 = g.render(ot, dt, opts).cpu().numpy()
+    grad1 = g.render_backward(ot, dt, gw_t, opts).cpu().numpy()
+    g.check()
+    check_colours(rgb1, ref, aux, rows, delta_of(R, 0.5), BG)
+    check_grads(grad1, gref)
     print(f"512^3 form {form}: colour err/tol {worst_c:.3f} (flagged {nflag}), grad err/tol {worst_g:.3f}, "
           f"{int(touched.sum())} rows touched")
 

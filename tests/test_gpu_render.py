@@ -5,7 +5,7 @@ import torch
 
 import oracle
 import synth
-from parity import bf16_grid_rows, check_colours, delta_of
+from parity import bf16_grid_rows, check_colours, delta_of, tie_flags
 
 pytestmark = pytest.mark.gpu
 
@@ -145,3 +145,19 @@ def test_gen_rays_parity(cuda_lib):
     bad = torch.tensor([-1, 8 * 64 * 64], dtype=torch.int64, device="cuda")
     ob, db = gen_rays(torch.from_numpy(cams).cuda(), bad, 64, 64)
     assert torch.all(db == 0) and torch.all(ob == 0)
+
+
+def test_count_nodes_on_a_dense_grid(cuda_lib):
+    """On a grid with every node occupied every cell is non-empty: all samples are marched, and every
+    counted node is occupied."""
+    from paper_2112_05131_gb300.grid import Grid, RenderOpts
+
+    sc = synth.scene_config("dense32")
+    g = Grid.from_host(sc.R, sc.idx, sc.rows)
+    o, d = synth.random_rays(500, seed=71)
+    counts = g.count_nodes(torch.from_numpy(o).cuda(), torch.from_numpy(d).cuda(), RenderOpts()).cpu().numpy()
+    _, aux = oracle.render(sc.R, sc.idx, sc.rows, o.astype(float), d.astype(float))
+    ok = ~tie_flags(aux, delta_of(sc.R, 0.5))
+    assert np.array_equal(counts[ok, 2], aux[ok, 1].astype(np.int64))
+    assert np.array_equal(counts[:, 0], counts[:, 1])
+    assert np.all((counts[:, 0] > 0) == (aux[:, 1] > 0))

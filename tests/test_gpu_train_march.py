@@ -198,3 +198,63 @@ def test_train_march_rejects_a_foreign_state(cuda_lib):
     grad = g.render_backward_train(ot, dt, torch.ones((500, 3), device="cuda"), opts, st)
     g.check()
     assert torch.count_nonzero(grad) > 0
+
+
+def test_plan_then_planned_equals_render_train(cuda_lib):
+    from paper_2112_05131_gb300._lib import PlxError
+    from paper_2112_05131_gb300.grid import Grid, RenderOpts
+
+    opts = RenderOpts(0.5, BG, 0.0)
+    sc = _sparse_scene(40, 0.2, 23)
+    g = Grid.from_host(sc.R, sc.idx, sc.rows)
+    o, d = synth.random_rays(3000, seed=24)
+    ot, dt = torch.from_numpy(o).cuda(), torch.from_numpy(d).cuda()
+    st = g.new_march_state(3000, opts)
+    a = g.render_train(ot, dt, opts, st).cpu().numpy()
+    g.march_plan(ot, dt, opts, st)
+    b = g.render_planned(ot, dt, opts, st).cpu().numpy()
+    assert np.array_equal(a.view(np.uint32), b.view(np.uint32))
+    # a planned march of other rays than the plan's: nothing written, the grid flagged
+    o2, d2 = ot.clone(), dt.clone()
+    rgb = torch.full((3000, 3), -5.0, device="cuda")
+    g.render_planned(o2, d2, opts, st, rgb)
+    torch.cuda.synchronize()
+    assert torch.all(rgb == -5.0)
+    with pytest.raises(PlxError, match="PLX_EDEVICE"):
+        g.check()
+
+
+@pytest.mark.parametrize("form", [0, 1])
+def test_overlapped_trainer_matches_serial(cuda_lib, form):
+    """Three streams and a deferred update compute what the serial order computes (up to the order in
+    which atomics add the TV and adjoint gradients)."""
+    from paper_2112_05131_gb300.grid import Grid, RenderOpts
+    from paper_2112_05131_gb300.train import StepConfig, Trainer, lr_sh, lr_sigma
+
+    gt = synth.scene_config("dense32")
+    sc = synth.perturb(gt, 0.05, seed=3)
+    cams = torch.from_numpy(synth.cameras_config("sphere8_64")).cuda()
+    opts = RenderOpts(0.5, (1.0, 1.0, 1.0), 0.0)
+    g_gt = Grid.from_host(gt.R, gt.idx, gt.rows)
+    batches = []
+    for s in range(4):
+        pix = torch.from_numpy(synth.pixel_batch(8, 64, 64, 2048, seed=40 + s)).cuda()
+        from paper_2112_05131_gb300.grid import gen_rays
+        o, d = gen_rays(cams, pix, 64, 64)
+        ss, sl = synth.tv_segments(gt.R, 0.3, 256, seed=50 + s)
+        batches.append((pix, g_gt.render(o, d, opts), torch.from_numpy(ss).cuda(), torch.from_numpy(sl).cuda(),
+                        int(sl.sum())))
+    rows = {}
+    for overlap in (False, True):
+        g = Grid.from_host(sc.R, sc.idx, sc.rows, sh_form=form)
+        tr = Trainer(g, cams, 64, 64, StepConfig(batch=2048, opts=opts, overlap=overlap))
+        for s, b in enumerate(batches):
+            tr.step(*b, lr_sigma(1000 + s), lr_sh(1000 + s))
+        tr.finish()
+        torch.cuda.synchronize()
+        g.check()
+        rows[overlap] = g.rows[:, :28].cpu().numpy()
+        if form == 1:  # the BF16 shadow follows the rows
+            assert torch.count_nonzero(g.rows_h) > 0
+    assert np.allclose(rows[True], rows[False], rtol=1e-4, atol=1e-6)
+    assert not np.array_equal(rows[True], sc.rows)  # the steps did change the grid
