@@ -291,6 +291,7 @@ plx_status march_state(const plx_grid *grid, const float *d_origins, const float
     ptrs->live = reinterpret_cast<uint8_t *>(b + L.live_off);
     ptrs->samp = plx::MarchLayout::store_samples(p.max_chunks) ? reinterpret_cast<uint16_t *>(b + L.samp_off) : nullptr;
     ptrs->vals = plx::MarchLayout::store_samples(p.max_chunks) ? reinterpret_cast<float4 *>(b + L.vals_off) : nullptr;
+    ptrs->setup = b + L.setup_off;
     ptrs->max_chunks = p.max_chunks;
     std::memset(hdr, 0, sizeof(*hdr));
     hdr->magic = plx::kMarchMagic;

@@ -335,8 +335,10 @@ struct MarchHeader {
 constexpr uint32_t kMarchMagic = 0x53584c50u;
 enum : int32_t { kMarchChunked = 1, kMarchRecompute = 2 };
 
+constexpr size_t kRaySetupBytes = 128;  // the march's per-ray setup (RaySetup, plx_march.cuh)
+
 struct MarchLayout {
-    size_t hdr_off, nocc_off, first_off, items_off, part_off, live_off, samp_off, vals_off, total;
+    size_t hdr_off, nocc_off, first_off, items_off, part_off, live_off, samp_off, vals_off, setup_off, total;
     // the plan stores each chunk's sample indices (uint16) when every index fits
     static bool store_samples(int max_chunks) { return (int64_t)max_chunks * 32 <= 65536; }
     static size_t round256(size_t b) { return (b + 255) & ~size_t(255); }
@@ -351,7 +353,8 @@ struct MarchLayout {
         L.live_off = L.part_off + round256(slots * 16);
         L.samp_off = L.live_off + round256(slots);
         L.vals_off = L.samp_off + (store_samples(max_chunks) ? round256(slots * 64) : 0);
-        L.total = L.vals_off + (store_samples(max_chunks) ? round256(slots * 32 * 16) : 0);
+        L.setup_off = L.vals_off + (store_samples(max_chunks) ? round256(slots * 32 * 16) : 0);
+        L.total = L.setup_off + round256(size_t(n) * kRaySetupBytes);
         return L;
     }
 };
@@ -365,6 +368,7 @@ struct MarchPtrs {
     uint8_t *live;    // [n][max_chunks] 1 if any sample of the chunk has positive density
     uint16_t *samp;   // [n][max_chunks][32] the chunk's sample indices, or null (then chunks rescan)
     float4 *vals;     // [n][max_chunks][32] each sample's (sigma, pre_R, pre_G, pre_B) from the forward, or null
+    void *setup;      // [n] the rays' march setup (RaySetup: clip, grid-space origin and direction, SH basis)
     int max_chunks;
 };
 

@@ -14,7 +14,7 @@ namespace plx {
 constexpr int kGatherBlocks = 4;
 
 // --------------------------------------------------------------------------- per-ray setup
-struct RaySetup {
+struct __align__(16) RaySetup {  // 128 bytes: the training march keeps one per ray in its state
     DF A[3];       // origin minus box corner, exact as a double-float
     float d[3];    // unit direction as given
     DF tn, tf;     // clipped parameter range
@@ -22,8 +22,9 @@ struct RaySetup {
     float dg[3];
     float Y[9];    // SH basis at the direction
     float feps;    // bound on |FP32 - exact| grid coordinate of any sample of the ray (see test_candidate)
-    bool hit;
+    int hit;       // the ray meets the box
 };
+static_assert(sizeof(RaySetup) == 128, "RaySetup layout");
 
 __device__ __forceinline__ RaySetup ray_setup_od(const GridView &g, const float o[3], const float d[3]) {
     RaySetup rs;

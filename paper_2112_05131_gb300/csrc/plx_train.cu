@@ -59,6 +59,20 @@ int sm_count() {
 
 __global__ void march_header_kernel(MarchHeader *dst, MarchHeader v) { *dst = v; }
 
+// ---------------------------------------------------------------------------- ray setup
+// The per-ray setup (double-float clip, grid-space origin and direction, SH basis, FP32 margin),
+// computed once per ray and read by the plan and by every chunk of the ray.
+__device__ __forceinline__ const RaySetup &setup_of(const MarchPtrs &st, int64_t ray) {
+    return reinterpret_cast<const RaySetup *>(st.setup)[ray];
+}
+
+__global__ void __launch_bounds__(128) march_setup_kernel(GridView g, const float *__restrict__ ro,
+                                                          const float *__restrict__ rd, int64_t n, MarchPtrs st) {
+    const int64_t ray = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (ray >= n) return;
+    reinterpret_cast<RaySetup *>(st.setup)[ray] = ray_setup(g, ro, rd, ray);
+}
+
 // ---------------------------------------------------------------------------- plan
 // One CTA per ray: its kPlanWarps warps test interleaved spans of 256 candidates (span q by warp
 // q mod kPlanWarps, candidate q 256 + 32 j + lane as in the other marches), keeping each span's
@@ -73,17 +87,12 @@ __global__ void __launch_bounds__(kPlanWarps * 32) march_plan_kernel(GridView g,
     __shared__ uint32_t s_mask[kPlanMaxSpans * kCand];
     __shared__ int s_cnt[kPlanMaxSpans + 1];
     __shared__ int s_last;
-    __shared__ RaySetup s_rs;
     const int lane = threadIdx.x & 31;
     const int wid = threadIdx.x >> 5;
     const unsigned lt = (1u << lane) - 1u;
     for (int64_t ray = blockIdx.x; ray < n; ray += gridDim.x) {  // uniform over the CTA
-        if (threadIdx.x == 0) {  // the ray's setup, once for the CTA
-            s_rs = ray_setup(g, ro, rd, ray);
-            s_last = -1;
-        }
-        __syncthreads();
-        const RaySetup rs = s_rs;
+        const RaySetup rs = setup_of(st, ray);  // every thread: a broadcast load, no barrier
+        if (threadIdx.x == 0) s_last = -1;  // read after phase 1's barrier
         const int mc = st.max_chunks;
         int2 *range = st.range + ray * mc;
         uint16_t *samp = st.samp ? st.samp + ray * mc * 32 : nullptr;  // chunk k's samples at [32 k, 32 k + 32)
@@ -191,10 +200,9 @@ __device__ __forceinline__ bool header_matches(const MarchHeader &h, const March
 
 // The inputs of one work item, loaded one item ahead so that their round trips overlap the
 // previous item's gather: the ray, its compacted-sample count, and this lane's sample index when
-// the plan stored the chunk's list.
+// the plan stored the chunk's list.  The ray's setup follows through shared memory (SetupPipe).
 struct ItemIn {
     int ray, k;  // ray -1: past the end of the list
-    float o[3], d[3];
     int n_occ;
     int s;
 };
@@ -210,20 +218,34 @@ __device__ __forceinline__ ItemIn load_item(const MarchPtrs &st, const float *__
     r.k = id.y;
     r.n_occ = 0;
     r.s = 0;
-#pragma unroll
-    for (int a = 0; a < 3; ++a) r.o[a] = r.d[a] = 0.0f;
     if (id.x >= 0) {
         const int64_t ray = id.x;
-#pragma unroll
-        for (int a = 0; a < 3; ++a) {
-            r.o[a] = __ldg(ro + 3 * ray + a);
-            r.d[a] = __ldg(rd + 3 * ray + a);
-        }
         r.n_occ = st.n_occ[ray];
         // lanes past the chunk's count read unused slots of the list; their value is never used
         if (st.samp) r.s = st.samp[(ray * st.max_chunks + id.y) * 32 + lane];
     }
     return r;
+}
+
+// A warp's two shared-memory slots for ray setups: the next item's setup is copied in with cp.async
+// (lanes 0-7, 16 bytes each) while the current item is processed, and read in place from there.
+struct SetupPipe {
+    RaySetup slot[2];
+};
+
+__device__ __forceinline__ void setup_fetch(SetupPipe &p, int buf, const MarchPtrs &st, int ray, int lane) {
+    if (ray >= 0 && lane < 8) {
+        const char *src = reinterpret_cast<const char *>(st.setup) + (int64_t)ray * kRaySetupBytes + 16 * lane;
+        const unsigned dst = (unsigned)__cvta_generic_to_shared(reinterpret_cast<char *>(&p.slot[buf]) + 16 * lane);
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(dst), "l"(src) : "memory");
+    }
+    asm volatile("cp.async.commit_group;\n" ::: "memory");
+}
+
+// Waits until every fetch but the most recent one has landed, and makes it visible to the warp.
+__device__ __forceinline__ void setup_wait_prev() {
+    asm volatile("cp.async.wait_group 1;\n" ::: "memory");
+    __syncwarp();
 }
 
 // The samples of the item: returns the count (lane i gets sample s if i < count), from the plan's list
@@ -253,6 +275,7 @@ __global__ void __launch_bounds__(kChunkWarps * 32, kGatherBlocks) march_chunks_
     GridView g, const float *__restrict__ ro, const float *__restrict__ rd, RenderParams p, MarchPtrs st,
     MarchHeader expect) {
     __shared__ int s_buf[kChunkWarps][32];
+    __shared__ SetupPipe s_pipe[kChunkWarps];
     const int lane = threadIdx.x & 31;
     const int wid = threadIdx.x >> 5;
     const MarchHeader h = *st.hdr;
@@ -264,17 +287,24 @@ __global__ void __launch_bounds__(kChunkWarps * 32, kGatherBlocks) march_chunks_
     const int mc = st.max_chunks;
     int it = blockIdx.x * kChunkWarps + wid;
     ItemIn cur = load_item(st, ro, rd, item_at(st, it, total), lane);
+    setup_fetch(s_pipe[wid], 0, st, cur.ray, lane);
     int2 id_next = item_at(st, it + stride, total);
-    for (; it < total; it += stride) {
+    int buf = 0;
+    for (; it < total; it += stride, buf ^= 1) {
         const ItemIn nxt = load_item(st, ro, rd, id_next, lane);
+        setup_fetch(s_pipe[wid], buf ^ 1, st, nxt.ray, lane);
         id_next = item_at(st, it + 2 * stride, total);
         const int64_t ray = cur.ray;
         const int k = cur.k;
-        const RaySetup rs = ray_setup_od(g, cur.o, cur.d);
+        setup_wait_prev();
+        const RaySetup &rs = s_pipe[wid].slot[buf];
         int s;
         const int cnt = item_samples(g, rs, p, st, cur, s_buf[wid], lane, s);
         cur = nxt;
-        if (cnt < 0) continue;
+        if (cnt < 0) {
+            __syncwarp();
+            continue;
+        }
         const bool valid = lane < cnt;
         float sig = 0.0f, col[3] = {0.0f, 0.0f, 0.0f};
         if (valid) {
@@ -299,7 +329,9 @@ __global__ void __launch_bounds__(kChunkWarps * 32, kGatherBlocks) march_chunks_
             st.part[ray * mc + k] = make_float4(c0, c1, c2, cp.chunk_prod);
             st.live[ray * mc + k] = live ? 1 : 0;
         }
+        __syncwarp();  // every lane is done with this slot before the next fetch overwrites it
     }
+    asm volatile("cp.async.wait_all;\n" ::: "memory");
 }
 
 // ---------------------------------------------------------------------------- combine
@@ -374,6 +406,7 @@ __global__ void __launch_bounds__(kChunkWarps * 32, VALS ? kBwdValsBlocks : kGat
     GridView g, const float *__restrict__ ro, const float *__restrict__ rd, RenderParams p, MarchPtrs st,
     MarchHeader expect, const float *__restrict__ grad_rgb, float *__restrict__ grad_rows) {
     __shared__ int s_buf[kChunkWarps][32];
+    __shared__ SetupPipe s_pipe[kChunkWarps];
     const int lane = threadIdx.x & 31;
     const int wid = threadIdx.x >> 5;
     const MarchHeader h = *st.hdr;
@@ -398,19 +431,26 @@ __global__ void __launch_bounds__(kChunkWarps * 32, VALS ? kBwdValsBlocks : kGat
     int2 id = next_live(it);
     int it_cur = it;
     ItemIn cur = load_item(st, ro, rd, id, lane);
+    setup_fetch(s_pipe[wid], 0, st, cur.ray, lane);
     int2 id_next = next_live(it_cur + stride);
-    while (cur.ray >= 0) {
+    int buf = 0;
+    for (; cur.ray >= 0; buf ^= 1) {
         const ItemIn nxt = load_item(st, ro, rd, id_next, lane);
+        setup_fetch(s_pipe[wid], buf ^ 1, st, nxt.ray, lane);
         id_next = next_live(it + stride);
         const int64_t ray = cur.ray;
         const int k = cur.k;
         const float4 q = st.part[ray * mc + k];  // (R_after, T_before)
         const float gr[3] = {__ldg(grad_rgb + 3 * ray), __ldg(grad_rgb + 3 * ray + 1), __ldg(grad_rgb + 3 * ray + 2)};
-        const RaySetup rs = ray_setup_od(g, cur.o, cur.d);
+        setup_wait_prev();
+        const RaySetup &rs = s_pipe[wid].slot[buf];
         int s;
         const int cnt = item_samples(g, rs, p, st, cur, s_buf[wid], lane, s);
         cur = nxt;
-        if (cnt < 0) continue;
+        if (cnt < 0) {
+            __syncwarp();
+            continue;
+        }
         const bool valid = lane < cnt;
         int32_t rr[8];
         float ff[3];
@@ -450,7 +490,9 @@ __global__ void __launch_bounds__(kChunkWarps * 32, VALS ? kBwdValsBlocks : kGat
             Rs[ch] = Ra[ch] + suf_ex;
         }
         if (cp.take && sig > 0.0f) scatter_sample(g, rr, ff, rs.Y, gr, pre, col, w, cp.Tn, Rs, p.delta, grad_rows);
+        __syncwarp();  // every lane is done with this slot before the next fetch overwrites it
     }
+    asm volatile("cp.async.wait_all;\n" ::: "memory");
 }
 
 // One resident wave: blocks_per_sm CTAs per SM, but no more warps than items can exist.
@@ -466,7 +508,10 @@ unsigned chunk_grid(int64_t n, int max_chunks, int blocks_per_sm = kGatherBlocks
 cudaError_t launch_march_plan(const GridView &g, const float *o, const float *d, int64_t n, const RenderParams &p,
                               const MarchPtrs &st, const MarchHeader &hdr, cudaStream_t s) {
     march_header_kernel<<<1, 1, 0, s>>>(st.hdr, hdr);
-    if (hdr.mode == kMarchChunked && n > 0) march_plan_kernel<<<(unsigned)n, kPlanWarps * 32, 0, s>>>(g, o, d, n, p, st);
+    if (hdr.mode == kMarchChunked && n > 0) {
+        march_setup_kernel<<<(unsigned)((n + 127) / 128), 128, 0, s>>>(g, o, d, n, st);
+        march_plan_kernel<<<(unsigned)n, kPlanWarps * 32, 0, s>>>(g, o, d, n, p, st);
+    }
     return cudaGetLastError();
 }
 
