@@ -150,6 +150,7 @@ plx_status plx_grid_create(const plx_grid_desc *desc, const int32_t *d_idx, floa
     v.rows = d_rows_f32;
     v.rows_h = d_rows_bf16;
     v.occ = reinterpret_cast<const uint32_t *>(g->ws + g->layout.occ_off);
+    v.occ_box = reinterpret_cast<const int *>(g->ws + g->layout.status_off + plx::WorkspaceLayout::kOccBoxOff);
     v.touched = reinterpret_cast<uint32_t *>(g->ws + g->layout.touched_off);
     v.tlist = reinterpret_cast<int32_t *>(g->ws + g->layout.list_off);
     v.tcount = reinterpret_cast<int *>(g->ws + g->layout.status_off + plx::WorkspaceLayout::kListCountOff);
@@ -443,8 +444,8 @@ plx_status plx_tv_grad(const plx_grid *grid, const int64_t *d_seg_start, const i
     if (!std::isfinite(lambda_sigma) || !std::isfinite(lambda_sh)) return fail(PLX_EINVAL, "lambda not finite");
     const float ls = (float)((double)lambda_sigma / (double)n_selected);
     const float lh = (float)((double)lambda_sh / (double)n_selected);
-    return cuda_status(plx::launch_tv(grid->view, d_seg_start, d_seg_len, n_seg, ls, lh, d_grad_rows, d_loss,
-                                      static_cast<cudaStream_t>(stream)), "plx_tv_grad");
+    return cuda_status(plx::launch_tv(grid->view, d_seg_start, d_seg_len, n_seg, n_selected, ls, lh, d_grad_rows,
+                                      d_loss, static_cast<cudaStream_t>(stream)), "plx_tv_grad");
 }
 
 plx_status plx_rmsprop_step(plx_grid *grid, float *d_grad_rows, float *d_v, float lr_sigma, float lr_sh, float beta,

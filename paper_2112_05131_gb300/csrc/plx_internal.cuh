@@ -24,10 +24,12 @@ constexpr unsigned kFull = 0xffffffffu;
 enum : int { kDevOk = 0, kDevBadRow = 1, kDevTooManySamples = 2, kDevCountMismatch = 3, kDevStateMismatch = 4, kDevBadTile = 5 };
 
 // Workspace layout of a grid: [status block 256 B][occupancy bits][touched bits][touched-row list].
-// The status block holds the device status word at byte 0 and the touched-list length at byte 64.
+// The status block holds the device status word at byte 0, the touched-list length at byte 64 and the
+// box of non-empty cells at byte 128 (six ints: R-1-lo per axis, then hi per axis).
 struct WorkspaceLayout {
     size_t status_off, occ_off, touched_off, list_off, total;
     static constexpr size_t kListCountOff = 64;
+    static constexpr size_t kOccBoxOff = 128;
     static size_t round256(size_t b) { return (b + 255) & ~size_t(255); }
     static WorkspaceLayout make(int64_t R, int64_t M) {
         WorkspaceLayout L;
@@ -46,6 +48,7 @@ struct GridView {
     const float *rows;          // F32 rows (may be null for a render-only BF16 grid)
     const uint16_t *rows_h;     // BF16-SH rows (null for the F32 form)
     const uint32_t *occ;        // bit per base node: 1 if any of the cell's 8 nodes is occupied
+    const int *occ_box;         // cells with an occupied corner lie in [R-1-box[a], box[3+a]] on axis a
     uint32_t *touched;          // bit per row: set when a gradient lands on the row
     int32_t *tlist;             // the touched rows as a list (built by the sparse RMSProp step)
     int *tcount;                // its length
@@ -398,7 +401,8 @@ cudaError_t launch_mse_grad(const float *rgb, const float *target, int64_t n, fl
 cudaError_t launch_build_occupancy(const GridView &g, uint32_t *occ, cudaStream_t s);
 cudaError_t launch_pack_bf16(const GridView &g, uint16_t *rows_h, cudaStream_t s);
 cudaError_t launch_tv(const GridView &g, const int64_t *seg_start, const int64_t *seg_len, int64_t n_seg,
-                      float scale_sigma, float scale_sh, float *grad_rows, float *loss, cudaStream_t s);
+                      int64_t n_selected, float scale_sigma, float scale_sh, float *grad_rows, float *loss,
+                      cudaStream_t s);
 cudaError_t launch_rmsprop(const GridView &g, float *rows, uint16_t *rows_h, float *grad, float *v,
                            float lr_sigma, float lr_sh, float beta, float eps, int sparse, cudaStream_t s);
 

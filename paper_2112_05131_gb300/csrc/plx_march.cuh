@@ -23,10 +23,12 @@ struct __align__(16) RaySetup {  // 128 bytes: the training march keeps one per 
     float Y[9];    // SH basis at the direction
     float feps;    // bound on |FP32 - exact| grid coordinate of any sample of the ray (see test_candidate)
     int hit;       // the ray meets the box
+    int s_lo, s_hi;  // samples outside [s_lo, s_hi) lie in empty cells (outside the box of non-empty cells)
 };
 static_assert(sizeof(RaySetup) == 128, "RaySetup layout");
 
-__device__ __forceinline__ RaySetup ray_setup_od(const GridView &g, const float o[3], const float d[3]) {
+__device__ __forceinline__ RaySetup ray_setup_od(const GridView &g, const RenderParams &p, const float o[3],
+                                                 const float d[3]) {
     RaySetup rs;
 #pragma unroll
     for (int a = 0; a < 3; ++a) rs.d[a] = d[a];
@@ -50,10 +52,40 @@ __device__ __forceinline__ RaySetup ray_setup_od(const GridView &g, const float 
     }
     const float tmax = rs.hit ? fabsf(rs.tf.hi) : 0.0f;
     rs.feps = 1.25f * 5.9604645e-8f * (ih * (3.0f * om + 5.0f * tmax) + (float)g.R);
+    // The candidate range: every cell with an occupied corner lies in the box of cells [lo, hi] (grid
+    // coordinates [lo, hi + 1]); a sample whose coordinate is outside that box widened by one cell on
+    // every side (far more than the FP32 error) is in an empty cell.  Slab test in FP32, then sample
+    // indices widened by two on each side; samples beyond max_chunks * 32 do not exist.
+    rs.s_lo = 0;
+    rs.s_hi = 0;
+    if (rs.hit) {
+        float t0 = rs.tn.hi, t1 = rs.tf.hi;
+        bool any = true;
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            const float blo = (float)(g.R - 1 - __ldg(g.occ_box + a)) - 1.0f;
+            const float bhi = (float)__ldg(g.occ_box + 3 + a) + 2.0f;
+            any = any && blo <= bhi;
+            if (rs.dg[a] == 0.0f) {
+                any = any && rs.og[a] >= blo && rs.og[a] <= bhi;
+            } else {
+                const float ta = (blo - rs.og[a]) / rs.dg[a], tb = (bhi - rs.og[a]) / rs.dg[a];
+                t0 = fmaxf(t0, fminf(ta, tb));
+                t1 = fminf(t1, fmaxf(ta, tb));
+            }
+        }
+        if (any && t0 <= t1) {
+            const float sa = floorf((t0 - rs.tn.hi) / p.delta) - 2.0f;
+            const float sb = ceilf((t1 - rs.tn.hi) / p.delta) + 3.0f;
+            const float smax = (float)(p.max_chunks * 32);
+            rs.s_lo = (int)fminf(fmaxf(sa, 0.0f), smax);
+            rs.s_hi = (int)fminf(fmaxf(sb, 0.0f), smax);
+        }
+    }
     return rs;
 }
 
-__device__ __forceinline__ RaySetup ray_setup(const GridView &g, const float *__restrict__ ro,
+__device__ __forceinline__ RaySetup ray_setup(const GridView &g, const RenderParams &p, const float *__restrict__ ro,
                                               const float *__restrict__ rd, int64_t ray) {
     float o[3], d[3];
 #pragma unroll
@@ -61,7 +93,7 @@ __device__ __forceinline__ RaySetup ray_setup(const GridView &g, const float *__
         o[a] = __ldg(ro + 3 * ray + a);
         d[a] = __ldg(rd + 3 * ray + a);
     }
-    return ray_setup_od(g, o, d);
+    return ray_setup_od(g, p, o, d);
 }
 
 // t_s = t_near + s * delta as a double-float (s * delta_hi is exact for s < 2^24).
@@ -256,7 +288,11 @@ __device__ __forceinline__ Cand test_candidate(const GridView &g, const RaySetup
     Cand c;
     c.occ = false;
     c.valid = false;
-    if (s >= p.max_chunks * 32) return c;
+    if (s >= rs.s_hi) return c;  // beyond the non-empty box (or past max_chunks * 32): no more samples
+    if (s < rs.s_lo) {            // before the non-empty box: valid and empty
+        c.valid = true;
+        return c;
+    }
     const float t32 = fmaf((float)s, p.delta, rs.tn.hi);
     const float kTEps = 1e-5f * (fabsf(rs.tf.hi) + 1.0f);
     bool exact = fabsf(t32 - rs.tf.hi) <= kTEps;

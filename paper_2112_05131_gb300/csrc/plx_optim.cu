@@ -30,6 +30,41 @@ __global__ void build_occupancy_kernel(GridView g, uint32_t *__restrict__ occ, i
     }
 }
 
+// The box of cells with an occupied corner (for the march's ray clip): a grid-stride pass over the
+// occupancy words, reduced per CTA in shared memory, then one atomicMax per CTA and bound.  Stored as
+// R-1-lo and hi, so that the zeroed status block starts as the empty box.
+__global__ void __launch_bounds__(256) occ_box_kernel(GridView g, const uint32_t *__restrict__ occ, int64_t n_words,
+                                                      int *__restrict__ box) {
+    __shared__ int s_box[6];
+    if (threadIdx.x < 6) s_box[threadIdx.x] = 0;
+    __syncthreads();
+    const int64_t R = g.R;
+    int b[6] = {0, 0, 0, 0, 0, 0};
+    for (int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; w < n_words; w += (int64_t)gridDim.x * blockDim.x) {
+        uint32_t word = __ldg(occ + w);
+        while (word) {
+            const int bit = __ffs(word) - 1;
+            word &= word - 1u;
+            const int64_t c = w * 32 + bit;
+            const int64_t ijk[3] = {c / (R * R), (c / R) % R, c % R};
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                b[a] = max(b[a], (int)(R - 1 - ijk[a]));
+                b[3 + a] = max(b[3 + a], (int)ijk[a]);
+            }
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < 6; ++i) {
+        int v = b[i];
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) v = max(v, __shfl_xor_sync(0xffffffffu, v, off));
+        if ((threadIdx.x & 31) == 0 && v > 0) atomicMax(&s_box[i], v);
+    }
+    __syncthreads();
+    if (threadIdx.x < 6 && s_box[threadIdx.x] > 0) atomicMax(&box[threadIdx.x], s_box[threadIdx.x]);
+}
+
 cudaError_t launch_build_occupancy(const GridView &g, uint32_t *occ, cudaStream_t s) {
     const int64_t R = g.R;
     const int64_t n_words = (R * R * R + 31) / 32;
@@ -37,6 +72,8 @@ cudaError_t launch_build_occupancy(const GridView &g, uint32_t *occ, cudaStream_
     int64_t blocks = (n_words + 7) / 8;
     if (blocks > 152 * 64) blocks = 152 * 64;
     build_occupancy_kernel<<<(unsigned)blocks, threads, 0, s>>>(g, occ, n_words);
+    const int64_t bblocks = std::min<int64_t>((n_words + 255) / 256, 152 * 8);
+    occ_box_kernel<<<(unsigned)bblocks, 256, 0, s>>>(g, occ, n_words, const_cast<int *>(g.occ_box));
     return cudaGetLastError();
 }
 
@@ -71,14 +108,16 @@ cudaError_t launch_pack_bf16(const GridView &g, uint16_t *rows_h, cudaStream_t s
 }
 
 // --------------------------------------------------------------------------- TV
-// Thread per selected node.  A node whose own row and +x/+y/+z neighbours are
-// all empty has t = 0 for every value and is skipped; the others load the
-// (up to) four rows as float4 groups and scatter float4 gradients:
+// A warp takes 32 consecutive selected nodes.  A node whose own row and
+// +x/+y/+z neighbours are all empty has t = 0 for every value and is skipped;
+// the others are handled four at a time, 8 lanes per node, each lane loading
+// one float4 quarter of the (up to) four rows and scattering float4 gradients:
 //   D_a = (V_d(v+e_a) - V_d(v)) * R/256; t = |D|; L += lam_d t;
 //   missing neighbour (NULL or outside): density 0, SH = V_d(v).
-// Each segment is split over kTvParts CTAs so short and long runs both fill the GPU.
+// Each segment is split over as many CTAs ("parts", sized on the host from the
+// average segment length) as it has 256-node spans, so short and long runs
+// both fill the GPU.
 constexpr int kTvThreads = 256;
-constexpr int kTvParts = 16;
 
 __device__ __forceinline__ float4 ld4(const float *p) { return __ldg(reinterpret_cast<const float4 *>(p)); }
 
@@ -133,8 +172,8 @@ __device__ __forceinline__ void tv_quarter(const GridView &g, int32_t rs, const 
 // at a time with 8 lanes each (one float4 quarter per lane), so a node's rows take one round trip.
 __global__ void __launch_bounds__(kTvThreads) tv_kernel(GridView g, const int64_t *__restrict__ seg_start,
                                                         const int64_t *__restrict__ seg_len, int64_t n_seg,
-                                                        float lam_sigma, float lam_sh, float *__restrict__ grad,
-                                                        float *__restrict__ loss) {
+                                                        int64_t parts, float lam_sigma, float lam_sh,
+                                                        float *__restrict__ grad, float *__restrict__ loss) {
     const int64_t R = g.R;
     const int64_t N = R * R * R;
     const float scale = (float)R / 256.0f;
@@ -144,12 +183,13 @@ __global__ void __launch_bounds__(kTvThreads) tv_kernel(GridView g, const int64_
     const int wid = threadIdx.x >> 5;
     constexpr int kWarps = kTvThreads / 32;
     float loss_acc = 0.0f;
-    for (int64_t item = blockIdx.x; item < n_seg * kTvParts; item += gridDim.x) {
-        const int64_t sg = item / kTvParts;
-        const int part = (int)(item % kTvParts);
+    // item = (segment, part): the parts of a segment interleave their 32-node spans
+    for (int64_t item = blockIdx.x; item < n_seg * parts; item += gridDim.x) {
+        const int64_t sg = item / parts;
+        const int64_t part = item % parts;
         const int64_t start = seg_start[sg];
         const int64_t len = seg_len[sg];
-        for (int64_t off0 = ((int64_t)part * kWarps + wid) * 32; off0 < len; off0 += (int64_t)kTvParts * kWarps * 32) {
+        for (int64_t off0 = (part * kWarps + wid) * 32; off0 < len; off0 += parts * kWarps * 32) {
             const int64_t off = off0 + lane;
             const int64_t n = start + off;
             // (i, j, k) of the warp's first node by one division, then carried lane by lane
@@ -204,11 +244,17 @@ __global__ void __launch_bounds__(kTvThreads) tv_kernel(GridView g, const int64_
 }
 
 cudaError_t launch_tv(const GridView &g, const int64_t *seg_start, const int64_t *seg_len, int64_t n_seg,
-                      float lam_sigma, float lam_sh, float *grad_rows, float *loss, cudaStream_t s) {
+                      int64_t n_selected, float lam_sigma, float lam_sh, float *grad_rows, float *loss,
+                      cudaStream_t s) {
     if (n_seg == 0) return cudaSuccess;
-    int64_t blocks = n_seg * kTvParts;
+    // parts per segment: one 32-node span per warp of the average segment
+    constexpr int64_t kCtaNodes = kTvThreads;
+    const int64_t avg = (n_selected + n_seg - 1) / n_seg;
+    const int64_t parts = std::max<int64_t>(1, std::min<int64_t>((avg + kCtaNodes - 1) / kCtaNodes, 1 << 20));
+    int64_t blocks = n_seg * parts;
     if (blocks > 152 * 32) blocks = 152 * 32;
-    tv_kernel<<<(unsigned)blocks, kTvThreads, 0, s>>>(g, seg_start, seg_len, n_seg, lam_sigma, lam_sh, grad_rows, loss);
+    tv_kernel<<<(unsigned)blocks, kTvThreads, 0, s>>>(g, seg_start, seg_len, n_seg, parts, lam_sigma, lam_sh,
+                                                      grad_rows, loss);
     return cudaGetLastError();
 }
 

@@ -116,7 +116,7 @@ __device__ __forceinline__ void march_forward(const GridView &g, const RenderPar
     C[0] = C[1] = C[2] = 0.0f;
     Tc = 1.0f;  // transmittance before the current chunk
     if (rs.hit) {
-        Stream st = {0, 0, 0, false};
+        Stream st = {rs.s_lo, rs.s_lo, rs.s_lo, false};
         for (;;) {
             refill(g, rs, p, ring, st, lane);
             int s;
@@ -162,7 +162,7 @@ __global__ void __launch_bounds__(kFwdWarps * 32, kGatherBlocks) render_fwd_kern
     const int wid = threadIdx.x >> 5;
     const int64_t ray = (int64_t)blockIdx.x * kFwdWarps + wid;
     if (ray >= n) return;  // uniform per warp
-    const RaySetup rs = ray_setup(g, ro, rd, ray);
+    const RaySetup rs = ray_setup(g, p, ro, rd, ray);
     float C[3], Tc;
     march_forward<FORM>(g, p, rs, s_ring[wid], lane, C, Tc);
     if (lane == 0) {
@@ -217,7 +217,7 @@ __global__ void __launch_bounds__(kFwdWarps * 32, kGatherBlocks) render_tiles_ke
     const RenderParams &p = tab.p[tile.scene];
     float o[3], d[3];
     pixel_ray(cams + 18 * (int64_t)tile.camera, x, y, o, d);
-    const RaySetup rs = ray_setup_od(g, o, d);
+    const RaySetup rs = ray_setup_od(g, p, o, d);
     float C[3], Tc;
     march_forward<FORM>(g, p, rs, s_ring[wid], lane, C, Tc);
     if (lane == 0) {
@@ -275,7 +275,7 @@ __global__ void __launch_bounds__(kBwdWarps * 32, kGatherBlocks) render_bwd_kern
     const int wid = threadIdx.x >> 5;
     const int64_t ray = (int64_t)blockIdx.x * kBwdWarps + wid;
     if (ray >= n) return;
-    const RaySetup rs = ray_setup(g, ro, rd, ray);
+    const RaySetup rs = ray_setup(g, p, ro, rd, ray);
     if (!rs.hit) return;
     for (int q = lane; q < kMaxChunks / 32; q += 32) s_live[wid][q] = 0u;
     __syncwarp();
@@ -285,7 +285,7 @@ __global__ void __launch_bounds__(kBwdWarps * 32, kGatherBlocks) render_bwd_kern
     float Tc = 1.0f;
     int n_chunks = 0;
     {
-        Stream st = {0, 0, 0, false};
+        Stream st = {rs.s_lo, rs.s_lo, rs.s_lo, false};
         for (;;) {
             refill(g, rs, p, ring, st, lane);
             int s;
@@ -396,11 +396,11 @@ __global__ void __launch_bounds__(kFwdWarps * 32) count_nodes_kernel(GridView g,
     const int wid = threadIdx.x >> 5;
     const int64_t ray = (int64_t)blockIdx.x * kFwdWarps + wid;
     if (ray >= n) return;
-    const RaySetup rs = ray_setup(g, ro, rd, ray);
+    const RaySetup rs = ray_setup(g, p, ro, rd, ray);
     int64_t nodes = 0, occ_nodes = 0, samples = 0;  // samples: uniform over the warp
     if (rs.hit) {
         int *ring = s_ring[wid];
-        Stream st = {0, 0, 0, false};
+        Stream st = {rs.s_lo, rs.s_lo, rs.s_lo, false};
         float Tc = 1.0f;
         int64_t carry = -1;  // cell of the last sample of the previous chunk
         for (;;) {

@@ -66,11 +66,11 @@ __device__ __forceinline__ const RaySetup &setup_of(const MarchPtrs &st, int64_t
     return reinterpret_cast<const RaySetup *>(st.setup)[ray];
 }
 
-__global__ void __launch_bounds__(128) march_setup_kernel(GridView g, const float *__restrict__ ro,
+__global__ void __launch_bounds__(128) march_setup_kernel(GridView g, RenderParams p, const float *__restrict__ ro,
                                                           const float *__restrict__ rd, int64_t n, MarchPtrs st) {
     const int64_t ray = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (ray >= n) return;
-    reinterpret_cast<RaySetup *>(st.setup)[ray] = ray_setup(g, ro, rd, ray);
+    reinterpret_cast<RaySetup *>(st.setup)[ray] = ray_setup(g, p, ro, rd, ray);
 }
 
 // ---------------------------------------------------------------------------- plan
@@ -100,13 +100,15 @@ __global__ void __launch_bounds__(kPlanWarps * 32) march_plan_kernel(GridView g,
         // max_chunks * 32 (so every rank / 32 < max_chunks)
         int L = 0;
         if (rs.hit) L = (int)fminf((float)(mc * 32), ceilf((rs.tf.hi - rs.tn.hi) / p.delta) + 2.0f);
-        const int n_spans = (L + kSpan - 1) / kSpan;
+        L = min(L, rs.s_hi);   // candidates outside [s_lo, s_hi) are empty: spans start at s_lo
+        const int s_first = rs.s_lo;
+        const int n_spans = L > s_first ? (L - s_first + kSpan - 1) / kSpan : 0;
         int n_occ = 0;
         for (int w0 = 0; w0 < n_spans; w0 += kPlanMaxSpans) {
             const int nw = min(kPlanMaxSpans, n_spans - w0);
             // phase 1: masks and counts of this window's spans
             for (int q = wid; q < nw; q += kPlanWarps) {
-                const int base = (w0 + q) * kSpan;
+                const int base = s_first + (w0 + q) * kSpan;
                 Cand c[kCand];
 #pragma unroll
                 for (int j = 0; j < kCand; ++j) {
@@ -146,7 +148,7 @@ __global__ void __launch_bounds__(kPlanWarps * 32) march_plan_kernel(GridView g,
                         for (int j = kCand - 1; j >= 0; --j) {
                             const unsigned m = s_mask[ql * kCand + j];
                             if (m) {
-                                s_last = (w0 + ql) * kSpan + 32 * j + 31 - __clz((int)m);
+                                s_last = s_first + (w0 + ql) * kSpan + 32 * j + 31 - __clz((int)m);
                                 break;
                             }
                         }
@@ -158,7 +160,7 @@ __global__ void __launch_bounds__(kPlanWarps * 32) march_plan_kernel(GridView g,
             __syncthreads();
             // phase 3: every occupied sample of the window writes its chunk boundary and list entry
             for (int q = wid; q < nw; q += kPlanWarps) {
-                const int base = (w0 + q) * kSpan;
+                const int base = s_first + (w0 + q) * kSpan;
                 int rank0 = s_cnt[q];
 #pragma unroll
                 for (int j = 0; j < kCand; ++j) {
@@ -509,7 +511,7 @@ cudaError_t launch_march_plan(const GridView &g, const float *o, const float *d,
                               const MarchPtrs &st, const MarchHeader &hdr, cudaStream_t s) {
     march_header_kernel<<<1, 1, 0, s>>>(st.hdr, hdr);
     if (hdr.mode == kMarchChunked && n > 0) {
-        march_setup_kernel<<<(unsigned)((n + 127) / 128), 128, 0, s>>>(g, o, d, n, st);
+        march_setup_kernel<<<(unsigned)((n + 127) / 128), 128, 0, s>>>(g, p, o, d, n, st);
         march_plan_kernel<<<(unsigned)n, kPlanWarps * 32, 0, s>>>(g, o, d, n, p, st);
     }
     return cudaGetLastError();

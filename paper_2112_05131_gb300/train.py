@@ -78,9 +78,13 @@ class Trainer:
         self.loss = torch.zeros(1, dtype=torch.float32, device=dev)
         self.state = grid.new_march_state(n, cfg.opts)  # fits every batch of up to n rays
         if cfg.overlap:
-            self.plan_stream = torch.cuda.Stream(device=dev)
-            self.tv_stream = torch.cuda.Stream(device=dev)
-        self._ev = {k: torch.cuda.Event() for k in ("start", "plan", "rms", "tv", "bwd")}
+            # the march (update, forward, MSE, adjoint) and the plan on high-priority streams, TV on a
+            # low-priority one: when both have blocks waiting, the scheduler starts the march's first
+            # and TV fills what is left
+            self.march_stream = torch.cuda.Stream(device=dev, priority=-1)
+            self.plan_stream = torch.cuda.Stream(device=dev, priority=-1)
+            self.tv_stream = torch.cuda.Stream(device=dev, priority=0)
+        self._ev = {k: torch.cuda.Event() for k in ("start", "plan", "rms", "tv", "bwd", "end")}
         self._bwd_recorded = False
         self.pending = None  # (lr_sigma, lr_sh) of an update not yet applied
 
@@ -132,8 +136,13 @@ class Trainer:
             mark(7)
             return rgb
 
+        # the march stream starts after everything the caller enqueued (inputs, the loss reset)
+        caller = main
+        ms = self.march_stream
+        ev["start"].record(caller)
+        ms.wait_event(ev["start"])
+        main = ms  # the stage events follow the march stream
         # rays and plan of this batch on the plan stream, once the last adjoint is done with rays and state
-        ev["start"].record(main)
         ps = self.plan_stream
         ps.wait_event(ev["start"])
         if self._bwd_recorded:
@@ -144,31 +153,34 @@ class Trainer:
         # the previous step's update, concurrently
         mark(0)
         if self.pending is not None:
-            self._update(main, self.pending)
+            self._update(ms, self.pending)
             self.pending = None
         mark(1)
         # TV of this step after that update, beside the march
         if do_tv:
-            ev["rms"].record(main)
+            ev["rms"].record(ms)
             self.tv_stream.wait_event(ev["rms"])
             g.tv_grad(seg_start, seg_len, n_selected, c.lambda_tv_sigma, c.lambda_tv_sh, self.grad,
                       stream=self.tv_stream)
             ev["tv"].record(self.tv_stream)
-        main.wait_event(ev["plan"])
+        ms.wait_event(ev["plan"])
         mark(2)
-        g.render_planned(o, d, c.opts, self.state, rgb, stream=main)
+        g.render_planned(o, d, c.opts, self.state, rgb, stream=ms)
         mark(3)
-        mse_grad(rgb, target, grgb, self.loss, stream=main)
+        mse_grad(rgb, target, grgb, self.loss, stream=ms)
         mark(4)
-        g.render_backward_train(o, d, grgb, c.opts, self.state, self.grad, stream=main)
-        ev["bwd"].record(main)
+        g.render_backward_train(o, d, grgb, c.opts, self.state, self.grad, stream=ms)
+        ev["bwd"].record(ms)
         self._bwd_recorded = True
         mark(5)
         if do_tv:
-            main.wait_event(ev["tv"])
+            ms.wait_event(ev["tv"])
         self.pending = (lr_s, lr_h)
         mark(6)
         mark(7)
+        # the caller's stream resumes after the step (colours, loss and gradient are then complete)
+        ev["end"].record(ms)
+        caller.wait_event(ev["end"])
         return rgb
 
     # the 7 intervals between step()'s 8 events: serial mode | overlap mode

@@ -161,3 +161,36 @@ def test_count_nodes_on_a_dense_grid(cuda_lib):
     assert np.array_equal(counts[ok, 2], aux[ok, 1].astype(np.int64))
     assert np.array_equal(counts[:, 0], counts[:, 1])
     assert np.all((counts[:, 0] > 0) == (aux[:, 1] > 0))
+
+
+@pytest.mark.parametrize("node", [(0, 0, 0), (9, 4, 13), (15, 15, 15), (0, 15, 7)])
+def test_render_single_occupied_node(cuda_lib, node):
+    """Only one node occupied: the march bounds each ray's candidates by the box of non-empty cells (the
+    cells around that node), so rays must still see the node from every direction and position."""
+    from paper_2112_05131_gb300.grid import Grid, RenderOpts
+
+    R = 16
+    idx = np.full(R ** 3, -1, np.int32)
+    i, j, k = node
+    idx[(i * R + j) * R + k] = 0
+    rows = np.zeros((1, 28), np.float32)
+    rows[0, 0] = 40.0
+    rows[0, [1, 10, 19]] = [2.0, 1.0, 0.5]
+    g = Grid.from_host(R, idx, rows)
+    # rays aimed at the node from all around, plus random ones, plus one starting next to it
+    h = 2.0 / (R - 1)
+    p = -1.0 + h * np.array(node, np.float64)
+    rng = np.random.default_rng(sum(node))
+    dirs = rng.normal(size=(600, 3))
+    dirs /= np.linalg.norm(dirs, axis=1, keepdims=True)
+    o = (p[None, :] - 2.5 * dirs + rng.normal(0, 0.3 * h, size=(600, 3))).astype(np.float32)
+    d = dirs.astype(np.float32)
+    o2, d2 = synth.random_rays(400, seed=5)
+    o = np.concatenate([o, o2, (p + 0.2 * h)[None, :].astype(np.float32)])
+    d = np.concatenate([d, d2, np.float32([[0.6, 0.0, 0.8]])])
+    opts = RenderOpts(0.5, (0.3, 0.3, 0.3), 0.0)
+    rgb = g.render(torch.from_numpy(o).cuda(), torch.from_numpy(d).cuda(), opts).cpu().numpy()
+    g.check()
+    ref, aux = oracle.render(R, idx, rows, o.astype(float), d.astype(float), bg=opts.bg)
+    check_colours(rgb, ref, aux, rows, delta_of(R, 0.5), opts.bg)
+    assert np.sum(np.abs(ref - np.float64(opts.bg)).max(1) > 1e-3) > 100  # many rays do see the node
