@@ -320,9 +320,10 @@ def extras(args, wl, dev_batches, cams_t, gt_grid, opts, timed_loop, st32, ms32)
     occ /= K
     samples /= K
     n = args.batch
-    # forward (chunks + combine): rays, colours, one index read per distinct node, one 112-byte row per
-    # distinct occupied node, and each sample's stored (sigma, pre) (16 B) and index (2 B)
-    fwd_bytes = n * (24 + 12) + 4 * nodes + 112 * occ + 18 * samples
+    # forward (chunks + combine with the MSE gradient): rays, colours, targets and dL/dC, one index read per
+    # distinct node, one 112-byte row per distinct occupied node, and each sample's stored (sigma, pre)
+    # (16 B) and index (2 B)
+    fwd_bytes = n * (24 + 12 + 24) + 4 * nodes + 112 * occ + 18 * samples  # + target in, dL/dC out
     # adjoint: rays and dL/dC, the stored per-sample values and indices, one index read per distinct node,
     # and a read-modify-write of each distinct occupied row's 112-byte gradient
     bwd_bytes = n * (24 + 12) + 18 * samples + 4 * nodes + 2 * 112 * occ
@@ -357,7 +358,8 @@ def extras(args, wl, dev_batches, cams_t, gt_grid, opts, timed_loop, st32, ms32)
         tv_b.append(12 * sel.size + 3 * 112 * distinct)
     tv_bytes = float(np.mean(tv_b))
     per_launch = {"render": fwd_bytes, "render_backward": bwd_bytes, "rmsprop_step": rms_bytes, "tv_grad": tv_bytes}
-    launches = {"render": "march_chunks_fwd + march_combine", "render_backward": "march_chunks_bwd",
+    launches = {"render": "march_chunks_fwd + march_combine (with the MSE gradient)",
+                "render_backward": "march_chunks_bwd",
                 "rmsprop_step": "rms_compact + rms_apply", "tv_grad": "tv_kernel"}
     dom = max(per_launch, key=lambda k: st32[k])
     ach = per_launch[dom] / (st32[dom] / 1e3) / 1e9

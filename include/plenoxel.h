@@ -224,6 +224,15 @@ plx_status plx_render_planned(const plx_grid *grid, const float *d_origins, cons
                               const plx_render_opts *opts, float *d_rgb, float *d_T_end, void *d_state,
                               size_t state_bytes, void *stream);
 
+/* plx_render_planned followed by plx_mse_grad in the same kernel (Sec. 3.4: the
+ * reconstruction loss of the batch): writes the colours d_rgb, the gradient
+ * d_grad_rgb = 2 (C - target) / n and adds L = sum |C - target|^2 / n to
+ * *d_loss (if not NULL).  d_target float [n][3]; d_grad_rgb may alias neither
+ * d_rgb nor d_target. */
+plx_status plx_render_planned_mse(const plx_grid *grid, const float *d_origins, const float *d_dirs, int64_t n,
+                                  const plx_render_opts *opts, const float *d_target, float *d_rgb,
+                                  float *d_grad_rgb, float *d_loss, void *d_state, size_t state_bytes, void *stream);
+
 /* As plx_render_backward, for the rays, grid and options of the last
  * plx_render_train (or plx_render_planned) that used d_state, enqueued after
  * it, before the grid's rows change.  The kernel checks the state's header (ray buffers, grid rows,

@@ -60,6 +60,8 @@ SIGNATURES = {
                                  c_size_t, c_void_p]),
     "plx_render_planned": (c_int32, [c_void_p, c_void_p, c_void_p, c_int64, ctypes.POINTER(plx_render_opts),
                                      c_void_p, c_void_p, c_void_p, c_size_t, c_void_p]),
+    "plx_render_planned_mse": (c_int32, [c_void_p, c_void_p, c_void_p, c_int64, ctypes.POINTER(plx_render_opts),
+                                         c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_size_t, c_void_p]),
     "plx_render_backward_train": (c_int32, [c_void_p, c_void_p, c_void_p, c_int64, ctypes.POINTER(plx_render_opts),
                                             c_void_p, c_void_p, c_size_t, c_void_p, c_void_p]),
     "plx_render_tiles": (c_int32, [ctypes.POINTER(c_void_p), c_int32, c_void_p, c_int32, c_void_p, c_int64,

@@ -362,7 +362,29 @@ plx_status plx_render_planned(const plx_grid *grid, const float *d_origins, cons
     st = march_state(grid, d_origins, d_dirs, n, opts, p, d_state, state_bytes, &ptrs, &hdr);
     if (st != PLX_OK) return st;
     return cuda_status(plx::launch_render_planned(grid->view, d_origins, d_dirs, n, p, ptrs, hdr, d_rgb, d_T_end,
-                                                  static_cast<cudaStream_t>(stream)), "plx_render_planned");
+                                                  nullptr, nullptr, nullptr, static_cast<cudaStream_t>(stream)),
+                       "plx_render_planned");
+}
+
+plx_status plx_render_planned_mse(const plx_grid *grid, const float *d_origins, const float *d_dirs, int64_t n,
+                                  const plx_render_opts *opts, const float *d_target, float *d_rgb,
+                                  float *d_grad_rgb, float *d_loss, void *d_state, size_t state_bytes, void *stream) {
+    plx_status st = check_grid(grid);
+    if (st == PLX_OK) st = check_opts(opts);
+    if (st != PLX_OK) return st;
+    if (n < 0 || n >= (int64_t(1) << 31)) return fail(PLX_EINVAL, "n out of range");
+    if (n > 0 && (!d_origins || !d_dirs || !d_rgb || !d_target || !d_grad_rgb))
+        return fail(PLX_EINVAL, "NULL ray, target or output buffer");
+    if (n > 0 && (d_grad_rgb == d_rgb || d_grad_rgb == d_target)) return fail(PLX_EINVAL, "d_grad_rgb aliases an input");
+    if (grid->desc.sh_form == PLX_SH_F32 && grid->desc.n_rows > 0 && !grid->rows) return fail(PLX_EINVAL, "grid has no F32 rows");
+    const plx::RenderParams p = make_params(grid, opts);
+    plx::MarchPtrs ptrs;
+    plx::MarchHeader hdr;
+    st = march_state(grid, d_origins, d_dirs, n, opts, p, d_state, state_bytes, &ptrs, &hdr);
+    if (st != PLX_OK) return st;
+    return cuda_status(plx::launch_render_planned(grid->view, d_origins, d_dirs, n, p, ptrs, hdr, d_rgb, nullptr,
+                                                  d_target, d_grad_rgb, d_loss, static_cast<cudaStream_t>(stream)),
+                       "plx_render_planned_mse");
 }
 
 plx_status plx_render_backward_train(const plx_grid *grid, const float *d_origins, const float *d_dirs, int64_t n,

@@ -386,7 +386,7 @@ cudaError_t launch_march_plan(const GridView &g, const float *o, const float *d,
                               const MarchPtrs &st, const MarchHeader &hdr, cudaStream_t s);
 cudaError_t launch_render_planned(const GridView &g, const float *o, const float *d, int64_t n,
                                   const RenderParams &p, const MarchPtrs &st, const MarchHeader &hdr, float *rgb,
-                                  float *T_end, cudaStream_t s);
+                                  float *T_end, const float *target, float *grad_rgb, float *loss, cudaStream_t s);
 cudaError_t launch_render_train(const GridView &g, const float *o, const float *d, int64_t n, const RenderParams &p,
                                 const MarchPtrs &st, const MarchHeader &hdr, float *rgb, float *T_end, cudaStream_t s);
 cudaError_t launch_render_backward_train(const GridView &g, const float *o, const float *d, int64_t n,

@@ -337,17 +337,12 @@ __global__ void __launch_bounds__(kChunkWarps * 32, kGatherBlocks) march_chunks_
 }
 
 // ---------------------------------------------------------------------------- combine
-__global__ void __launch_bounds__(kCombineWarps * 32) march_combine_kernel(GridView g, int64_t n, RenderParams p,
-                                                                           MarchPtrs st, MarchHeader expect,
-                                                                           float *__restrict__ rgb,
-                                                                           float *__restrict__ T_out) {
-    const int lane = threadIdx.x & 31;
-    const int64_t ray = (int64_t)blockIdx.x * kCombineWarps + (threadIdx.x >> 5);
-    if (ray >= n) return;
-    if (!header_matches(*st.hdr, expect)) {  // uniform over the grid: the state holds no plan of these rays
-        if (ray == 0 && lane == 0) report(g.status, kDevStateMismatch);
-        return;
-    }
+// One ray's combine: T before each chunk, the colour (and, with `target`, the MSE gradient and the
+// ray's squared error into *loss_slot), and the colour arriving after each chunk for the adjoint.
+__device__ __forceinline__ void combine_ray(const RenderParams &p, const MarchPtrs &st, int64_t ray, int lane,
+                                            float *__restrict__ rgb, float *__restrict__ T_out,
+                                            const float *__restrict__ target, float *__restrict__ grad_rgb,
+                                            float inv_n, float *loss_slot) {
     const int mc = st.max_chunks;
     const int nch = (st.n_occ[ray] + 31) >> 5;
     float4 *part = st.part + ray * mc;
@@ -372,10 +367,19 @@ __global__ void __launch_bounds__(kCombineWarps * 32) march_combine_kernel(GridV
     C[1] = warp_sum(C[1]);
     C[2] = warp_sum(C[2]);
     if (lane == 0) {
-        rgb[3 * ray + 0] = fmaf(Tc, p.bg[0], C[0]);
-        rgb[3 * ray + 1] = fmaf(Tc, p.bg[1], C[1]);
-        rgb[3 * ray + 2] = fmaf(Tc, p.bg[2], C[2]);
+        float sq = 0.0f;
+#pragma unroll
+        for (int ch = 0; ch < 3; ++ch) {
+            const float c = fmaf(Tc, p.bg[ch], C[ch]);
+            rgb[3 * ray + ch] = c;
+            if (target) {
+                const float diff = c - __ldg(target + 3 * ray + ch);
+                grad_rgb[3 * ray + ch] = 2.0f * diff * inv_n;
+                sq = fmaf(diff, diff, sq);
+            }
+        }
         if (T_out) T_out[ray] = Tc;
+        if (loss_slot) *loss_slot = sq;
     }
     // reverse over chunks: the colour that arrives after each chunk
     float Rs[3] = {Tc * p.bg[0], Tc * p.bg[1], Tc * p.bg[2]};
@@ -397,11 +401,41 @@ __global__ void __launch_bounds__(kCombineWarps * 32) march_combine_kernel(GridV
     }
 }
 
+// With `target`, the kernel also forms the MSE gradient 2 (C - target) / n (Sec. 3.4) and adds
+// L = sum |C - target|^2 / n to *loss (one atomic per CTA).
+__global__ void __launch_bounds__(kCombineWarps * 32) march_combine_kernel(GridView g, int64_t n, RenderParams p,
+                                                                           MarchPtrs st, MarchHeader expect,
+                                                                           float *__restrict__ rgb,
+                                                                           float *__restrict__ T_out,
+                                                                           const float *__restrict__ target,
+                                                                           float *__restrict__ grad_rgb,
+                                                                           float *__restrict__ loss, float inv_n) {
+    __shared__ float s_loss[kCombineWarps];
+    const int lane = threadIdx.x & 31;
+    const int wid = threadIdx.x >> 5;
+    const int64_t ray = (int64_t)blockIdx.x * kCombineWarps + wid;
+    if (target && loss && lane == 0) s_loss[wid] = 0.0f;
+    if (!header_matches(*st.hdr, expect)) {  // uniform over the grid: no plan of these rays
+        if (blockIdx.x == 0 && threadIdx.x == 0) report(g.status, kDevStateMismatch);
+        return;
+    }
+    if (ray < n) combine_ray(p, st, ray, lane, rgb, T_out, target, grad_rgb, inv_n, target && loss ? &s_loss[wid] : nullptr);
+    if (target && loss) {
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            float acc = 0.0f;
+            for (int w = 0; w < kCombineWarps; ++w) acc += s_loss[w];
+            if (acc != 0.0f) atomicAdd(loss, acc * inv_n);
+        }
+    }
+}
+
+
 // ---------------------------------------------------------------------------- adjoint
 
 // With the forward's stored values (VALS) the adjoint gathers no rows: half the registers, twice the
 // resident warps to hide the index loads and atomics.
-constexpr int kBwdValsBlocks = 5;
+constexpr int kBwdValsBlocks = 6;
 
 template <int FORM, bool VALS>
 __global__ void __launch_bounds__(kChunkWarps * 32, VALS ? kBwdValsBlocks : kGatherBlocks) march_chunks_bwd_kernel(
@@ -519,8 +553,12 @@ cudaError_t launch_march_plan(const GridView &g, const float *o, const float *d,
 
 cudaError_t launch_render_planned(const GridView &g, const float *o, const float *d, int64_t n,
                                   const RenderParams &p, const MarchPtrs &st, const MarchHeader &hdr, float *rgb,
-                                  float *T_end, cudaStream_t s) {
-    if (hdr.mode == kMarchRecompute) return launch_render(g, o, d, n, p, rgb, T_end, s);
+                                  float *T_end, const float *target, float *grad_rgb, float *loss, cudaStream_t s) {
+    if (hdr.mode == kMarchRecompute) {
+        cudaError_t e = launch_render(g, o, d, n, p, rgb, T_end, s);
+        if (e == cudaSuccess && target) e = launch_mse_grad(rgb, target, n, grad_rgb, loss, s);
+        return e;
+    }
     if (n == 0) return cudaSuccess;
     const unsigned grid = chunk_grid(n, st.max_chunks);
     if (g.form == PLX_SH_F32)
@@ -528,7 +566,7 @@ cudaError_t launch_render_planned(const GridView &g, const float *o, const float
     else
         march_chunks_fwd_kernel<PLX_SH_BF16><<<grid, kChunkWarps * 32, 0, s>>>(g, o, d, p, st, hdr);
     march_combine_kernel<<<(unsigned)((n + kCombineWarps - 1) / kCombineWarps), kCombineWarps * 32, 0, s>>>(
-        g, n, p, st, hdr, rgb, T_end);
+        g, n, p, st, hdr, rgb, T_end, target, grad_rgb, loss, (float)(1.0 / (double)n));
     return cudaGetLastError();
 }
 
@@ -537,7 +575,7 @@ cudaError_t launch_render_train(const GridView &g, const float *o, const float *
                                 cudaStream_t s) {
     cudaError_t e = launch_march_plan(g, o, d, n, p, st, hdr, s);
     if (e != cudaSuccess) return e;
-    return launch_render_planned(g, o, d, n, p, st, hdr, rgb, T_end, s);
+    return launch_render_planned(g, o, d, n, p, st, hdr, rgb, T_end, nullptr, nullptr, nullptr, s);
 }
 
 cudaError_t launch_render_backward_train(const GridView &g, const float *o, const float *d, int64_t n,

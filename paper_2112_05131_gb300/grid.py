@@ -227,6 +227,19 @@ class Grid:
                _p(T_end), _p(state), state.numel(), _stream(stream))
         return rgb
 
+    def render_planned_mse(self, origins: torch.Tensor, dirs: torch.Tensor, opts: RenderOpts, state: torch.Tensor,
+                           target: torch.Tensor, rgb: torch.Tensor, grad_rgb: torch.Tensor,
+                           loss: Optional[torch.Tensor] = None, stream=None):
+        """plx_render_planned_mse: colours, the MSE gradient and the loss of a planned training batch."""
+        n = origins.shape[0]
+        _need(target, torch.float32, "target", (n, 3))
+        _need(rgb, torch.float32, "rgb", (n, 3))
+        _need(grad_rgb, torch.float32, "grad_rgb", (n, 3))
+        _need(state, torch.uint8, "state")
+        L.call("plx_render_planned_mse", self.handle, _p(origins), _p(dirs), n, ctypes.byref(opts.c()), _p(target),
+               _p(rgb), _p(grad_rgb), _p(loss), _p(state), state.numel(), _stream(stream))
+        return rgb
+
     def render_backward_train(self, origins, dirs, grad_rgb, opts: RenderOpts, state: torch.Tensor,
                               grad_rows: Optional[torch.Tensor] = None, stream=None):
         """plx_render_backward_train: the adjoint of the last render_train on these rays, from its state."""

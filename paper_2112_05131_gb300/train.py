@@ -1,8 +1,8 @@
 """The optimisation step of Sec. 3.4 as a sequence of library calls, and the learning-rate schedules.
 
 One step (Supp. A.1: 5000-ray batches, RMSProp, stochastic TV on contiguous segments):
-  plx_gen_rays -> plx_march_plan -> plx_render_planned -> plx_mse_grad -> plx_render_backward_train
-  -> plx_tv_grad -> plx_rmsprop_step
+  plx_gen_rays -> plx_march_plan -> plx_render_planned_mse (forward and MSE gradient)
+  -> plx_render_backward_train -> plx_tv_grad -> plx_rmsprop_step
 all libplenoxel calls with no host synchronisation.  The training march splits rays into chunk work
 items and hands the march state from the forward to the adjoint.
 
@@ -19,11 +19,11 @@ from typing import List, Optional
 
 import torch
 
-from .grid import ROW, Grid, RenderOpts, gen_rays, mse_grad
+from .grid import ROW, Grid, RenderOpts, gen_rays
 
-# kernels one step enqueues with stop_thresh = 0: gen_rays, march_plan (header, plan), render_planned
-# (chunks, combine), mse, backward_train, tv, rmsprop (compact, apply; sparse mode)
-LAUNCHES_PER_STEP = 11
+# kernels one step enqueues with stop_thresh = 0: gen_rays, march_plan (header, setup, plan),
+# render_planned_mse (chunks, combine with the MSE gradient), backward_train, tv, rmsprop (compact, apply)
+LAUNCHES_PER_STEP = 10
 
 
 def lr_sigma(step: int, init: float = 30.0, final: float = 0.05, max_steps: int = 250000, delay_steps: int = 15000,
@@ -103,9 +103,9 @@ class Trainer:
              seg_len: Optional[torch.Tensor], n_selected: int, lr_s: float, lr_h: float,
              events: Optional[List[torch.cuda.Event]] = None, stream=None):
         """One optimisation step.  `events`, if given, holds 8 events recorded on the main stream; the 7
-        intervals between them are the stages named in STAGES (serial mode: rays and plan, -, forward, MSE,
-        adjoint, TV, update; overlap mode: the previous step's update, the wait for this step's plan,
-        forward, MSE, adjoint, the wait for TV, -).  In overlap mode call finish() after the last step."""
+        intervals between them are the stages named in STAGES (serial mode: rays and plan, -, forward with
+        the MSE gradient, -, adjoint, TV, update; overlap mode: the previous step's update, the wait for this
+        step's plan, forward with the MSE gradient, -, adjoint, the wait for TV, -).  In overlap mode call finish() after the last step."""
         g, c = self.grid, self.cfg
         n = pix.shape[0]
         o, d, rgb, grgb = self.o[:n], self.d[:n], self.rgb[:n], self.grad_rgb[:n]
@@ -123,9 +123,8 @@ class Trainer:
             g.march_plan(o, d, c.opts, self.state, stream=main)
             mark(1)
             mark(2)
-            g.render_planned(o, d, c.opts, self.state, rgb, stream=main)
+            g.render_planned_mse(o, d, c.opts, self.state, target, rgb, grgb, self.loss, stream=main)
             mark(3)
-            mse_grad(rgb, target, grgb, self.loss, stream=main)
             mark(4)
             g.render_backward_train(o, d, grgb, c.opts, self.state, self.grad, stream=main)
             mark(5)
@@ -165,9 +164,8 @@ class Trainer:
             ev["tv"].record(self.tv_stream)
         ms.wait_event(ev["plan"])
         mark(2)
-        g.render_planned(o, d, c.opts, self.state, rgb, stream=ms)
+        g.render_planned_mse(o, d, c.opts, self.state, target, rgb, grgb, self.loss, stream=ms)
         mark(3)
-        mse_grad(rgb, target, grgb, self.loss, stream=ms)
         mark(4)
         g.render_backward_train(o, d, grgb, c.opts, self.state, self.grad, stream=ms)
         ev["bwd"].record(ms)
@@ -184,5 +182,5 @@ class Trainer:
         return rgb
 
     # the 7 intervals between step()'s 8 events: serial mode | overlap mode
-    STAGES = ("rays_plan|prev_update", "-|plan_wait", "render", "mse_grad", "render_backward", "tv_grad|tv_wait",
+    STAGES = ("rays_plan|prev_update", "-|plan_wait", "render", "-", "render_backward", "tv_grad|tv_wait",
               "rmsprop_step|-")

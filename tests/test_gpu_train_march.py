@@ -293,3 +293,34 @@ def test_overlapped_trainer_matches_serial(cuda_lib, form):
     ga.check()
     gb.check()
     assert np.allclose(losses["a"], losses["b"], rtol=1e-3), losses
+
+
+def test_planned_mse_matches_oracle(cuda_lib):
+    """plx_render_planned_mse: the colours, dL/dC = 2 (C - target) / n and L of the batch against the
+    oracle's render and MSE."""
+    from paper_2112_05131_gb300.grid import Grid, RenderOpts
+
+    opts = RenderOpts(0.5, BG, 0.0)
+    sc = _sparse_scene(40, 0.2, 25)
+    g = Grid.from_host(sc.R, sc.idx, sc.rows)
+    n = 1500
+    o, d = synth.random_rays(n, seed=26)
+    tgt = np.random.default_rng(27).uniform(0, 1, size=(n, 3)).astype(np.float32)
+    ot, dt = torch.from_numpy(o).cuda(), torch.from_numpy(d).cuda()
+    st = g.new_march_state(n, opts)
+    rgb = torch.empty((n, 3), device="cuda")
+    grad = torch.empty((n, 3), device="cuda")
+    loss = torch.zeros(1, device="cuda")
+    g.march_plan(ot, dt, opts, st)
+    g.render_planned_mse(ot, dt, opts, st, torch.from_numpy(tgt).cuda(), rgb, grad, loss)
+    g.check()
+    ref, aux = oracle.render(sc.R, sc.idx, sc.rows, o.astype(float), d.astype(float), bg=BG)
+    check_colours(rgb.cpu().numpy(), ref, aux, sc.rows, delta_of(40, 0.5), BG)
+    L_ref, g_ref = oracle.mse(rgb.cpu().numpy().astype(np.float64), tgt.astype(np.float64))
+    assert np.allclose(grad.cpu().numpy(), g_ref, rtol=1e-6, atol=1e-12)
+    assert loss.item() == pytest.approx(L_ref, rel=1e-5)
+    # the same state then drives the adjoint
+    gr = g.render_backward_train(ot, dt, grad, opts, st)
+    gref = oracle.render_backward(sc.R, sc.idx, sc.rows, o.astype(float), d.astype(float),
+                                  grad.cpu().numpy().astype(np.float64), bg=BG)
+    check_grads(gr.cpu().numpy(), gref)
