@@ -63,7 +63,9 @@ def _load():
             "orc_mse": (D, [P, P, I64, P]),
             "orc_tv": (D, [I64, P, P, I64, P, P, I64, D, D, P]),
             "orc_rmsprop": (None, [I64, P, P, P, D, D, D, D]),
+            "orc_max_weight": (None, [I64, P, P, I64, P, P, P, I64, P, P]),
             "orc_prune": (I64, [I64, P, P, I64, D, ctypes.c_int, P, P]),
+            "orc_prune_key": (I64, [I64, P, P, I64, P, D, ctypes.c_int, P, P]),
             "orc_upsample": (I64, [I64, P, P, I64, I64, P, P]),
             "orc_round_bf16": (None, [P, I64]),
             "orc_num_threads": (ctypes.c_int, []),
@@ -258,6 +260,38 @@ def prune(R, idx, rows, tau, dilate=True):
     m = lib.orc_prune(R, _p(idx), _p(rows), rows.shape[1], float(tau), int(bool(dilate)), _p(idx_out), None)
     rows_out = np.empty((m, rows.shape[1]), np.float64)
     lib.orc_prune(R, _p(idx), _p(rows), rows.shape[1], float(tau), int(bool(dilate)), _p(idx_out), _p(rows_out))
+    return idx_out, rows_out
+
+
+def max_weight(R, idx, rows, o, d, step_vox=0.5, stop_thresh=0.0, aabb=None, wmax=None):
+    """Largest sample weight T_s alpha_s crediting each row over the rays (the weight-threshold prune's
+    key, Sec. 3.4): a sample credits the 8 corner nodes of its cell.  Returns wmax [M] FP64 (max-updated
+    in place when given)."""
+    lib = _load()
+    idx = _c(idx, np.int32)
+    rows = _rows(rows)
+    o = _c(o, np.float64)
+    d = _c(d, np.float64)
+    if wmax is None:
+        wmax = np.zeros(rows.shape[0], np.float64)
+    assert wmax.dtype == np.float64 and wmax.flags.c_contiguous and wmax.shape == (rows.shape[0],)
+    lib.orc_max_weight(R, _p(idx), _p(rows), rows.shape[1], _p(_aabb(aabb)), _p(o), _p(d), o.shape[0],
+                       _p(_opts(step_vox, 0.0, stop_thresh)), _p(wmax))
+    return wmax
+
+
+def prune_key(R, idx, rows, key, tau, dilate=True):
+    """Prune with dilation on a per-row key (hot = key >= tau).  Returns (idx', rows' [M',stride])."""
+    lib = _load()
+    idx = _c(idx, np.int32)
+    rows = _rows(rows)
+    key = _c(key, np.float64)
+    assert key.shape == (rows.shape[0],)
+    idx_out = np.empty(R ** 3, np.int32)
+    args = (R, _p(idx), _p(rows), rows.shape[1], _p(key), float(tau), int(bool(dilate)), _p(idx_out))
+    m = lib.orc_prune_key(*args, None)
+    rows_out = np.empty((m, rows.shape[1]), np.float64)
+    lib.orc_prune_key(*args, _p(rows_out))
     return idx_out, rows_out
 
 

@@ -38,7 +38,13 @@
  *                       equals it where T_{s+1} c and R_s do not cancel
  *   orc_tv              pinned: linear-ramp closed form, finite differences
  *   orc_rmsprop         pinned: constant-gradient closed form
+ *   orc_max_weight      pinned: closed form exp(-sigma s delta)(1 - exp(-sigma
+ *                       delta)) on a constant field along an axis, which also
+ *                       fixes the 8-corner attribution; max over a union of
+ *                       ray sets = elementwise max; empty grid = all zero
  *   orc_prune           pinned: exhaustive 3x3x3 enumeration on small grids
+ *   orc_prune_key       pinned: equals orc_prune for key = density; exhaustive
+ *                       enumeration with a random key
  *   orc_upsample        pinned: affine field resampled exactly; exhaustive
  *                       support enumeration on small grids
  *   orc_round_bf16      pinned: exact RNE cases (ties, carries) by hand
@@ -460,6 +466,55 @@ void orc_render_backward_mag(int64_t R, const int32_t *idx, const double *rows, 
 }
 
 /* ------------------------------------------------------------------------- */
+/* Maximum sample weight per node over a set of rays, the key of the        */
+/* weight-threshold prune (Sec. 3.4 "Coarse to Fine": a voxel is dropped    */
+/* when its weight T_i (1 - exp(-sigma_i delta_i)) stays under a threshold   */
+/* on every training ray).  Samples and weights are those of orc_render.    */
+/* Reading (values live on the nodes, Sec. 3): a sample counts toward every  */
+/* one of the 8 corner nodes of the cell it lies in -- the nodes its values  */
+/* are interpolated from -- whatever its trilinear weights; a NULL corner    */
+/* has no row and takes nothing.                                             */
+/*   wmax[row] = max(wmax[row], max over samples s crediting row of w_s)     */
+/* wmax [M] is updated in place (callers start from zeros and may call again */
+/* with more rays).                                                          */
+/* ------------------------------------------------------------------------- */
+void orc_max_weight(int64_t R, const int32_t *idx, const double *rows, int64_t row_stride,
+                    const double *aabb, const double *o, const double *d, int64_t n,
+                    const double *opts, double *wmax)
+{
+    orc_grid g;
+    grid_init(&g, R, idx, rows, row_stride, aabb);
+    double hmin = g.h[0] < g.h[1] ? g.h[0] : g.h[1];
+    if (g.h[2] < hmin) hmin = g.h[2];
+    double delta = opts[0] * hmin;
+    double bg[3] = {opts[1], opts[2], opts[3]};
+    double stop = opts[4];
+    double diag = 0.0;
+    for (int a = 0; a < 3; ++a) diag += (g.hi[a] - g.lo[a]) * (g.hi[a] - g.lo[a]);
+    int64_t cap = (int64_t)(sqrt(diag) / delta) + 4;
+#pragma omp parallel
+    {
+        orc_sample *smp = (orc_sample *)malloc(sizeof(orc_sample) * (size_t)cap);
+#pragma omp for schedule(dynamic, 8)
+        for (int64_t r = 0; r < n; ++r) {
+            orc_ray_out res;
+            int64_t ns = march(&g, o + 3 * r, d + 3 * r, delta, bg, stop, &res, smp, cap);
+            if (ns > cap) ns = cap;
+            for (int64_t s = 0; s < ns; ++s) {
+                double w = smp[s].w;
+                for (int c = 0; c < 8; ++c) {
+                    int32_t row = g.idx[smp[s].node[c]];
+                    if (row < 0) continue;
+#pragma omp atomic compare
+                    if (wmax[row] < w) { wmax[row] = w; }
+                }
+            }
+        }
+        free(smp);
+    }
+}
+
+/* ------------------------------------------------------------------------- */
 /* MSE reconstruction loss over the ray batch (Eq. 2, Sec. 3.4):             */
 /*   L = 1/|R| sum_r ||C_r - Chat_r||_2^2,  dL/dChat = 2 (Chat - C) / |R|.   */
 /* ------------------------------------------------------------------------- */
@@ -563,21 +618,28 @@ void orc_rmsprop(int64_t M, double *x, double *v, double *grad, double lr_sigma,
 }
 
 /* ------------------------------------------------------------------------- */
-/* Prune by density threshold with dilation (Sec. 3.4 "Coarse to Fine").    */
-/* hot(n)  = node n occupied and sigma(n) >= tau                             */
+/* Pruning with dilation (Sec. 3.4 "Coarse to Fine").  A node is hot when it */
+/* is occupied and its key is at least tau; the key is its density (the     */
+/* density-threshold form) or a per-row value the caller supplies (the       */
+/* weight-threshold form, with the rows' maximum weights, orc_max_weight).   */
+/* hot(n)  = node n occupied and key(n) >= tau                               */
 /* keep(n) = node n occupied and (dilate ? any hot node in the 3x3x3         */
 /*           neighbourhood of n clipped to the grid : hot(n))                */
 /* Kept nodes get new row ids in ascending n; their rows are copied.         */
 /* idx_out [R^3]; rows_out [n_keep, row_stride] may be NULL (count only).    */
 /* Returns n_keep.                                                           */
 /* ------------------------------------------------------------------------- */
-int64_t orc_prune(int64_t R, const int32_t *idx, const double *rows, int64_t row_stride,
-                  double tau, int dilate, int32_t *idx_out, double *rows_out)
+static int64_t prune_impl(int64_t R, const int32_t *idx, const double *rows, int64_t row_stride,
+                          const double *key, double tau, int dilate, int32_t *idx_out, double *rows_out)
 {
     int64_t N = R * R * R;
     unsigned char *hot = (unsigned char *)malloc((size_t)N);
-    for (int64_t n = 0; n < N; ++n)
-        hot[n] = idx[n] >= 0 && rows[(int64_t)idx[n] * row_stride] >= tau;
+    for (int64_t n = 0; n < N; ++n) {
+        hot[n] = 0;
+        if (idx[n] < 0) continue;
+        double k = key ? key[idx[n]] : rows[(int64_t)idx[n] * row_stride];
+        hot[n] = k >= tau;
+    }
     int64_t next = 0;
     for (int64_t n = 0; n < N; ++n) {
         int keep = 0;
@@ -607,6 +669,20 @@ int64_t orc_prune(int64_t R, const int32_t *idx, const double *rows, int64_t row
     }
     free(hot);
     return next;
+}
+
+/* density-threshold form: key = sigma (row column 0) */
+int64_t orc_prune(int64_t R, const int32_t *idx, const double *rows, int64_t row_stride,
+                  double tau, int dilate, int32_t *idx_out, double *rows_out)
+{
+    return prune_impl(R, idx, rows, row_stride, NULL, tau, dilate, idx_out, rows_out);
+}
+
+/* weight-threshold form: key [M], one value per row */
+int64_t orc_prune_key(int64_t R, const int32_t *idx, const double *rows, int64_t row_stride,
+                      const double *key, double tau, int dilate, int32_t *idx_out, double *rows_out)
+{
+    return prune_impl(R, idx, rows, row_stride, key, tau, dilate, idx_out, rows_out);
 }
 
 /* ------------------------------------------------------------------------- */

@@ -591,14 +591,23 @@ def test_rmsprop_constant_gradient_closed_form():
 
 # ----------------------------------------------------------------------------- prune / upsample
 
-def test_prune_matches_exhaustive_neighbourhoods():
+@pytest.mark.parametrize("mode", ["density", "key"])
+def test_prune_matches_exhaustive_neighbourhoods(mode):
     R = 6
     idx, rows = random_sparse(R, 0.3, 110, sigma_range=(0, 10))
     tau = 7.0
-    rows[0, 0] = tau  # sigma == tau counts as hot
+    if mode == "density":
+        rows[0, 0] = tau  # sigma == tau counts as hot
+        key = rows[:, 0]
+    else:  # an unrelated per-row key (the weight-threshold form)
+        key = np.random.default_rng(111).uniform(0, 10, size=rows.shape[0])
+        key[1] = tau
     for dilate in (True, False):
-        idx2, rows2 = oracle.prune(R, idx, rows, tau, dilate)
-        hot = lambda i, j, k: idx[(i * R + j) * R + k] >= 0 and rows[idx[(i * R + j) * R + k], 0] >= tau
+        if mode == "density":
+            idx2, rows2 = oracle.prune(R, idx, rows, tau, dilate)
+        else:
+            idx2, rows2 = oracle.prune_key(R, idx, rows, key, tau, dilate)
+        hot = lambda i, j, k: idx[(i * R + j) * R + k] >= 0 and key[idx[(i * R + j) * R + k]] >= tau
         expect_idx = np.full(R ** 3, -1, np.int32)
         kept = []
         for i, j, k in itertools.product(range(R), repeat=3):
@@ -615,6 +624,75 @@ def test_prune_matches_exhaustive_neighbourhoods():
                 kept.append(rows[idx[n]])
         assert np.array_equal(idx2, expect_idx)
         assert np.array_equal(rows2, np.array(kept).reshape(-1, NV))
+
+
+def test_prune_key_with_density_key_equals_density_prune():
+    R = 7
+    idx, rows = random_sparse(R, 0.5, 112, sigma_range=(0, 10))
+    for dilate in (True, False):
+        a = oracle.prune(R, idx, rows, 4.0, dilate)
+        b = oracle.prune_key(R, idx, rows, rows[:, 0].copy(), 4.0, dilate)
+        assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
+
+
+# ----------------------------------------------------------------------------- maximum weight (prune key)
+
+@pytest.mark.parametrize("stop", [0.0, 0.5])
+def test_max_weight_constant_field_closed_form(stop):
+    """Density sigma0 on every node, a ray along +x at off-lattice grid coordinates (y, z) = (j0 + 0.3,
+    k0 + 0.6), entering the box at grid x = 0, step 0.37 voxel.  Sample s sits at grid x = 0.37 s, has
+    T_s = exp(-sigma0 s delta) and weight T_s (1 - exp(-sigma0 delta)), and is taken while T_s >= stop.
+    It credits the 8 corners of cell floor(0.37 s): nodes (i, j, k) with i in {cell, cell + 1}, j in
+    {j0, j0 + 1}, k in {k0, k0 + 1}.  Each of those nodes holds the largest weight crediting it (the
+    earliest sample, weights falling along the ray); all other nodes hold 0."""
+    R, step, sigma0 = 9, 0.37, 1.7
+    h = 2.0 / (R - 1)
+    delta = step * h
+    j0, k0 = 3, 5
+    idx, rows = constant_field(R, sigma0, (0.3, 0.2, 0.1))
+    o = np.array([[-3.0, -1.0 + h * (j0 + 0.3), -1.0 + h * (k0 + 0.6)]])
+    d = np.array([[1.0, 0.0, 0.0]])
+    w = oracle.max_weight(R, idx, rows, o, d, step_vox=step, stop_thresh=stop)
+    alpha = 1.0 - math.exp(-sigma0 * delta)
+    expect = np.zeros(R ** 3)
+    s = 0
+    while 0.37 * s < R - 1:
+        T = math.exp(-sigma0 * s * delta)
+        if T < stop:
+            break
+        cell = min(math.floor(0.37 * s), R - 2)
+        for i, j, k in itertools.product((cell, cell + 1), (j0, j0 + 1), (k0, k0 + 1)):
+            n = (i * R + j) * R + k
+            expect[n] = max(expect[n], T * alpha)
+        s += 1
+    assert np.count_nonzero(expect) == (4 * R if stop == 0 else np.count_nonzero(expect))
+    assert np.max(np.abs(w - expect)) < 1e-14
+    # the first sample (x = 0) credits the far corners of cell 0 although its trilinear weight there is 0
+    assert w[(1 * R + j0) * R + k0] == pytest.approx(alpha, rel=1e-14)
+
+
+def test_max_weight_union_of_ray_sets_is_the_elementwise_max():
+    R = 10
+    idx, rows = random_sparse(R, 0.6, 113, sigma_range=(0, 30))
+    o, d = synth.random_rays(120, seed=114)
+    wa = oracle.max_weight(R, idx, rows, o[:70], d[:70])
+    wb = oracle.max_weight(R, idx, rows, o[70:], d[70:])
+    wab = oracle.max_weight(R, idx, rows, o, d)
+    assert np.array_equal(wab, np.maximum(wa, wb))
+    again = oracle.max_weight(R, idx, rows, o[70:], d[70:], wmax=wa.copy())  # in-place continuation
+    assert np.array_equal(again, wab)
+    # every weight is at most the ray's total weight 1 - T_end (weights sum with T_end to one)
+    _, aux = oracle.render(R, idx, rows, o, d, bg=0.0)
+    assert 0.0 < wab.max() <= np.max(1.0 - aux[:, 0]) + 1e-15
+    assert np.all(wab >= 0.0)
+
+
+def test_max_weight_zero_density_is_zero():
+    R = 6
+    idx, rows = random_sparse(R, 0.2, 115, sigma_range=(0, 1))
+    rows[:, 0] = 0.0
+    o, d = synth.random_rays(40, seed=116)
+    assert np.all(oracle.max_weight(R, idx, rows, o, d) == 0.0)
 
 
 @pytest.mark.parametrize("R,R2", [(5, 9), (5, 10), (4, 7), (6, 11)])
