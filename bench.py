@@ -7,7 +7,7 @@ thin shell, SH ~ N(0, 0.2), the training grid = that ground truth + N(0, 0.02)),
 100 cameras of 800x800 on the upper hemisphere, 5000-ray batches drawn uniformly
 from all pixels, step 0.5 voxel, white background.  One step runs every
 per-step kernel of the method: ray generation, forward march, MSE gradient,
-adjoint, TV gradient on 1% of the nodes in 4096-node segments (Supp. A.1), and
+adjoint, TV gradient on 1% of the nodes in 4096-node segments (Supp. B.1), and
 the sparse RMSProp update.  Targets are the ground truth rendered by the same
 kernels before timing.  The grid (1.0 GB in FP32) exceeds the 129 MB L2, and
 every step uses a different batch; L2 is not flushed between steps.
@@ -60,6 +60,8 @@ def parse_args():
     ap.add_argument("--skip-serving", action="store_true", help="leave out the serving measurement")
     ap.add_argument("--skip-c2f", action="store_true", help="leave out the coarse-to-fine run")
     ap.add_argument("--c2f-steps", type=int, default=12800)
+    ap.add_argument("--c2f-prune", choices=("density", "weight"), default="density",
+                    help="coarse-to-fine pruning: density >= 5, or maximum weight >= 0.256 (Sec. 3.4)")
     ap.add_argument("--skip-large-batch", action="store_true", help="leave out the 2^18-ray batch measurement")
     return ap.parse_args()
 
@@ -169,6 +171,55 @@ def load_peaks():
         d = json.load(open(p))
         return float(d["hbm_gbs"]), "measured"
     return 6800.0, "fallback"
+
+
+# DRAM traffic of the step's kernels, from a one-pass ncu capture summarised in profiles/, valid only
+# while the library's sources are those the capture ran (their digest is recorded beside the table)
+TRAFFIC_PROFILE = os.path.join(ROOT, "profiles", "traffic_sparse512.md")
+STAGE_KERNELS = {"render": ("march_chunks_fwd_kernel", "march_combine_kernel"),
+                 "render_backward": ("march_chunks_bwd_kernel",),
+                 "rmsprop_step": ("rms_compact_kernel", "rms_apply_kernel"),
+                 "tv_grad": ("tv_kernel",)}
+
+
+def library_digest() -> str:
+    """sha256 (first 16 hex digits) of the library's CUDA sources and its header, in name order."""
+    import glob
+    import hashlib
+
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2112_05131_gb300", "csrc")
+    files = sorted(glob.glob(os.path.join(csrc, "*.cu")) + glob.glob(os.path.join(csrc, "*.cuh")))
+    for f in files + [os.path.join(ROOT, "include", "plenoxel.h")]:
+        h.update(os.path.basename(f).encode())
+        with open(f, "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic(stage: str, workload: str):
+    """(bytes per launch of the stage's kernels, note); bytes is None unless the summary covers this workload
+    and was captured from the current sources."""
+    if workload != "sparse512" or not os.path.exists(TRAFFIC_PROFILE):
+        return None, "no capture of this workload"
+    text = open(TRAFFIC_PROFILE).read()
+    digest = None
+    table = {}
+    for line in text.splitlines():
+        if line.startswith("Library source digest:"):
+            digest = line.split("`")[1]
+        cells = [c.strip() for c in line.strip().strip("|").split("|")]
+        if line.startswith("|") and len(cells) >= 4 and cells[0].split(" ")[0].endswith("_kernel"):
+            try:
+                table[cells[0].split(" ")[0]] = float(cells[3]) * 1e6
+            except ValueError:
+                pass
+    if digest != library_digest():
+        return None, f"sources changed since the capture (captured {digest}, now {library_digest()})"
+    try:
+        return sum(table[k] for k in STAGE_KERNELS[stage]), f"ncu dram__bytes_read+write, digest {digest}"
+    except KeyError:
+        return None, "kernel missing from the capture"
 
 
 # --------------------------------------------------------------------------- workload
@@ -363,11 +414,13 @@ def extras(args, wl, dev_batches, cams_t, gt_grid, opts, timed_loop, st32, ms32)
                 "rmsprop_step": "rms_compact + rms_apply", "tv_grad": "tv_kernel"}
     dom = max(per_launch, key=lambda k: st32[k])
     ach = per_launch[dom] / (st32[dom] / 1e3) / 1e9
+    traffic, traffic_note = profiled_traffic(dom, args.workload)
     res["roofline"] = {"kernel": f"{dom} ({launches[dom]})", "bound": "hbm", "achieved": ach, "peak": peak,
                        "unit": "GB/s", "frac": ach / peak,
                        "peak_source": f"{peak_kind} hbm_gbs (STREAM-style copy), burst",
                        "timing": "CUDA events around the stage on the launching stream, serial run",
-                       "algorithmic_bytes_per_launch": per_launch[dom], "traffic": None}
+                       "algorithmic_bytes_per_launch": per_launch[dom], "traffic": traffic,
+                       "traffic_source": traffic_note, "library_digest": library_digest()}
     res["algorithmic"] = {"distinct_nodes_per_ray": nodes / n, "occupied_nodes_per_ray": occ / n,
                           "marched_samples_per_ray": samples / n,
                           "touched_rows_per_step": float(np.mean(touched)),
@@ -478,7 +531,35 @@ def extras(args, wl, dev_batches, cams_t, gt_grid, opts, timed_loop, st32, ms32)
         kept = gp.M
         del gp
     res["grid_ops"] = {"prune_sigma5_ms": min(t), "prune_kept_rows": kept, "rows": g.M}
+    # weight-threshold prune (Sec. 3.4): maximum weight over every pixel ray of every training view, then
+    # the keyed prune at the paper's synthetic threshold 0.256.  The workload's densities (peak 50) give a
+    # sample at most alpha = 0.09 at 512^3, so no weight would reach 0.256: the grid's densities are scaled
+    # x20 for this measurement (peak 1000, sharp surfaces as in trained synthetic scenes).
     del g
+    torch.cuda.empty_cache()
+    rows_op = wl["train"].rows.copy()
+    rows_op[:, 0] *= np.float32(20.0)
+    g = Grid.from_host(R, wl["train"].idx, rows_op)
+    del rows_op
+    stream = torch.cuda.current_stream()
+    wmax = torch.zeros(g.M, dtype=torch.float32, device=cams_t.device)
+    g.max_weight_views(cams_t, W, H, opts, views=[0], wmax=wmax)  # warm-up
+    e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+    wmax.zero_()
+    torch.cuda.synchronize()
+    e0.record(stream)
+    g.max_weight_views(cams_t, W, H, opts, wmax=wmax)
+    e1.record(stream)
+    gp = g.prune(0.256, True, key=wmax)
+    e2.record(stream)
+    torch.cuda.synchronize()
+    n_rays = wl["n_views"] * W * H
+    res["grid_ops"].update({
+        "max_weight_all_views_ms": e0.elapsed_time(e1), "max_weight_rays": n_rays,
+        "max_weight_Mrays_per_s": n_rays / (e0.elapsed_time(e1) / 1e3) / 1e6,
+        "prune_weight0256_ms": e1.elapsed_time(e2), "prune_weight_kept_rows": gp.M,
+        "max_weight_launches": 2 * wl["n_views"]})
+    del g, gp, wmax
     torch.cuda.empty_cache()
     if R >= 64:
         half = synth.scene_config(f"sparse{R // 2}_0.08") if R > 256 else None
@@ -558,14 +639,16 @@ def coarse_to_fine(args, wl, cams_t, gt_grid, opts):
     test_t = torch.from_numpy(synth.cameras_config(wl["test_cams"])).to(cams_t.device)
     truth = render_views(gt_grid, test_t, W, H, opts)
     prep = time.perf_counter() - t0
-    cfg = C2FConfig(steps=args.c2f_steps, upsample_at=(args.c2f_steps // 3, 2 * args.c2f_steps // 3))
+    cfg = C2FConfig(steps=args.c2f_steps, upsample_at=(args.c2f_steps // 3, 2 * args.c2f_steps // 3),
+                    prune_by=args.c2f_prune)
     log = []
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     g = train(images, cams_t, W, H, cfg, log)
     wall = time.perf_counter() - t0
     final = render_views(g, test_t, W, H, opts)
-    out = {"steps": cfg.steps, "batch": cfg.batch, "wall_s": wall, "steps_per_s": cfg.steps / wall,
+    out = {"steps": cfg.steps, "batch": cfg.batch, "prune_by": cfg.prune_by, "wall_s": wall,
+           "steps_per_s": cfg.steps / wall,
            "stages": log, "final_reso": g.reso, "final_rows": g.M,
            "psnr_test_db": psnr(final, truth), "views": {"train": images.shape[0], "test": truth.shape[0]},
            "images_render_s": prep}

@@ -22,7 +22,7 @@
  *   a code in the grid's device status word, skip the access and go on;
  *   plx_check() reports it.  No kernel traps or waits on another kernel.
  *
- * Grid layout (Sec. 3.2; Supp. A.1 "Implementation Details")
+ * Grid layout (Sec. 3.2; Supp. B.1 "Implementation Details")
  * ---------------------------------------------------------
  * - The grid is a dense R x R x R lattice of nodes ("each occupied voxel
  *   corner stores ...", Sec. 3).  Node (i,j,k) has linear id
@@ -53,7 +53,7 @@
  *   its cell (Sec. 3.3): g = clamp((x - aabb_min)/h, 0, R-1),
  *   base = min(floor(g), R-2), f = g - base.
  * - sigma_s = max(0, interpolated sigma); colour c_ch = max(0, sum_l Y_l(d)
- *   k_{ch,l}) with real degree-2 SH Y_0..Y_8 (Sec. 3.2; ReLU per Supp. A.1).
+ *   k_{ch,l}) with real degree-2 SH Y_0..Y_8 (Sec. 3.2; ReLU per Supp. B.1).
  * - Compositing: T_0 = 1, alpha_s = 1 - exp(-sigma_s delta), w_s = T_s
  *   alpha_s, T_{s+1} = T_s (1 - alpha_s); before sample s the march stops if
  *   T_s < stop_thresh; C = sum_s w_s c_s + T_end * bg.
@@ -169,8 +169,8 @@ plx_status plx_gen_rays(const float *d_cams, int32_t n_cams, int32_t W, int32_t 
 plx_status plx_render(const plx_grid *grid, const float *d_origins, const float *d_dirs, int64_t n,
                       const plx_render_opts *opts, float *d_rgb, float *d_T_end, void *stream);
 
-/* Adjoint of plx_render (Sec. 3.4: the renderer is differentiated end to end;
- * Supp. A.1 "gradient kernels").  d_grad_rgb float [n][3] = dL/dC.  Adds
+/* Adjoint of plx_render (Sec. 3.5: the renderer is differentiated end to end;
+ * Supp. B.1 "gradient kernels").  d_grad_rgb float [n][3] = dL/dC.  Adds
  * dL/d(row values) into d_grad_rows F32 [n_rows][32] (+=; padding columns
  * untouched) and marks the rows it touches in the grid's touched bitmask.
  * The march is recomputed (no per-sample state is stored).  Per sample:
@@ -186,7 +186,7 @@ plx_status plx_render_backward(const plx_grid *grid, const float *d_origins, con
 
 /* ---------------------------------------------------------------- training march
  *
- * The forward/adjoint pair of the optimisation step (Sec. 3.4; Supp. A.1:
+ * The forward/adjoint pair of the optimisation step (Sec. 3.5; Supp. B.1:
  * batches of 5000 rays), computing exactly what plx_render and
  * plx_render_backward compute (up to FP32 summation order), but splitting
  * every ray into chunks of 32 compacted samples that run as independent work
@@ -224,7 +224,7 @@ plx_status plx_render_planned(const plx_grid *grid, const float *d_origins, cons
                               const plx_render_opts *opts, float *d_rgb, float *d_T_end, void *d_state,
                               size_t state_bytes, void *stream);
 
-/* plx_render_planned followed by plx_mse_grad in the same kernel (Sec. 3.4: the
+/* plx_render_planned followed by plx_mse_grad in the same kernel (Sec. 3.5: the
  * reconstruction loss of the batch): writes the colours d_rgb, the gradient
  * d_grad_rgb = 2 (C - target) / n and adds L = sum |C - target|^2 / n to
  * *d_loss (if not NULL).  d_target float [n][3]; d_grad_rgb may alias neither
@@ -281,7 +281,22 @@ plx_status plx_render_tiles(const plx_grid *const *grids, int32_t n_grids, const
 plx_status plx_count_nodes(const plx_grid *grid, const float *d_origins, const float *d_dirs, int64_t n,
                            const plx_render_opts *opts, int64_t *d_counts, void *stream);
 
-/* Reconstruction loss of a ray batch (Sec. 3.4, the MSE term of the loss):
+/* Key of the weight-threshold prune (Sec. 3.4 "Coarse to Fine": a voxel is
+ * dropped when its weight T_s (1 - exp(-sigma_s delta)) is small on every
+ * training ray).  Marches the n rays exactly as plx_render and, for every
+ * taken sample with a positive weight, raises d_wmax[r] to that weight for
+ * each occupied corner node (row r) of the sample's cell -- all 8 corners,
+ * whatever their trilinear weights.
+ *   d_origins, d_dirs  float [n][3] device
+ *   d_wmax             float [M] device, updated in place (max); it must hold
+ *                      non-negative values (zeros to start), and calls over
+ *                      further rays continue the maximum
+ * Either SH form (the density is what matters).  Stream-ordered; nothing is
+ * allocated. */
+plx_status plx_max_weight(const plx_grid *grid, const float *d_origins, const float *d_dirs, int64_t n,
+                          const plx_render_opts *opts, float *d_wmax, void *stream);
+
+/* Reconstruction loss of a ray batch (Sec. 3.5, the MSE term of the loss):
  *   L = 1/n sum_r ||C_r - Chat_r||^2  and  dL/dChat_r = 2 (Chat_r - C_r) / n.
  *   d_rgb, d_target  float [n][3]: rendered and target colours
  *   d_grad_rgb       float [n][3] output (may alias neither input)
@@ -291,7 +306,7 @@ plx_status plx_mse_grad(const float *d_rgb, const float *d_target, int64_t n, fl
 
 /* ---------------------------------------------------------------- regulariser / optimiser */
 
-/* Total-variation gradient (Sec. 3.4 loss; Supp. A.1: stochastic contiguous
+/* Total-variation gradient (Sec. 3.5 loss; Supp. B.1: stochastic contiguous
  * segments, differences scaled by R/256, missing density neighbour = 0,
  * missing SH neighbour = own value).  For each selected node v (empty nodes
  * may be selected) and value d:
@@ -308,7 +323,7 @@ plx_status plx_tv_grad(const plx_grid *grid, const int64_t *d_seg_start, const i
                        int64_t n_seg, int64_t n_selected, float lambda_sigma, float lambda_sh,
                        float *d_grad_rows, float *d_loss, void *stream);
 
-/* RMSProp (Sec. 3.4) on every entry with a non-zero gradient:
+/* RMSProp (Sec. 3.5) on every entry with a non-zero gradient:
  *   v <- beta v + (1 - beta) g^2;  x <- x - lr g / (sqrt(v) + eps);  g <- 0,
  * lr = lr_sigma for the density column, lr_sh for the SH columns.  Entries
  * with g == 0 keep x and v unchanged.  Updates the F32 rows in place and,
@@ -341,6 +356,14 @@ plx_status plx_grid_prune_count(const plx_grid *grid, float tau, int32_t dilate,
                                 int64_t *n_keep, void *stream);
 plx_status plx_grid_prune_apply(const plx_grid *grid, const void *d_ws, int64_t n_keep, int32_t *d_idx_new,
                                 float *d_rows_new, void *stream);
+
+/* Weight-threshold pruning (Sec. 3.4 "Coarse to Fine"; the paper's synthetic
+ * and 360-degree scenes use it): as plx_grid_prune_count, but hot(n) =
+ * occupied and d_key[row of n] >= tau, with d_key float [M] on the device
+ * (normally the rows' maximum weights from plx_max_weight; the paper's
+ * synthetic threshold is 0.256).  Follow it with plx_grid_prune_apply. */
+plx_status plx_grid_prune_count_key(const plx_grid *grid, const float *d_key, float tau, int32_t dilate, void *d_ws,
+                                    int64_t *n_keep, void *stream);
 
 /* Trilinear resampling to a new resolution (Sec. 3.4: subdivide and
  * initialise by trilinear interpolation; any resolution).  New node i' along

@@ -4,7 +4,7 @@ Only the test suite, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
 ``bench.py`` may import this package.  It wraps ``plx_oracle.c`` (plain C,
 FP64) through ctypes and shares no code with the CUDA library.  Every function
 takes NumPy arrays and returns NumPy arrays; see the C file for the definition
-each one follows (Eq. 1, Sec. 3.2-3.4, Supp. A.1) and the pin that checks it.
+each one follows (Eq. 1, Sec. 3.2-3.4, Supp. B.1) and the pin that checks it.
 """
 from __future__ import annotations
 
@@ -217,7 +217,7 @@ def render_backward_mag(R, idx, rows, o, d, grad_rgb, step_vox=0.5, bg=(1.0, 1.0
 
 
 def mse(pred, target):
-    """(L, dL/dpred) for Eq. 2's reconstruction term."""
+    """(L, dL/dpred) for the reconstruction term of Eq. 3."""
     lib = _load()
     pred = _c(pred, np.float64)
     target = _c(target, np.float64)
@@ -227,7 +227,7 @@ def mse(pred, target):
 
 
 def tv(R, idx, rows, seg_start, seg_len, lambda_sigma, lambda_sh, grad_rows=None):
-    """TV loss and gradient (Sec. 3.4, Supp. A.1).  Returns (L, grad_rows [M,28])."""
+    """TV loss and gradient (Sec. 3.5, Supp. B.1).  Returns (L, grad_rows [M,28])."""
     lib = _load()
     idx = _c(idx, np.int32)
     rows = _rows(rows)
@@ -241,7 +241,7 @@ def tv(R, idx, rows, seg_start, seg_len, lambda_sigma, lambda_sh, grad_rows=None
 
 
 def rmsprop(x, v, grad, lr_sigma, lr_sh, beta=0.95, eps=1e-8):
-    """RMSProp on entries with non-zero gradient (Sec. 3.4).  Returns new (x, v, grad) FP64."""
+    """RMSProp on entries with non-zero gradient (Sec. 3.5).  Returns new (x, v, grad) FP64."""
     lib = _load()
     x = np.array(x, np.float64, order="C", copy=True)
     v = np.array(v, np.float64, order="C", copy=True)

@@ -12,13 +12,13 @@
  * eye: one loop per definition, FP64 arithmetic, no blocking, no skipping of
  * empty space, no early exits other than the ones the definition states.
  *
- * Grid semantics (Sec. 3.2; Supp. A.1 "Implementation Details"):
+ * Grid semantics (Sec. 3.2; Supp. B.1 "Implementation Details"):
  *   - a dense int32 index volume idx[R*R*R]; idx[n] == -1 is a NULL cell,
  *     otherwise it is the row of that node in the data table;
  *   - node (i,j,k) has linear id n = (i*R + j)*R + k (k fastest, i <-> x);
  *   - a data row holds 28 values [sigma, R0..R8, G0..G8, B0..B8] at
  *     `row_stride` doubles per row (28 or more; FP32 inputs convert exactly);
- *   - NULL cells count as all-zero values (Supp. A.1);
+ *   - NULL cells count as all-zero values (Supp. B.1);
  *   - values live on the lattice nodes ("each occupied voxel corner", Sec. 3);
  *     node (i,j,k) sits at aabb_min + (i,j,k) * h, h = (aabb_max-aabb_min)/(R-1).
  *
@@ -89,7 +89,7 @@ void orc_sh_basis(const double *dir, double *Y)
 }
 
 /* ------------------------------------------------------------------------- */
-/* Grid description and NULL-as-zero value lookup (Supp. A.1).               */
+/* Grid description and NULL-as-zero value lookup (Supp. B.1).               */
 /* ------------------------------------------------------------------------- */
 typedef struct {
     int64_t R;
@@ -247,7 +247,7 @@ typedef struct {
     double sigma;         /* max(0, sigma_pre)                               */
     double k[ORC_NV - 1]; /* interpolated SH coefficients, [ch*9 + l]        */
     double pre[3];        /* sum_l Y_l k_{ch,l}                              */
-    double c[3];          /* ReLU colour (Supp. A.1)                         */
+    double c[3];          /* ReLU colour (Supp. B.1)                         */
     double T;             /* transmittance before this sample                */
     double alpha;         /* 1 - exp(-sigma * delta)                         */
     double w;             /* T * alpha                                       */
@@ -350,8 +350,8 @@ void orc_render(int64_t R, const int32_t *idx, const double *rows, int64_t row_s
 }
 
 /*
- * Exported adjoint of orc_render (Sec. 3.4: the renderer is differentiable;
- * Supp. A.1 "gradient kernels").  grad_rgb [n,3] = dL/dC.  Accumulates
+ * Exported adjoint of orc_render (Sec. 3.5: the renderer is differentiable;
+ * Supp. B.1 "gradient kernels").  grad_rgb [n,3] = dL/dC.  Accumulates
  * (+=) dL/d(row values) into grad_rows [M, 28] (FP64, dense 28 columns).
  *
  * Per sample s, with R_s = sum_{j>s} w_j c_j + T_end bg computed as an
@@ -515,7 +515,7 @@ void orc_max_weight(int64_t R, const int32_t *idx, const double *rows, int64_t r
 }
 
 /* ------------------------------------------------------------------------- */
-/* MSE reconstruction loss over the ray batch (Eq. 2, Sec. 3.4):             */
+/* MSE reconstruction loss over the ray batch (Eq. 3, Sec. 3.5):             */
 /*   L = 1/|R| sum_r ||C_r - Chat_r||_2^2,  dL/dChat = 2 (Chat - C) / |R|.   */
 /* ------------------------------------------------------------------------- */
 double orc_mse(const double *pred, const double *target, int64_t n, double *grad)
@@ -531,7 +531,7 @@ double orc_mse(const double *pred, const double *target, int64_t n, double *grad
 }
 
 /* ------------------------------------------------------------------------- */
-/* Total variation (Sec. 3.4 loss; Supp. A.1 normalisation and edge rules).  */
+/* Total variation (Sec. 3.5 loss; Supp. B.1 normalisation and edge rules).  */
 /* For each selected node v and value d:                                     */
 /*   D_a(v,d) = (V_d(v + e_a) - V_d(v)) * R / 256                            */
 /*   t(v,d)   = sqrt(D_x^2 + D_y^2 + D_z^2)                                  */
@@ -597,7 +597,7 @@ double orc_tv(int64_t R, const int32_t *idx, const double *rows, int64_t row_str
 }
 
 /* ------------------------------------------------------------------------- */
-/* RMSProp (Sec. 3.4), applied to every entry with a non-zero gradient:      */
+/* RMSProp (Sec. 3.5), applied to every entry with a non-zero gradient:      */
 /*   v <- beta v + (1 - beta) g^2 ;  x <- x - lr g / (sqrt(v) + eps) ; g <- 0 */
 /* lr = lr_sigma for column 0 (density) and lr_sh for the SH columns.        */
 /* x, v, grad are [M, 28] FP64.                                              */

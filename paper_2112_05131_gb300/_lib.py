@@ -68,6 +68,8 @@ SIGNATURES = {
                                    ctypes.POINTER(plx_render_opts), c_void_p]),
     "plx_count_nodes": (c_int32, [c_void_p, c_void_p, c_void_p, c_int64, ctypes.POINTER(plx_render_opts), c_void_p,
                                   c_void_p]),
+    "plx_max_weight": (c_int32, [c_void_p, c_void_p, c_void_p, c_int64, ctypes.POINTER(plx_render_opts), c_void_p,
+                                 c_void_p]),
     "plx_mse_grad": (c_int32, [c_void_p, c_void_p, c_int64, c_void_p, c_void_p, c_void_p]),
     "plx_tv_grad": (c_int32, [c_void_p, c_void_p, c_void_p, c_int64, c_int64, c_float, c_float, c_void_p, c_void_p,
                               c_void_p]),
@@ -75,6 +77,8 @@ SIGNATURES = {
                                    c_void_p]),
     "plx_prune_workspace_bytes": (c_size_t, [c_int32]),
     "plx_grid_prune_count": (c_int32, [c_void_p, c_float, c_int32, c_void_p, ctypes.POINTER(c_int64), c_void_p]),
+    "plx_grid_prune_count_key": (c_int32, [c_void_p, c_void_p, c_float, c_int32, c_void_p, ctypes.POINTER(c_int64),
+                                           c_void_p]),
     "plx_grid_prune_apply": (c_int32, [c_void_p, c_void_p, c_int64, c_void_p, c_void_p, c_void_p]),
     "plx_grid_prune_noalloc": (c_int32, [c_void_p, c_float, c_int32, c_void_p, c_void_p, ctypes.POINTER(c_int64),
                                          c_void_p]),

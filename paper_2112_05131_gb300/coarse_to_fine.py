@@ -1,11 +1,15 @@
-"""The coarse-to-fine optimisation loop (Sec. 3.4 "Coarse to Fine", Supp. A.1) on libplenoxel.
+"""The coarse-to-fine optimisation loop (Sec. 3.4 "Coarse to Fine", Supp. B.1) on libplenoxel.
 
-Training starts from a dense low-resolution grid; at fixed steps the grid is pruned (nodes whose
-density, and whose 3x3x3 neighbourhood's density, fall below a threshold are dropped) and then
+Training starts from a dense low-resolution grid; at fixed steps the grid is pruned and then
 upsampled to twice the resolution by trilinear interpolation, and optimisation continues on the
-new grid with fresh RMSProp state.  Every step is Trainer.step (ray generation, training march,
-MSE gradient, adjoint, TV on a random 1% of the nodes in contiguous segments, sparse RMSProp);
-prune and upsample are plx_grid_prune_* / plx_grid_upsample_*.
+new grid with fresh RMSProp state.  Pruning drops a node when neither it nor any node of its 3x3x3
+neighbourhood is hot; hot means a density of at least `prune_tau` (prune_by="density"), or a
+largest sample weight over every pixel ray of every training view of at least `weight_tau`
+(prune_by="weight", the form the paper uses on synthetic scenes with threshold 0.256).
+
+Every step is Trainer.step (ray generation, training march, MSE gradient, adjoint, TV on a random
+1% of the nodes in contiguous segments, sparse RMSProp); the weights are plx_max_weight, prune
+and upsample are plx_grid_prune_* / plx_grid_upsample_*.
 
 The training images are the ground-truth grid rendered by plx_render for every training view and
 held in host memory; each step's 5000 pixels are drawn on the host with a seeded generator, their
@@ -30,7 +34,9 @@ class C2FConfig:
     steps: int = 12800
     start_reso: int = 128
     upsample_at: Sequence[int] = (4266, 8533)
+    prune_by: str = "density"  # or "weight"
     prune_tau: float = 5.0
+    weight_tau: float = 0.256
     batch: int = 5000
     lambda_tv_sigma: float = 5e-4
     lambda_tv_sh: float = 1e-3
@@ -112,7 +118,14 @@ def train(train_images: np.ndarray, cams: torch.Tensor, W: int, H: int, cfg: C2F
             tr.finish()
             torch.cuda.synchronize()
             before = (grid.reso, grid.M)
-            pruned = grid.prune(cfg.prune_tau, True)
+            if cfg.prune_by == "weight":
+                key = grid.max_weight_views(cams, W, H, cfg.opts)
+                pruned = grid.prune(cfg.weight_tau, True, key=key)
+                del key
+            elif cfg.prune_by == "density":
+                pruned = grid.prune(cfg.prune_tau, True)
+            else:
+                raise ValueError(f"prune_by must be 'density' or 'weight', not {cfg.prune_by!r}")
             grid = pruned.upsample(2 * grid.reso)
             del pruned, tr
             torch.cuda.empty_cache()

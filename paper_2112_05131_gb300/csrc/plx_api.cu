@@ -445,6 +445,21 @@ plx_status plx_count_nodes(const plx_grid *grid, const float *d_origins, const f
                                                static_cast<cudaStream_t>(stream)), "plx_count_nodes");
 }
 
+plx_status plx_max_weight(const plx_grid *grid, const float *d_origins, const float *d_dirs, int64_t n,
+                          const plx_render_opts *opts, float *d_wmax, void *stream) {
+    plx_status st = check_grid(grid);
+    if (st == PLX_OK) st = check_opts(opts);
+    if (st != PLX_OK) return st;
+    if (n < 0 || n >= (int64_t(1) << 36)) return fail(PLX_EINVAL, "n out of range");
+    if (n > 0 && (!d_origins || !d_dirs)) return fail(PLX_EINVAL, "NULL ray buffer");
+    if (grid->desc.n_rows > 0 && !d_wmax) return fail(PLX_EINVAL, "d_wmax is NULL");
+    if (d_wmax && !aligned(d_wmax, 4)) return fail(PLX_EINVAL, "d_wmax must be 4-byte aligned");
+    if (grid->desc.sh_form == PLX_SH_F32 && grid->desc.n_rows > 0 && !grid->rows) return fail(PLX_EINVAL, "grid has no F32 rows");
+    plx::RenderParams p = make_params(grid, opts);
+    return cuda_status(plx::launch_max_weight(grid->view, d_origins, d_dirs, n, p, d_wmax,
+                                              static_cast<cudaStream_t>(stream)), "plx_max_weight");
+}
+
 plx_status plx_mse_grad(const float *d_rgb, const float *d_target, int64_t n, float *d_grad_rgb, float *d_loss,
                         void *stream) {
     if (n < 0 || n >= (int64_t(1) << 36)) return fail(PLX_EINVAL, "n out of range");
@@ -495,8 +510,8 @@ size_t plx_upsample_workspace_bytes(int32_t new_reso) {
     return plx::upsample_ws_bytes(new_reso);
 }
 
-plx_status plx_grid_prune_count(const plx_grid *grid, float tau, int32_t dilate, void *d_ws, int64_t *n_keep,
-                                void *stream) {
+static plx_status prune_count(const plx_grid *grid, const float *d_key, float tau, int32_t dilate, void *d_ws,
+                              int64_t *n_keep, void *stream, const char *who) {
     plx_status st = check_grid(grid);
     if (st != PLX_OK) return st;
     if (!n_keep) return fail(PLX_EINVAL, "n_keep is NULL");
@@ -504,14 +519,25 @@ plx_status plx_grid_prune_count(const plx_grid *grid, float tau, int32_t dilate,
     if (grid->desc.n_rows > 0 && !grid->rows) return fail(PLX_EINVAL, "pruning needs the grid's F32 rows");
     if (std::isnan(tau)) return fail(PLX_EINVAL, "tau is NaN");
     cudaStream_t s = static_cast<cudaStream_t>(stream);
-    cudaError_t e = plx::launch_prune_count(grid->view, tau, dilate ? 1 : 0, d_ws, s);
+    cudaError_t e = plx::launch_prune_count(grid->view, d_key, tau, dilate ? 1 : 0, d_ws, s);
     int64_t count = 0;
     if (e == cudaSuccess) e = cudaMemcpyAsync(&count, static_cast<char *>(d_ws) + plx::kWsCountOff, sizeof(int64_t),
                                               cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-    if (e != cudaSuccess) return cuda_status(e, "plx_grid_prune_count");
+    if (e != cudaSuccess) return cuda_status(e, who);
     *n_keep = count;
     return PLX_OK;
+}
+
+plx_status plx_grid_prune_count(const plx_grid *grid, float tau, int32_t dilate, void *d_ws, int64_t *n_keep,
+                                void *stream) {
+    return prune_count(grid, nullptr, tau, dilate, d_ws, n_keep, stream, "plx_grid_prune_count");
+}
+
+plx_status plx_grid_prune_count_key(const plx_grid *grid, const float *d_key, float tau, int32_t dilate, void *d_ws,
+                                    int64_t *n_keep, void *stream) {
+    if (grid && grid->desc.n_rows > 0 && !d_key) return fail(PLX_EINVAL, "d_key is NULL");
+    return prune_count(grid, d_key, tau, dilate, d_ws, n_keep, stream, "plx_grid_prune_count_key");
 }
 
 plx_status plx_grid_prune_apply(const plx_grid *grid, const void *d_ws, int64_t n_keep, int32_t *d_idx_new,

@@ -95,7 +95,9 @@ __global__ void __launch_bounds__(1024) scan_kernel(const uint32_t *__restrict__
 }
 
 // --------------------------------------------------------------------------- prune
-__global__ void prune_hot_kernel(GridView g, float tau, uint32_t *__restrict__ hot, int64_t n_words) {
+// hot(n): node n occupied and its key >= tau; the key is the row's density, or key[row] when given.
+__global__ void prune_hot_kernel(GridView g, const float *__restrict__ key, float tau, uint32_t *__restrict__ hot,
+                                 int64_t n_words) {
     const int lane = threadIdx.x & 31;
     const int64_t N = (int64_t)g.R * g.R * g.R;
     for (int64_t w = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); w < n_words;
@@ -104,7 +106,7 @@ __global__ void prune_hot_kernel(GridView g, float tau, uint32_t *__restrict__ h
         bool h = false;
         if (n < N) {
             const int32_t r = row_of(g, n);
-            h = r >= 0 && __ldg(g.rows + (int64_t)r * kRowF) >= tau;
+            h = r >= 0 && (key ? __ldg(key + r) : __ldg(g.rows + (int64_t)r * kRowF)) >= tau;
         }
         const unsigned word = __ballot_sync(kFull, h);
         if (lane == 0) hot[w] = word;
@@ -170,7 +172,7 @@ __global__ void __launch_bounds__(1024) prune_apply_kernel(GridView g, const uin
     dst[7] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
 }
 
-cudaError_t launch_prune_count(const GridView &g, float tau, int dilate, void *ws, cudaStream_t s) {
+cudaError_t launch_prune_count(const GridView &g, const float *key, float tau, int dilate, void *ws, cudaStream_t s) {
     const int64_t N = (int64_t)g.R * g.R * g.R;
     MapLayout L = MapLayout::make(N, true);
     char *base = static_cast<char *>(ws);
@@ -180,7 +182,7 @@ cudaError_t launch_prune_count(const GridView &g, float tau, int dilate, void *w
     uint32_t *offsets = reinterpret_cast<uint32_t *>(base + L.offsets_off);
     int64_t blocks = (L.n_words + 7) / 8;
     if (blocks > 152 * 64) blocks = 152 * 64;
-    prune_hot_kernel<<<(unsigned)blocks, 256, 0, s>>>(g, tau, hot, L.n_words);
+    prune_hot_kernel<<<(unsigned)blocks, 256, 0, s>>>(g, key, tau, hot, L.n_words);
     prune_keep_kernel<<<(unsigned)L.n_blocks, 1024, 0, s>>>(g, dilate, hot, keep, counts);
     scan_kernel<<<1, 1024, 0, s>>>(counts, offsets, L.n_blocks, reinterpret_cast<int64_t *>(base + kWsCountOff));
     return cudaGetLastError();

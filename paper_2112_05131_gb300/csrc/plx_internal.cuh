@@ -1,7 +1,7 @@
 // plx_internal.cuh -- device-side view of a Plenoxel grid and the helpers the
 // kernels share (SH basis, box clip, warp scans, status reporting).
 //
-// Layout facts used throughout (Sec. 3.2; Supp. A.1):
+// Layout facts used throughout (Sec. 3.2; Supp. B.1):
 //   node (i,j,k) -> n = (i*R + j)*R + k; idx[n] = -1 for a NULL node;
 //   F32 row  = 32 floats   [sigma, 27 SH (R0..R8, G0..G8, B0..B8), 4 pad];
 //   BF16 row = 32 uint16   [sigma FP32 (2 slots), 27 SH bf16, 3 pad].
@@ -396,6 +396,8 @@ cudaError_t launch_render_tiles(const GridView *g, const RenderParams *p, int n_
                                 int n_cams, const plx_tile *tiles, int64_t n_tiles, cudaStream_t s);
 cudaError_t launch_count_nodes(const GridView &g, const float *o, const float *d, int64_t n, const RenderParams &p,
                                int64_t *out, cudaStream_t s);
+cudaError_t launch_max_weight(const GridView &g, const float *o, const float *d, int64_t n, const RenderParams &p,
+                              float *wmax, cudaStream_t s);
 cudaError_t launch_mse_grad(const float *rgb, const float *target, int64_t n, float *grad, float *loss,
                             cudaStream_t s);
 cudaError_t launch_build_occupancy(const GridView &g, uint32_t *occ, cudaStream_t s);
@@ -409,7 +411,8 @@ cudaError_t launch_rmsprop(const GridView &g, float *rows, uint16_t *rows_h, flo
 // prune / upsample (plx_gridops.cu)
 size_t prune_ws_bytes(int64_t R);
 size_t upsample_ws_bytes(int64_t R2);
-cudaError_t launch_prune_count(const GridView &g, float tau, int dilate, void *ws, cudaStream_t s);
+// key: a per-row value compared with tau (the weight-threshold form), or nullptr for the density
+cudaError_t launch_prune_count(const GridView &g, const float *key, float tau, int dilate, void *ws, cudaStream_t s);
 cudaError_t launch_prune_apply(const GridView &g, const void *ws, int64_t n_keep, int32_t *idx_new,
                                float *rows_new, cudaStream_t s);
 cudaError_t launch_upsample_count(const GridView &g, int R2, void *ws, cudaStream_t s);

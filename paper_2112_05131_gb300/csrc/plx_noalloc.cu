@@ -74,7 +74,7 @@ extern "C" plx_status plx_grid_prune_noalloc(const plx_grid *grid, float tau, in
     cudaError_t e = scratch_for_current_device(&ws);
     if (e != cudaSuccess) return plx::set_error(PLX_ECUDA, cudaGetErrorString(e));
     cudaStream_t s = static_cast<cudaStream_t>(stream);
-    e = plx::launch_prune_count(*v, tau, dilate ? 1 : 0, ws, s);
+    e = plx::launch_prune_count(*v, nullptr, tau, dilate ? 1 : 0, ws, s);
     int64_t count = 0;
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(&count, static_cast<char *>(ws) + plx::kWsCountOff, sizeof(int64_t), cudaMemcpyDeviceToHost, s);

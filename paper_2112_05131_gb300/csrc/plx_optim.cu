@@ -1,6 +1,6 @@
 // plx_optim.cu -- the kernels around the renderer: the cell-occupancy mask
 // used for empty-space skipping, BF16-SH packing, the total-variation gradient
-// (Sec. 3.4, Supp. A.1) and the RMSProp update (Sec. 3.4).
+// (Sec. 3.5, Supp. B.1) and the RMSProp update (Sec. 3.5).
 #include <algorithm>
 
 #include "plx_internal.cuh"
@@ -123,7 +123,7 @@ __device__ __forceinline__ float4 ld4(const float *p) { return __ldg(reinterpret
 
 __device__ __forceinline__ float comp(const float4 &v, int c) { return c == 0 ? v.x : c == 1 ? v.y : c == 2 ? v.z : v.w; }
 
-// TV (Sec. 3.4; Supp. A.1) of one float4 quarter q (< 7) of one node: per value d of the quarter,
+// TV (Sec. 3.5; Supp. B.1) of one float4 quarter q (< 7) of one node: per value d of the quarter,
 // D_a = (V_d(n + e_a) - V_d(n)) R/256, t = sqrt(sum_a D_a^2), loss += lam_d t, and the gradient
 // lam_d (R/256) D_a / t to the +a neighbour and minus its sum to the node (0 when t = 0).  A missing
 // neighbour (NULL or outside) has density 0 and SH equal to the node's own (no gradient for it).
@@ -266,7 +266,7 @@ cudaError_t launch_tv(const GridView &g, const int64_t *seg_start, const int64_t
 // which the scattered rows need to reach DRAM efficiently.  Entries with a zero
 // gradient keep x and v; a row with any update is re-packed into its BF16-SH
 // form when the grid has one.
-// RMSProp (Sec. 3.4) on one float4 quarter q (< 7) of a row: for every entry with g != 0,
+// RMSProp (Sec. 3.5) on one float4 quarter q (< 7) of a row: for every entry with g != 0,
 // v <- beta v + (1 - beta) g^2, x <- x - lr g / (sqrt(v) + eps), then g <- 0; the BF16-SH
 // shadow of the quarter is refreshed.  g4, x4, v4 were loaded by the caller.
 __device__ __forceinline__ void rms_update(int64_t r, int q, float4 g4, float4 x4, float4 v4, float *__restrict__ rows,

@@ -7,7 +7,7 @@
 // 112-byte row reads as float4 vectors), the warp turns per-sample alphas into
 // transmittances with a prefix product, and early termination ends the loop at
 // chunk granularity.  Compared with one warp per ray and one lane per SH
-// coefficient (the design Supp. A.1 describes for a Titan RTX), this cuts the
+// coefficient (the design Supp. B.1 describes for a Titan RTX), this cuts the
 // serial chain of dependent loads per ray by 32x, which is what bounds a
 // 5000-ray batch on a 152-SM part.  Cells with no occupied corner (a bit in
 // the grid's occupancy mask) cost one mask read, issued kCand at a time.
@@ -451,6 +451,73 @@ cudaError_t launch_count_nodes(const GridView &g, const float *o, const float *d
                                int64_t *out, cudaStream_t s) {
     if (n == 0) return cudaSuccess;
     count_nodes_kernel<<<(unsigned)((n + kFwdWarps - 1) / kFwdWarps), kFwdWarps * 32, 0, s>>>(g, o, d, n, p, out);
+    return cudaGetLastError();
+}
+
+// --------------------------------------------------------------------------- weight-threshold prune key
+// plx_max_weight: over the given rays, the largest weight T_s alpha_s of the samples
+// crediting each row (Sec. 3.4, weight-threshold pruning).  A sample credits the 8
+// corner nodes of its cell, the nodes its values come from, whatever their
+// trilinear weights; NULL corners have no row.  The march, its samples and its
+// weights are those of plx_render (samples in all-empty cells have weight 0 and
+// credit no row, so compaction changes nothing).  Weights are positive floats,
+// whose order is their bit patterns' order as unsigned integers: the maximum is
+// an unsigned atomicMax, issued only when the weight beats the value in L2.
+__global__ void __launch_bounds__(kFwdWarps * 32) max_weight_kernel(GridView g, const float *__restrict__ ro,
+                                                                    const float *__restrict__ rd, int64_t n,
+                                                                    RenderParams p, float *__restrict__ wmax) {
+    __shared__ int s_ring[kFwdWarps][kRing];
+    const int lane = threadIdx.x & 31;
+    const int wid = threadIdx.x >> 5;
+    const int64_t ray = (int64_t)blockIdx.x * kFwdWarps + wid;
+    if (ray >= n) return;  // uniform per warp
+    const RaySetup rs = ray_setup(g, p, ro, rd, ray);
+    if (!rs.hit) return;   // uniform per warp
+    int *ring = s_ring[wid];
+    Stream st = {rs.s_lo, rs.s_lo, rs.s_lo, false};
+    float Tc = 1.0f;
+    for (;;) {
+        refill(g, rs, p, ring, st, lane);
+        int s;
+        const int cnt = take_chunk(ring, st, lane, s);
+        if (cnt == 0) break;
+        const bool valid = lane < cnt;
+        float sig = 0.0f;
+        int32_t r[8];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) r[k] = -1;
+        if (valid) {
+            DF gc[3];
+            sample_coords(g, rs, sample_t(rs, p, s), gc);
+            const Cell c = locate(g, gc);
+#pragma unroll
+            for (int k = 0; k < 8; ++k) r[k] = row_of(g, corner_node(g, c.base, k));
+            float acc = 0.0f;
+#pragma unroll
+            for (int k = 0; k < 8; ++k)
+                if (r[k] >= 0) acc = fmaf(corner_weight(c.f, k), row_sigma(g, g.form, r[k]), acc);
+            sig = fmaxf(acc, 0.0f);
+        }
+        const Composite cp = composite(sig, valid, Tc, p, lane);
+        const float w = cp.T * cp.alpha;
+        if (cp.take && w > 0.0f) {
+            const unsigned wb = __float_as_uint(w);
+#pragma unroll
+            for (int k = 0; k < 8; ++k) {
+                if (r[k] < 0) continue;
+                unsigned *a = reinterpret_cast<unsigned *>(wmax + r[k]);
+                if (wb > __ldcg(a)) atomicMax(a, wb);
+            }
+        }
+        Tc *= cp.chunk_prod;
+        if (cp.tmask != __ballot_sync(kFull, valid)) break;  // T fell below stop_thresh
+    }
+}
+
+cudaError_t launch_max_weight(const GridView &g, const float *o, const float *d, int64_t n, const RenderParams &p,
+                              float *wmax, cudaStream_t s) {
+    if (n == 0) return cudaSuccess;
+    max_weight_kernel<<<(unsigned)((n + kFwdWarps - 1) / kFwdWarps), kFwdWarps * 32, 0, s>>>(g, o, d, n, p, wmax);
     return cudaGetLastError();
 }
 

@@ -1,5 +1,5 @@
 // plx_train.cu -- the chunk-parallel march of the optimisation step (Eq. 1 and
-// its adjoint for a batch of training rays, Sec. 3.4 / Supp. A.1).
+// its adjoint for a batch of training rays, Sec. 3.5 / Supp. B.1).
 //
 // Why a second march: a 5000-ray batch is about two waves of one-warp-per-ray
 // work on a 152-SM part, and a ray through the dense shell and blobs carries
@@ -401,7 +401,7 @@ __device__ __forceinline__ void combine_ray(const RenderParams &p, const MarchPt
     }
 }
 
-// With `target`, the kernel also forms the MSE gradient 2 (C - target) / n (Sec. 3.4) and adds
+// With `target`, the kernel also forms the MSE gradient 2 (C - target) / n (Sec. 3.5) and adds
 // L = sum |C - target|^2 / n to *loss (one atomic per CTA).
 __global__ void __launch_bounds__(kCombineWarps * 32) march_combine_kernel(GridView g, int64_t n, RenderParams p,
                                                                            MarchPtrs st, MarchHeader expect,

@@ -262,6 +262,39 @@ class Grid:
                _stream(stream))
         return out
 
+    def max_weight(self, origins, dirs, opts: RenderOpts = RenderOpts(), wmax: Optional[torch.Tensor] = None,
+                   stream=None) -> torch.Tensor:
+        """plx_max_weight: per row, the largest weight of the samples crediting it over these rays, float32
+        [M] (max-updated in place when given; start from zeros)."""
+        n = origins.shape[0]
+        if wmax is None:
+            wmax = torch.zeros(self.M, dtype=torch.float32, device=self.idx.device)
+        _need(wmax, torch.float32, "wmax", (self.M,))
+        L.call("plx_max_weight", self.handle, _p(origins), _p(dirs), n, ctypes.byref(opts.c()), _p(wmax),
+               _stream(stream))
+        return wmax
+
+    def max_weight_views(self, cams: torch.Tensor, W: int, H: int, opts: RenderOpts = RenderOpts(),
+                         views: Optional[Sequence[int]] = None, wmax: Optional[torch.Tensor] = None,
+                         stream=None) -> torch.Tensor:
+        """plx_max_weight over every pixel ray of the given views (all views of `cams` by default), one
+        view per launch; the rays of a view are generated by plx_gen_rays into a reused buffer."""
+        dev = self.idx.device
+        s = stream if stream is not None else torch.cuda.current_stream(dev)
+        with torch.cuda.stream(s):
+            if wmax is None:
+                wmax = torch.zeros(self.M, dtype=torch.float32, device=dev)
+            n = W * H
+            o = torch.empty((n, 3), dtype=torch.float32, device=dev)
+            d = torch.empty((n, 3), dtype=torch.float32, device=dev)
+            base = torch.arange(n, dtype=torch.int64, device=dev)
+            pix = torch.empty_like(base)
+            for v in (range(cams.shape[0]) if views is None else views):
+                torch.add(base, int(v) * n, out=pix)
+                gen_rays(cams, pix, W, H, o, d, stream=s)
+                self.max_weight(o, d, opts, wmax, stream=s)
+        return wmax
+
     def tv_grad(self, seg_start: torch.Tensor, seg_len: torch.Tensor, n_selected: int, lambda_sigma: float,
                 lambda_sh: float, grad_rows: torch.Tensor, loss: Optional[torch.Tensor] = None, stream=None):
         _need(seg_start, torch.int64, "seg_start")
@@ -277,12 +310,19 @@ class Grid:
         L.call("plx_rmsprop_step", self.handle, _p(grad_rows), _p(v), float(lr_sigma), float(lr_sh), float(beta),
                float(eps), 1 if sparse else 0, _stream(stream))
 
-    def prune(self, tau: float, dilate: bool = True, stream=None) -> "Grid":
+    def prune(self, tau: float, dilate: bool = True, key: Optional[torch.Tensor] = None, stream=None) -> "Grid":
+        """Density-threshold prune (key None), or weight-threshold prune on a per-row key (float32 [M], e.g.
+        max_weight_views), with 3x3x3 dilation."""
         lib = L.load()
         ws = torch.empty(lib.plx_prune_workspace_bytes(self.reso), dtype=torch.uint8, device=self.idx.device)
         n_keep = ctypes.c_int64()
-        L.call("plx_grid_prune_count", self.handle, float(tau), 1 if dilate else 0, _p(ws), ctypes.byref(n_keep),
-               _stream(stream))
+        if key is None:
+            L.call("plx_grid_prune_count", self.handle, float(tau), 1 if dilate else 0, _p(ws), ctypes.byref(n_keep),
+                   _stream(stream))
+        else:
+            _need(key, torch.float32, "key", (self.M,))
+            L.call("plx_grid_prune_count_key", self.handle, _p(key), float(tau), 1 if dilate else 0, _p(ws),
+                   ctypes.byref(n_keep), _stream(stream))
         idx_new = torch.empty(self.reso ** 3, dtype=torch.int32, device=self.idx.device)
         rows_new = torch.empty((n_keep.value, ROW), dtype=torch.float32, device=self.idx.device)
         L.call("plx_grid_prune_apply", self.handle, _p(ws), n_keep.value, _p(idx_new),

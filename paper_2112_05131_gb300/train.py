@@ -1,6 +1,6 @@
-"""The optimisation step of Sec. 3.4 as a sequence of library calls, and the learning-rate schedules.
+"""The optimisation step of Sec. 3.5 as a sequence of library calls, and the learning-rate schedules.
 
-One step (Supp. A.1: 5000-ray batches, RMSProp, stochastic TV on contiguous segments):
+One step (Supp. B.1: 5000-ray batches, RMSProp, stochastic TV on contiguous segments):
   plx_gen_rays -> plx_march_plan -> plx_render_planned_mse (forward and MSE gradient)
   -> plx_render_backward_train -> plx_tv_grad -> plx_rmsprop_step
 all libplenoxel calls with no host synchronisation.  The training march splits rays into chunk work
@@ -28,7 +28,7 @@ LAUNCHES_PER_STEP = 10
 
 def lr_sigma(step: int, init: float = 30.0, final: float = 0.05, max_steps: int = 250000, delay_steps: int = 15000,
              delay_mult: float = 0.01) -> float:
-    """Delayed exponential decay for density (Supp. A.1, the Mip-NeRF schedule): log-linear from
+    """Delayed exponential decay for density (Supp. B.1, the Mip-NeRF schedule): log-linear from
     `init` to `final` over `max_steps`, scaled during the first `delay_steps` by
     delay_mult + (1 - delay_mult) sin(pi/2 clip(step/delay_steps, 0, 1)).  The paper does not print the
     delay multiplier; 0.01 is this implementation's choice."""
@@ -41,7 +41,7 @@ def lr_sigma(step: int, init: float = 30.0, final: float = 0.05, max_steps: int 
 
 
 def lr_sh(step: int, init: float = 1e-2, final: float = 5e-6, max_steps: int = 250000) -> float:
-    """Pure exponential decay for the SH coefficients (Supp. A.1)."""
+    """Pure exponential decay for the SH coefficients (Supp. B.1)."""
     t = min(max(step / max_steps, 0.0), 1.0)
     return math.exp((1.0 - t) * math.log(init) + t * math.log(final))
 

@@ -6,7 +6,7 @@ camera poses, pixel ids and voxel segments; rendering, interpolation, SH,
 compositing, TV, RMSProp, pruning and upsampling live on each side separately.
 
 The paper's workloads (NeRF-synthetic: 100 views of 800x800 on the upper
-hemisphere, white background, Sec. 4.1; 256^3 -> 512^3 grids, Supp. A.2) are
+hemisphere, white background, Sec. 4.1; 256^3 -> 512^3 grids, Supp. B.2) are
 datasets that are not available; the generators below stand in for them with
 the same shapes.  Scene recipes:
 
@@ -215,7 +215,7 @@ def pixel_batch(n_views: int, W: int, H: int, n: int, seed: int) -> np.ndarray:
 
 def tv_segments(R: int, fraction: float, seg_len: int, seed: int):
     """Random contiguous runs of ``seg_len`` linear node ids covering ~``fraction`` of R^3
-    (Supp. A.1: TV on random contiguous segments in pointer-grid order).  Non-overlapping,
+    (Supp. B.1: TV on random contiguous segments in pointer-grid order).  Non-overlapping,
     sorted; returns (start int64 [S], length int64 [S])."""
     rng = np.random.default_rng(seed)
     N = R ** 3

@@ -1,4 +1,4 @@
-"""The coarse-to-fine loop (Sec. 3.4, Supp. A.1) at a small scale: a dense 16^3 start, prune + upsample
+"""The coarse-to-fine loop (Sec. 3.4, Supp. B.1) at a small scale: a dense 16^3 start, prune + upsample
 to 32^3 and 64^3, training images from the ground-truth grid (spot-checked against the oracle)."""
 import numpy as np
 import pytest
@@ -11,7 +11,8 @@ from parity import check_colours, delta_of
 pytestmark = pytest.mark.gpu
 
 
-def test_coarse_to_fine_small(cuda_lib):
+@pytest.mark.parametrize("prune_by", ["density", "weight"])
+def test_coarse_to_fine_small(cuda_lib, prune_by):
     from paper_2112_05131_gb300.coarse_to_fine import C2FConfig, dense_grid, psnr, render_views, train
     from paper_2112_05131_gb300.grid import Grid, RenderOpts
 
@@ -33,7 +34,7 @@ def test_coarse_to_fine_small(cuda_lib):
     check_colours(images.reshape(-1, 3)[pix], ref, aux, gt.rows, delta_of(64, 0.5), opts.bg)
 
     cfg = C2FConfig(steps=900, start_reso=16, upsample_at=(300, 600), batch=2048, tv_segment=256, chunk=100,
-                    lambda_tv_sigma=1e-5, lambda_tv_sh=1e-4)
+                    lambda_tv_sigma=1e-5, lambda_tv_sh=1e-4, prune_by=prune_by)
     log = []
     g = train(images, cams_t, W, H, cfg, log)
     assert g.reso == 64
@@ -41,5 +42,5 @@ def test_coarse_to_fine_small(cuda_lib):
     start = render_views(dense_grid(16, 0.1), test_t, W, H, opts)
     final = render_views(g, test_t, W, H, opts)
     p0, p1 = psnr(start, truth), psnr(final, truth)
-    print(f"coarse-to-fine 16->32->64: held-out PSNR {p0:.2f} dB -> {p1:.2f} dB; stages {log}")
+    print(f"coarse-to-fine 16->32->64 ({prune_by} prune): held-out PSNR {p0:.2f} dB -> {p1:.2f} dB; stages {log}")
     assert p1 > p0 + 3.0

@@ -391,7 +391,7 @@ def _loss_render(R, idx, rows, o, d, gw, stop, bg):
     (5, 0.2, 0.0, -4.0, 0.0)])  # last: density and colour ReLUs both active and inactive
 def test_render_backward_matches_central_differences(R, frac_empty, stop, sig_lo, dc):
     idx, rows = random_sparse(R, frac_empty, 50 + R, sigma_range=(sig_lo, 6.0), sh_std=0.1 if dc else 0.6)
-    rows[:, 1] += dc / Y00  # dc = 1: colours sit well above the ReLU kink (Supp. A.1)
+    rows[:, 1] += dc / Y00  # dc = 1: colours sit well above the ReLU kink (Supp. B.1)
     rows[:, 10] += dc / Y00
     rows[:, 19] += dc / Y00
     o, d = synth.random_rays(16, seed=60 + R, spread=0.7)
@@ -513,7 +513,7 @@ def test_tv_linear_ramp_closed_form():
 
 def test_tv_constant_field_edges():
     """Constant field c: only boundary nodes contribute, and only for density
-    (missing density neighbour = 0; missing SH neighbour = own value, Supp. A.1)."""
+    (missing density neighbour = 0; missing SH neighbour = own value, Supp. B.1)."""
     R = 5
     c = 2.5
     idx, rows = dense(R, np.full((R ** 3, NV), c))
