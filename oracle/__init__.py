@@ -64,6 +64,7 @@ def _load():
             "orc_tv": (D, [I64, P, P, I64, P, P, I64, D, D, P]),
             "orc_rmsprop": (None, [I64, P, P, P, D, D, D, D]),
             "orc_max_weight": (None, [I64, P, P, I64, P, P, P, I64, P, P]),
+            "orc_sparsity": (D, [I64, P, P, I64, P, P, P, I64, P, D, P]),
             "orc_prune": (I64, [I64, P, P, I64, D, ctypes.c_int, P, P]),
             "orc_prune_key": (I64, [I64, P, P, I64, P, D, ctypes.c_int, P, P]),
             "orc_upsample": (I64, [I64, P, P, I64, I64, P, P]),
@@ -278,6 +279,22 @@ def max_weight(R, idx, rows, o, d, step_vox=0.5, stop_thresh=0.0, aabb=None, wma
     lib.orc_max_weight(R, _p(idx), _p(rows), rows.shape[1], _p(_aabb(aabb)), _p(o), _p(d), o.shape[0],
                        _p(_opts(step_vox, 0.0, stop_thresh)), _p(wmax))
     return wmax
+
+
+def sparsity(R, idx, rows, o, d, lambda_s, step_vox=0.5, stop_thresh=0.0, aabb=None, grad_rows=None):
+    """Cauchy sparsity prior lambda_s sum log(1 + 2 sigma^2) over every marched sample (Sec. 3.7, Eq. 4).
+    Returns (L, grad_rows [M,28] FP64, density column accumulated)."""
+    lib = _load()
+    idx = _c(idx, np.int32)
+    rows = _rows(rows)
+    o = _c(o, np.float64)
+    d = _c(d, np.float64)
+    if grad_rows is None:
+        grad_rows = np.zeros((rows.shape[0], NV), np.float64)
+    assert grad_rows.dtype == np.float64 and grad_rows.flags.c_contiguous and grad_rows.shape == (rows.shape[0], NV)
+    L = lib.orc_sparsity(R, _p(idx), _p(rows), rows.shape[1], _p(_aabb(aabb)), _p(o), _p(d), o.shape[0],
+                         _p(_opts(step_vox, 0.0, stop_thresh)), float(lambda_s), _p(grad_rows))
+    return float(L), grad_rows
 
 
 def prune_key(R, idx, rows, key, tau, dilate=True):

@@ -417,6 +417,60 @@ def test_render_backward_matches_central_differences(R, frac_empty, stop, sig_lo
     assert np.all(err <= 1e-6 * np.maximum(np.abs(an), 1e-3 * scale) + floor)
 
 
+# ----------------------------------------------------------------------------- Cauchy sparsity prior
+
+@pytest.mark.parametrize("stop", [0.0, 0.05])
+def test_sparsity_constant_field_closed_form(stop):
+    """sigma = sigma0 on every node: each of a ray's N samples (the render's closed-form count) adds
+    log(1 + 2 sigma0^2), and its gradient lambda 4 sigma0 / (1 + 2 sigma0^2) splits over corners whose
+    trilinear weights sum to one, so the density column of the gradient sums to lambda N times that."""
+    R, sigma0, lam, step_vox = 12, 2.3, 1e-3, 0.37
+    idx, rows = constant_field(R, sigma0, (0.5, 0.5, 0.5))
+    delta = step_vox * 2.0 / (R - 1)
+    o = np.array([[-3.0, 0.2, -0.4], [0.3, -3.0, 0.1], [2.2, 2.9, -1.7]])
+    d = np.array([[1.0, 0.0, 0.0], [0.1, 1.0, -0.05], [-0.5, -0.8, 0.45]])
+    d /= np.linalg.norm(d, axis=1, keepdims=True)
+    N = 0
+    for r in range(o.shape[0]):
+        t0, t1 = box_segment(o[r], d[r])
+        n = math.ceil((t1 - t0) / delta)
+        if stop > 0:
+            n = min(n, math.ceil(math.log(1.0 / stop) / (sigma0 * delta)))
+        N += n
+    L, g = oracle.sparsity(R, idx, rows, o, d, lam, step_vox=step_vox, stop_thresh=stop)
+    assert L == pytest.approx(lam * N * math.log(1 + 2 * sigma0 ** 2), rel=1e-13)
+    assert g[:, 0].sum() == pytest.approx(lam * N * 4 * sigma0 / (1 + 2 * sigma0 ** 2), rel=1e-12)
+    assert np.all(g[:, 1:] == 0.0)
+
+
+def test_sparsity_matches_central_differences():
+    R = 5
+    idx, rows = random_sparse(R, 0.3, 81, sigma_range=(-3.0, 6.0))
+    o, d = synth.random_rays(12, seed=82, spread=0.7)
+    o, d = o.astype(float), d.astype(float)
+    lam = 0.7
+    L0, an = oracle.sparsity(R, idx, rows, o, d, lam)
+    h = 1e-5
+    fd = np.zeros(rows.shape[0])
+    for m in range(rows.shape[0]):
+        rp, rm = rows.copy(), rows.copy()
+        rp[m, 0] += h
+        rm[m, 0] -= h
+        fd[m] = (oracle.sparsity(R, idx, rp, o, d, lam)[0] - oracle.sparsity(R, idx, rm, o, d, lam)[0]) / (2 * h)
+    scale = np.max(np.abs(an[:, 0]))
+    assert scale > 0 and L0 > 0
+    floor = 8 * np.finfo(float).eps * abs(L0) / h
+    assert np.all(np.abs(fd - an[:, 0]) <= 1e-6 * np.maximum(np.abs(an[:, 0]), 1e-3 * scale) + floor)
+
+
+def test_sparsity_of_non_positive_density_is_zero():
+    R = 6
+    idx, rows = random_sparse(R, 0.2, 83, sigma_range=(-5.0, 0.0))
+    o, d = synth.random_rays(30, seed=84)
+    L, g = oracle.sparsity(R, idx, rows, o, d, 1.0)
+    assert L == 0.0 and np.all(g == 0.0)
+
+
 def test_backward_abs_bounds_the_adjoint():
     """|adjoint(g')| <= abs-adjoint(g) for every |g'| <= g (triangle inequality), with equality for a
     single ray and channel on the SH columns of its colour-channel (one sign per term there)."""
