@@ -626,8 +626,10 @@ def large_batch(args, wl, cams_t, gt_grid, opts, n=1 << 18, steps=8, warmup=3):
 
 def coarse_to_fine(args, wl, cams_t, gt_grid, opts):
     """Training images = the ground truth rendered for the 100 training views; a dense 128^3 start (sigma 0.1,
-    SH 0); prune (sigma < 5, dilated) and upsample at steps 4266 and 8533 of 12800; TV 5e-4 / 1e-3 on 1% of the
-    nodes; PSNR on the 25 held-out views against the ground truth's renders."""
+    SH 0); prune (sigma < 5, or maximum weight < 0.256 with --c2f-prune weight; dilated) and upsample at steps
+    4266 and 8533 of 12800; TV 5e-4 / 1e-3 on 1% of the nodes; PSNR on the 25 held-out views against the ground
+    truth's renders.  Every step also counts the rows that received a gradient (one small launch), reported
+    per stage every 500 steps as a fraction of the grid's rows."""
     import torch
 
     import synth
@@ -640,7 +642,7 @@ def coarse_to_fine(args, wl, cams_t, gt_grid, opts):
     truth = render_views(gt_grid, test_t, W, H, opts)
     prep = time.perf_counter() - t0
     cfg = C2FConfig(steps=args.c2f_steps, upsample_at=(args.c2f_steps // 3, 2 * args.c2f_steps // 3),
-                    prune_by=args.c2f_prune)
+                    prune_by=args.c2f_prune, track_touched=True, touched_every=500)
     log = []
     torch.cuda.synchronize()
     t0 = time.perf_counter()

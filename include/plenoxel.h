@@ -179,10 +179,17 @@ plx_status plx_render(const plx_grid *grid, const float *d_origins, const float 
  *   R = sum_{j>s} w_j c_j + T_end bg,
  * scattered to the 8 corners with their trilinear weights (NULL corners skip).
  * Rows are accumulated with float atomics, so the summation order (and the
- * last bits) can vary between runs. */
+ * last bits) can vary between runs.
+ * lambda_sparsity (>= 0, finite) adds the Cauchy sparsity prior of Sec. 3.7
+ * (Eq. 4), lambda_sparsity sum log(1 + 2 sigma_s^2) over every sample the
+ * rays take (sigma_s the activated density): its density gradient
+ * lambda_sparsity 4 sigma_s / (1 + 2 sigma_s^2) joins dL/dsigma_s above, and
+ * its value is added to *d_loss_sparsity (device float, may be NULL; one
+ * atomic per 32 samples).  0 leaves the prior out. */
 plx_status plx_render_backward(const plx_grid *grid, const float *d_origins, const float *d_dirs,
                                int64_t n, const plx_render_opts *opts, const float *d_grad_rgb,
-                               float *d_grad_rows, void *stream);
+                               float *d_grad_rows, float lambda_sparsity, float *d_loss_sparsity,
+                               void *stream);
 
 /* ---------------------------------------------------------------- training march
  *
@@ -237,10 +244,12 @@ plx_status plx_render_planned_mse(const plx_grid *grid, const float *d_origins, 
  * plx_render_train (or plx_render_planned) that used d_state, enqueued after
  * it, before the grid's rows change.  The kernel checks the state's header (ray buffers, grid rows,
  * sizes, options) on the device; on a mismatch it adds nothing and plx_check
- * then returns PLX_EDEVICE. */
+ * then returns PLX_EDEVICE.  lambda_sparsity and d_loss_sparsity: the Cauchy
+ * sparsity prior, as in plx_render_backward. */
 plx_status plx_render_backward_train(const plx_grid *grid, const float *d_origins, const float *d_dirs, int64_t n,
                                      const plx_render_opts *opts, const float *d_grad_rgb, const void *d_state,
-                                     size_t state_bytes, float *d_grad_rows, void *stream);
+                                     size_t state_bytes, float *d_grad_rows, float lambda_sparsity,
+                                     float *d_loss_sparsity, void *stream);
 
 /* ---------------------------------------------------------------- serving
  *
@@ -335,6 +344,14 @@ plx_status plx_tv_grad(const plx_grid *grid, const int64_t *d_seg_start, const i
  * Both modes clear the touched bitmask. */
 plx_status plx_rmsprop_step(plx_grid *grid, float *d_grad_rows, float *d_v, float lr_sigma,
                             float lr_sh, float beta, float eps, int32_t sparse, void *stream);
+
+/* Gradient sparsity (Sec. 3.8 and its figure: after the first minutes of
+ * optimisation few voxels receive a gradient): writes to *d_count (device
+ * int64) the number of rows marked in the grid's touched bitmask, i.e. the
+ * rows that the adjoints and TV have added to since the last
+ * plx_rmsprop_step -- call it before that step.  One small launch; reads
+ * n_rows / 8 bytes. */
+plx_status plx_count_touched(const plx_grid *grid, int64_t *d_count, void *stream);
 
 /* ---------------------------------------------------------------- prune / upsample */
 

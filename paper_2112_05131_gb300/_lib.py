@@ -52,7 +52,7 @@ SIGNATURES = {
     "plx_render": (c_int32, [c_void_p, c_void_p, c_void_p, c_int64, ctypes.POINTER(plx_render_opts), c_void_p,
                              c_void_p, c_void_p]),
     "plx_render_backward": (c_int32, [c_void_p, c_void_p, c_void_p, c_int64, ctypes.POINTER(plx_render_opts),
-                                      c_void_p, c_void_p, c_void_p]),
+                                      c_void_p, c_void_p, c_float, c_void_p, c_void_p]),
     "plx_march_state_bytes": (c_size_t, [c_void_p, c_int64, ctypes.POINTER(plx_render_opts)]),
     "plx_render_train": (c_int32, [c_void_p, c_void_p, c_void_p, c_int64, ctypes.POINTER(plx_render_opts), c_void_p,
                                    c_void_p, c_void_p, c_size_t, c_void_p]),
@@ -63,11 +63,12 @@ SIGNATURES = {
     "plx_render_planned_mse": (c_int32, [c_void_p, c_void_p, c_void_p, c_int64, ctypes.POINTER(plx_render_opts),
                                          c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_size_t, c_void_p]),
     "plx_render_backward_train": (c_int32, [c_void_p, c_void_p, c_void_p, c_int64, ctypes.POINTER(plx_render_opts),
-                                            c_void_p, c_void_p, c_size_t, c_void_p, c_void_p]),
+                                            c_void_p, c_void_p, c_size_t, c_void_p, c_float, c_void_p, c_void_p]),
     "plx_render_tiles": (c_int32, [ctypes.POINTER(c_void_p), c_int32, c_void_p, c_int32, c_void_p, c_int64,
                                    ctypes.POINTER(plx_render_opts), c_void_p]),
     "plx_count_nodes": (c_int32, [c_void_p, c_void_p, c_void_p, c_int64, ctypes.POINTER(plx_render_opts), c_void_p,
                                   c_void_p]),
+    "plx_count_touched": (c_int32, [c_void_p, c_void_p, c_void_p]),
     "plx_max_weight": (c_int32, [c_void_p, c_void_p, c_void_p, c_int64, ctypes.POINTER(plx_render_opts), c_void_p,
                                  c_void_p]),
     "plx_mse_grad": (c_int32, [c_void_p, c_void_p, c_int64, c_void_p, c_void_p, c_void_p]),

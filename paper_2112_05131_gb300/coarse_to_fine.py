@@ -46,6 +46,10 @@ class C2FConfig:
     opts: RenderOpts = field(default_factory=lambda: RenderOpts(0.5, (1.0, 1.0, 1.0), 0.0))
     chunk: int = 256  # steps whose pixel batches are prepared and uploaded together
     seed: int = 0
+    # record the fraction of rows that receive a gradient at every step (Sec. 3.8: the gradient becomes
+    # sparse within the first minutes); each stage's log entry then holds it every `touched_every` steps
+    track_touched: bool = False
+    touched_every: int = 100
 
 
 def dense_grid(R: int, sigma: float, device="cuda") -> Grid:
@@ -107,16 +111,18 @@ def train(train_images: np.ndarray, cams: torch.Tensor, W: int, H: int, cfg: C2F
     dev = cams.device
     grid = dense_grid(cfg.start_reso, cfg.init_sigma, dev)
     sc = StepConfig(batch=cfg.batch, opts=cfg.opts, lambda_tv_sigma=cfg.lambda_tv_sigma,
-                    lambda_tv_sh=cfg.lambda_tv_sh)
+                    lambda_tv_sh=cfg.lambda_tv_sh, track_touched=cfg.track_touched)
     tr = Trainer(grid, cams, W, H, sc)
     batches = _Batches(train_images, cfg, dev)
     ups = sorted(int(s) for s in cfg.upsample_at)
     t_stage = time.perf_counter()
+    stage_start = 0
     for step in range(cfg.steps):
         if ups and step == ups[0]:
             ups.pop(0)
             tr.finish()
             torch.cuda.synchronize()
+            touched = _touched_curve(tr, grid.M, stage_start, cfg)
             before = (grid.reso, grid.M)
             if cfg.prune_by == "weight":
                 key = grid.max_weight_views(cams, W, H, cfg.opts)
@@ -133,13 +139,26 @@ def train(train_images: np.ndarray, cams: torch.Tensor, W: int, H: int, cfg: C2F
             torch.cuda.synchronize()
             if log is not None:
                 log.append({"step": step, "from": before, "to": (grid.reso, grid.M),
-                            "stage_s": time.perf_counter() - t_stage})
+                            "stage_s": time.perf_counter() - t_stage, **touched})
             t_stage = time.perf_counter()
+            stage_start = step
         pix, tgt, ss, sl, nsel = batches.get(step, grid.reso)
         tr.step(pix, tgt, ss, sl, nsel, lr_sigma(step), lr_sh(step))
     tr.finish()
     torch.cuda.synchronize()
     grid.check()
     if log is not None:
-        log.append({"step": cfg.steps, "final": (grid.reso, grid.M), "stage_s": time.perf_counter() - t_stage})
+        log.append({"step": cfg.steps, "final": (grid.reso, grid.M), "stage_s": time.perf_counter() - t_stage,
+                    **_touched_curve(tr, grid.M, stage_start, cfg)})
     return grid
+
+
+def _touched_curve(tr: Trainer, M: int, stage_start: int, cfg: C2FConfig) -> dict:
+    """The stage's fraction of rows with a gradient, every `touched_every` steps and at its last step."""
+    if not cfg.track_touched:
+        return {}
+    frac = tr.touched_counts() / max(M, 1)
+    if frac.size == 0:
+        return {}
+    keep = list(range(0, frac.size, cfg.touched_every)) + [frac.size - 1]
+    return {"touched_frac": {int(stage_start + k): float(frac[k]) for k in keep}}

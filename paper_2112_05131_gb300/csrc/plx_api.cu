@@ -83,6 +83,8 @@ plx::RenderParams make_params(const plx_grid *g, const plx_render_opts *o) {
     p.stop = o->stop_thresh;
     double max_samples = std::sqrt(diag2) / delta + 2.0;
     p.max_chunks = (int)std::fmin(1e9, std::ceil(max_samples / 32.0) + 1.0);
+    p.lam_s = 0.0f;
+    p.loss_s = nullptr;
     return p;
 }
 
@@ -248,14 +250,20 @@ plx_status plx_render(const plx_grid *grid, const float *d_origins, const float 
 }
 
 plx_status plx_render_backward(const plx_grid *grid, const float *d_origins, const float *d_dirs, int64_t n,
-                               const plx_render_opts *opts, const float *d_grad_rgb, float *d_grad_rows, void *stream) {
+                               const plx_render_opts *opts, const float *d_grad_rgb, float *d_grad_rows,
+                               float lambda_sparsity, float *d_loss_sparsity, void *stream) {
     plx_status st = check_grid(grid);
     if (st == PLX_OK) st = check_opts(opts);
     if (st != PLX_OK) return st;
     if (n < 0 || n >= (int64_t(1) << 36)) return fail(PLX_EINVAL, "n out of range");
     if (n > 0 && (!d_origins || !d_dirs || !d_grad_rgb || !d_grad_rows)) return fail(PLX_EINVAL, "NULL buffer");
     if (d_grad_rows && !aligned(d_grad_rows, 16)) return fail(PLX_EINVAL, "d_grad_rows must be 16-byte aligned");
+    if (!(lambda_sparsity >= 0.0f) || !std::isfinite(lambda_sparsity))
+        return fail(PLX_EINVAL, "lambda_sparsity must be finite and >= 0");
+    if (d_loss_sparsity && !aligned(d_loss_sparsity, 4)) return fail(PLX_EINVAL, "d_loss_sparsity must be 4-byte aligned");
     plx::RenderParams p = make_params(grid, opts);
+    p.lam_s = lambda_sparsity;
+    p.loss_s = d_loss_sparsity;
     if (p.max_chunks > 256)
         return fail(PLX_EUNSUPPORTED, "rays of up to %d samples exceed the backward's 8192-sample limit; raise step_vox",
                     p.max_chunks * 32);
@@ -389,14 +397,20 @@ plx_status plx_render_planned_mse(const plx_grid *grid, const float *d_origins, 
 
 plx_status plx_render_backward_train(const plx_grid *grid, const float *d_origins, const float *d_dirs, int64_t n,
                                      const plx_render_opts *opts, const float *d_grad_rgb, const void *d_state,
-                                     size_t state_bytes, float *d_grad_rows, void *stream) {
+                                     size_t state_bytes, float *d_grad_rows, float lambda_sparsity,
+                                     float *d_loss_sparsity, void *stream) {
     plx_status st = check_grid(grid);
     if (st == PLX_OK) st = check_opts(opts);
     if (st != PLX_OK) return st;
     if (n < 0 || n >= (int64_t(1) << 31)) return fail(PLX_EINVAL, "n out of range");
     if (n > 0 && (!d_origins || !d_dirs || !d_grad_rgb || !d_grad_rows)) return fail(PLX_EINVAL, "NULL buffer");
     if (d_grad_rows && !aligned(d_grad_rows, 16)) return fail(PLX_EINVAL, "d_grad_rows must be 16-byte aligned");
-    const plx::RenderParams p = make_params(grid, opts);
+    if (!(lambda_sparsity >= 0.0f) || !std::isfinite(lambda_sparsity))
+        return fail(PLX_EINVAL, "lambda_sparsity must be finite and >= 0");
+    if (d_loss_sparsity && !aligned(d_loss_sparsity, 4)) return fail(PLX_EINVAL, "d_loss_sparsity must be 4-byte aligned");
+    plx::RenderParams p = make_params(grid, opts);
+    p.lam_s = lambda_sparsity;
+    p.loss_s = d_loss_sparsity;
     plx::MarchPtrs ptrs;
     plx::MarchHeader hdr;
     st = march_state(grid, d_origins, d_dirs, n, opts, p, const_cast<void *>(d_state), state_bytes, &ptrs, &hdr);
@@ -443,6 +457,14 @@ plx_status plx_count_nodes(const plx_grid *grid, const float *d_origins, const f
     plx::RenderParams p = make_params(grid, opts);
     return cuda_status(plx::launch_count_nodes(grid->view, d_origins, d_dirs, n, p, d_counts,
                                                static_cast<cudaStream_t>(stream)), "plx_count_nodes");
+}
+
+plx_status plx_count_touched(const plx_grid *grid, int64_t *d_count, void *stream) {
+    plx_status st = check_grid(grid);
+    if (st != PLX_OK) return st;
+    if (!d_count || !aligned(d_count, 8)) return fail(PLX_EINVAL, "d_count must be non-NULL and 8-byte aligned");
+    return cuda_status(plx::launch_count_touched(grid->view, d_count, static_cast<cudaStream_t>(stream)),
+                       "plx_count_touched");
 }
 
 plx_status plx_max_weight(const plx_grid *grid, const float *d_origins, const float *d_dirs, int64_t n,

@@ -311,6 +311,10 @@ struct RenderParams {
     float bg[3];
     float stop;
     int max_chunks;
+    // Cauchy sparsity prior (adjoints only): lam_s sum log(1 + 2 sigma^2) over the taken samples;
+    // lam_s = 0 leaves it out, loss_s (nullable) accumulates its value
+    float lam_s;
+    float *loss_s;
 };
 
 // March state written by plx_render_train and read by plx_render_backward_train.
@@ -398,6 +402,7 @@ cudaError_t launch_count_nodes(const GridView &g, const float *o, const float *d
                                int64_t *out, cudaStream_t s);
 cudaError_t launch_max_weight(const GridView &g, const float *o, const float *d, int64_t n, const RenderParams &p,
                               float *wmax, cudaStream_t s);
+cudaError_t launch_count_touched(const GridView &g, int64_t *out, cudaStream_t s);
 cudaError_t launch_mse_grad(const float *rgb, const float *target, int64_t n, float *grad, float *loss,
                             cudaStream_t s);
 cudaError_t launch_build_occupancy(const GridView &g, uint32_t *occ, cudaStream_t s);

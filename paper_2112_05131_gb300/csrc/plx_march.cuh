@@ -390,21 +390,37 @@ __device__ __forceinline__ int scan_range(const GridView &g, const RaySetup &rs,
     return cnt;
 }
 
+
+// The Cauchy sparsity prior (Sec. 3.7, Eq. 4) at one sample of density sigma >= 0 (taken: every
+// taken sample counts; sigma = 0 adds nothing): returns its density gradient
+// lam_s 4 sigma / (1 + 2 sigma^2) and adds lam_s sum log(1 + 2 sigma^2) over the warp's samples to
+// *p.loss_s (one atomic per warp).  Call from all 32 lanes.
+__device__ __forceinline__ float sparsity_prior(const RenderParams &p, bool taken, float sigma) {
+    if (p.lam_s == 0.0f) return 0.0f;  // uniform
+    const float s2 = taken ? 2.0f * sigma * sigma : 0.0f;
+    if (p.loss_s) {
+        const float l = warp_sum(log1pf(s2));
+        if ((threadIdx.x & 31) == 0 && l != 0.0f) atomicAdd(p.loss_s, p.lam_s * l);
+    }
+    return taken ? p.lam_s * 4.0f * sigma / (1.0f + s2) : 0.0f;
+}
+
 // --------------------------------------------------------------------------- adjoint of one sample
 // Gradients of one taken sample with positive density with respect to its
 // interpolated values (the adjoint of Eq. 1 with SH colour and ReLUs), scattered
 // to the cell's 8 corners with their trilinear weights (NULL corners skip):
-//   dL/dsigma = delta sum_ch g_ch (T_{s+1} c_ch - R_ch),   R = colour after the sample,
-//   dL/dk_{ch,l} = g_ch w [pre_ch > 0] Y_l.
+//   dL/dsigma = delta sum_ch g_ch (T_{s+1} c_ch - R_ch) + gsig_prior,   R = colour after the sample,
+//   dL/dk_{ch,l} = g_ch w [pre_ch > 0] Y_l,
+// gsig_prior being the density gradient of a per-sample prior (sparsity_prior).
 // Rows are accumulated with float4 atomics and marked in the touched mask.
 __device__ __forceinline__ void scatter_sample(const GridView &g, const int32_t rr[8], const float ff[3],
                                                const float Y[9], const float gr[3], const float pre[3],
                                                const float col[3], float w, float Tn, const float Rs[3],
-                                               float delta, float *__restrict__ grad_rows) {
+                                               float delta, float gsig_prior, float *__restrict__ grad_rows) {
     float gsig = 0.0f;
 #pragma unroll
     for (int ch = 0; ch < 3; ++ch) gsig = fmaf(gr[ch], Tn * col[ch] - Rs[ch], gsig);
-    gsig *= delta;
+    gsig = fmaf(gsig, delta, gsig_prior);
     float gpre[3];
 #pragma unroll
     for (int ch = 0; ch < 3; ++ch) gpre[ch] = pre[ch] > 0.0f ? gr[ch] * w : 0.0f;

@@ -304,6 +304,30 @@ __device__ __forceinline__ void rms_update(int64_t r, int q, float4 g4, float4 x
     }
 }
 
+// plx_count_touched: the number of rows marked in the touched bitmask, i.e. the rows that received a
+// gradient (adjoint or TV) since the last RMSProp step (Sec. 3.8: the gradient is sparse).  One CTA
+// sums the popcounts of the mask words and writes the total.
+__global__ void __launch_bounds__(1024) count_touched_kernel(GridView g, int64_t n_words, int64_t *__restrict__ out) {
+    __shared__ unsigned long long s_part[32];
+    unsigned long long c = 0;
+    for (int64_t w = threadIdx.x; w < n_words; w += blockDim.x) {
+        uint32_t word = __ldcg(g.touched + w);
+        const int64_t left = g.M - w * 32;  // >= 1
+        if (left < 32) word &= (1u << left) - 1u;
+        c += (unsigned long long)__popc(word);
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) c += __shfl_xor_sync(kFull, c, off);
+    if ((threadIdx.x & 31) == 0) s_part[threadIdx.x >> 5] = c;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        c = threadIdx.x < (blockDim.x >> 5) ? s_part[threadIdx.x] : 0ull;
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) c += __shfl_xor_sync(kFull, c, off);
+        if (threadIdx.x == 0) *out = (int64_t)c;
+    }
+}
+
 // Sparse mode, pass 1: the rows marked in the touched bitmask, as a list, and the mask cleared.  A
 // warp takes 32 mask words at a time; the order of the list does not matter (rows update independently).
 __global__ void __launch_bounds__(256) rms_compact_kernel(GridView g, int64_t n_words) {
@@ -400,6 +424,11 @@ cudaError_t launch_rmsprop(const GridView &g, float *rows, uint16_t *rows_h, flo
         cudaError_t e = cudaMemsetAsync(g.touched, 0, (size_t)n_words * 4, s);
         if (e != cudaSuccess) return e;
     }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_count_touched(const GridView &g, int64_t *out, cudaStream_t s) {
+    count_touched_kernel<<<1, 1024, 0, s>>>(g, (g.M + 31) / 32, out);
     return cudaGetLastError();
 }
 

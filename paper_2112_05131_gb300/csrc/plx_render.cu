@@ -354,8 +354,9 @@ __global__ void __launch_bounds__(kBwdWarps * 32, kGatherBlocks) render_bwd_kern
             Rs[ch] = Rsuf[ch] + suf_ex;
             Rsuf[ch] += __shfl_sync(kFull, suf, 0);
         }
+        const float gprior = sparsity_prior(p, take && occupied, sig);
         if (take && occupied && sig > 0.0f)
-            scatter_sample(g, rr, ff, rs.Y, gr, pre, col, w, cp.Tn, Rs, p.delta, grad_rows);
+            scatter_sample(g, rr, ff, rs.Y, gr, pre, col, w, cp.Tn, Rs, p.delta, gprior, grad_rows);
     }
 }
 

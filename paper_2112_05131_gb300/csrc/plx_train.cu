@@ -525,7 +525,9 @@ __global__ void __launch_bounds__(kChunkWarps * 32, VALS ? kBwdValsBlocks : kGat
             if (lane == 31) suf_ex = 0.0f;
             Rs[ch] = Ra[ch] + suf_ex;
         }
-        if (cp.take && sig > 0.0f) scatter_sample(g, rr, ff, rs.Y, gr, pre, col, w, cp.Tn, Rs, p.delta, grad_rows);
+        const float gprior = sparsity_prior(p, cp.take, sig);
+        if (cp.take && sig > 0.0f)
+            scatter_sample(g, rr, ff, rs.Y, gr, pre, col, w, cp.Tn, Rs, p.delta, gprior, grad_rows);
         __syncwarp();  // every lane is done with this slot before the next fetch overwrites it
     }
     asm volatile("cp.async.wait_all;\n" ::: "memory");

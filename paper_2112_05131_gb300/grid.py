@@ -171,14 +171,19 @@ class Grid:
         return rgb
 
     def render_backward(self, origins, dirs, grad_rgb, opts: RenderOpts = RenderOpts(),
-                        grad_rows: Optional[torch.Tensor] = None, stream=None):
+                        grad_rows: Optional[torch.Tensor] = None, lambda_sparsity: float = 0.0,
+                        loss_sparsity: Optional[torch.Tensor] = None, stream=None):
+        """plx_render_backward; lambda_sparsity > 0 adds the Cauchy sparsity prior (its value is added to
+        loss_sparsity, a float32 [1] device tensor, when given)."""
         n = origins.shape[0]
         _need(grad_rgb, torch.float32, "grad_rgb", (n, 3))
         if grad_rows is None:
             grad_rows = torch.zeros((self.M, ROW), dtype=torch.float32, device=origins.device)
         _need(grad_rows, torch.float32, "grad_rows", (self.M, ROW))
+        if loss_sparsity is not None:
+            _need(loss_sparsity, torch.float32, "loss_sparsity", (1,))
         L.call("plx_render_backward", self.handle, _p(origins), _p(dirs), n, ctypes.byref(opts.c()), _p(grad_rgb),
-               _p(grad_rows), _stream(stream))
+               _p(grad_rows), float(lambda_sparsity), _p(loss_sparsity), _stream(stream))
         return grad_rows
 
     def march_state_bytes(self, n: int, opts: RenderOpts = RenderOpts()) -> int:
@@ -241,16 +246,21 @@ class Grid:
         return rgb
 
     def render_backward_train(self, origins, dirs, grad_rgb, opts: RenderOpts, state: torch.Tensor,
-                              grad_rows: Optional[torch.Tensor] = None, stream=None):
-        """plx_render_backward_train: the adjoint of the last render_train on these rays, from its state."""
+                              grad_rows: Optional[torch.Tensor] = None, lambda_sparsity: float = 0.0,
+                              loss_sparsity: Optional[torch.Tensor] = None, stream=None):
+        """plx_render_backward_train: the adjoint of the last render_train on these rays, from its state
+        (with the Cauchy sparsity prior when lambda_sparsity > 0, as render_backward)."""
         n = origins.shape[0]
         _need(grad_rgb, torch.float32, "grad_rgb", (n, 3))
         _need(state, torch.uint8, "state")
         if grad_rows is None:
             grad_rows = torch.zeros((self.M, ROW), dtype=torch.float32, device=origins.device)
         _need(grad_rows, torch.float32, "grad_rows", (self.M, ROW))
+        if loss_sparsity is not None:
+            _need(loss_sparsity, torch.float32, "loss_sparsity", (1,))
         L.call("plx_render_backward_train", self.handle, _p(origins), _p(dirs), n, ctypes.byref(opts.c()),
-               _p(grad_rgb), _p(state), state.numel(), _p(grad_rows), _stream(stream))
+               _p(grad_rgb), _p(state), state.numel(), _p(grad_rows), float(lambda_sparsity), _p(loss_sparsity),
+               _stream(stream))
         return grad_rows
 
     def count_nodes(self, origins, dirs, opts: RenderOpts = RenderOpts(), stream=None) -> torch.Tensor:
@@ -260,6 +270,14 @@ class Grid:
         out = torch.empty((n, 3), dtype=torch.int64, device=origins.device)
         L.call("plx_count_nodes", self.handle, _p(origins), _p(dirs), n, ctypes.byref(opts.c()), _p(out),
                _stream(stream))
+        return out
+
+    def count_touched(self, out: Optional[torch.Tensor] = None, stream=None) -> torch.Tensor:
+        """plx_count_touched: rows that received a gradient since the last RMSProp step (int64 [1], device)."""
+        if out is None:
+            out = torch.empty(1, dtype=torch.int64, device=self.idx.device)
+        _need(out, torch.int64, "out", (1,))
+        L.call("plx_count_touched", self.handle, _p(out), _stream(stream))
         return out
 
     def max_weight(self, origins, dirs, opts: RenderOpts = RenderOpts(), wmax: Optional[torch.Tensor] = None,

@@ -2,7 +2,8 @@
 
 One step (Supp. B.1: 5000-ray batches, RMSProp, stochastic TV on contiguous segments):
   plx_gen_rays -> plx_march_plan -> plx_render_planned_mse (forward and MSE gradient)
-  -> plx_render_backward_train -> plx_tv_grad -> plx_rmsprop_step
+  -> plx_render_backward_train (with the Cauchy sparsity prior when configured) -> plx_tv_grad
+  -> plx_rmsprop_step
 all libplenoxel calls with no host synchronisation.  The training march splits rays into chunk work
 items and hands the march state from the forward to the adjoint.
 
@@ -52,11 +53,18 @@ class StepConfig:
     opts: RenderOpts = field(default_factory=lambda: RenderOpts(0.5, (1.0, 1.0, 1.0), 0.0))
     lambda_tv_sigma: float = 1e-5
     lambda_tv_sh: float = 1e-3
+    # Cauchy sparsity prior on the samples' densities (Sec. 3.7; the paper uses 1e-12 on forward-facing and
+    # 1e-11 on 360-degree scenes, none on synthetic ones), fused into the adjoint; its value accumulates in
+    # Trainer.loss_sparsity
+    lambda_sparsity: float = 0.0
     beta: float = 0.95
     eps: float = 1e-8
     sparse_rmsprop: bool = True
     # three streams and a deferred RMSProp (see the module docstring); False: one stream, in order
     overlap: bool = True
+    # record, every step, how many rows received a gradient (plx_count_touched; Sec. 3.8's gradient
+    # sparsity), into Trainer.touched_counts()
+    track_touched: bool = False
 
 
 class Trainer:
@@ -76,6 +84,7 @@ class Trainer:
         self.rgb = torch.empty((n, 3), dtype=torch.float32, device=dev)
         self.grad_rgb = torch.empty((n, 3), dtype=torch.float32, device=dev)
         self.loss = torch.zeros(1, dtype=torch.float32, device=dev)
+        self.loss_sparsity = torch.zeros(1, dtype=torch.float32, device=dev)
         self.state = grid.new_march_state(n, cfg.opts)  # fits every batch of up to n rays
         if cfg.overlap:
             # the march (update, forward, MSE, adjoint) and the plan on high-priority streams, TV on a
@@ -87,6 +96,26 @@ class Trainer:
         self._ev = {k: torch.cuda.Event() for k in ("start", "plan", "rms", "tv", "bwd", "end")}
         self._bwd_recorded = False
         self.pending = None  # (lr_sigma, lr_sh) of an update not yet applied
+        self._touched = torch.zeros(1 << 16 if cfg.track_touched else 0, dtype=torch.int64, device=dev)
+        self._n_touched = 0
+
+    def _count_touched(self, stream):
+        """Appends this step's touched-row count (before the update clears the mask) to the log."""
+        if not self.cfg.track_touched:
+            return
+        if self._n_touched == self._touched.numel():  # grow the log; ordered on `stream` like its writes
+            with torch.cuda.stream(stream):
+                grown = torch.zeros(2 * self._touched.numel(), dtype=torch.int64, device=self._touched.device)
+                grown[: self._n_touched].copy_(self._touched)
+            self._touched.record_stream(stream)  # its memory is not reused before `stream` is past the copy
+            self._touched = grown
+        self.grid.count_touched(self._touched[self._n_touched:self._n_touched + 1], stream=stream)
+        self._n_touched += 1
+
+    def touched_counts(self):
+        """Rows that received a gradient in each recorded step (host int64 array; synchronises)."""
+        torch.cuda.synchronize(self._touched.device)
+        return self._touched[: self._n_touched].cpu().numpy()
 
     def _update(self, main, lrs):
         c = self.cfg
@@ -126,10 +155,12 @@ class Trainer:
             g.render_planned_mse(o, d, c.opts, self.state, target, rgb, grgb, self.loss, stream=main)
             mark(3)
             mark(4)
-            g.render_backward_train(o, d, grgb, c.opts, self.state, self.grad, stream=main)
+            g.render_backward_train(o, d, grgb, c.opts, self.state, self.grad, c.lambda_sparsity,
+                                    self.loss_sparsity if c.lambda_sparsity > 0 else None, stream=main)
             mark(5)
             if do_tv:
                 g.tv_grad(seg_start, seg_len, n_selected, c.lambda_tv_sigma, c.lambda_tv_sh, self.grad, stream=main)
+            self._count_touched(main)
             mark(6)
             self._update(main, (lr_s, lr_h))
             mark(7)
@@ -167,12 +198,14 @@ class Trainer:
         g.render_planned_mse(o, d, c.opts, self.state, target, rgb, grgb, self.loss, stream=ms)
         mark(3)
         mark(4)
-        g.render_backward_train(o, d, grgb, c.opts, self.state, self.grad, stream=ms)
+        g.render_backward_train(o, d, grgb, c.opts, self.state, self.grad, c.lambda_sparsity,
+                                self.loss_sparsity if c.lambda_sparsity > 0 else None, stream=ms)
         ev["bwd"].record(ms)
         self._bwd_recorded = True
         mark(5)
         if do_tv:
             ms.wait_event(ev["tv"])
+        self._count_touched(ms)
         self.pending = (lr_s, lr_h)
         mark(6)
         mark(7)

@@ -92,7 +92,7 @@ def test_host_validation_rejects_bad_arguments(lib):
     opts = _lib.plx_render_opts()
     opts.step_vox = 0.5
     _einval(lib, lib.plx_render(null, null, null, 10, ctypes.byref(opts), null, null, null))
-    _einval(lib, lib.plx_render_backward(null, null, null, 10, ctypes.byref(opts), null, null, null))
+    _einval(lib, lib.plx_render_backward(null, null, null, 10, ctypes.byref(opts), null, null, 0.0, null, null))
     _einval(lib, lib.plx_gen_rays(null, 0, 8, 8, null, 4, null, null, null))
     _einval(lib, lib.plx_gen_rays(null, 1, 8, 8, null, 4, null, null, null))
     _einval(lib, lib.plx_mse_grad(null, null, 3, null, null, null))
