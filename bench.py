@@ -62,7 +62,13 @@ def parse_args():
     ap.add_argument("--c2f-steps", type=int, default=12800)
     ap.add_argument("--c2f-prune", choices=("density", "weight"), default="density",
                     help="coarse-to-fine pruning: density >= 5, or maximum weight >= 0.256 (Sec. 3.4)")
+    ap.add_argument("--c2f-paper", action="store_true",
+                    help="run the coarse-to-fine loop on the paper's synthetic schedule instead (256^3 start, "
+                         "weight prune and upsample at 38400, 128000 steps, TV in stage 1 only; about 2 minutes)")
     ap.add_argument("--skip-large-batch", action="store_true", help="leave out the 2^18-ray batch measurement")
+    ap.add_argument("--only-render", action="store_true",
+                    help="profiling aid: only the full-frame renders of the held-out views (FP32, then BF16-SH), "
+                         "no training step; the first plx_render launches are three untimed FP32 frames")
     return ap.parse_args()
 
 
@@ -255,6 +261,10 @@ def run_ours(args, world, rank, local):
     stream = torch.cuda.current_stream()
     opts = RenderOpts(0.5, (1.0, 1.0, 1.0), 0.0)
     cams_t = torch.from_numpy(wl["cams"]).to(dev)
+
+    if args.only_render:
+        print(json.dumps({"only_render": True, "workload": args.workload, "render": frame_renders(args, wl, dev, opts)}))
+        return
 
     gt_grid = Grid.from_host(R, wl["gt"].idx, wl["gt"].rows)
     dev_batches = []
@@ -474,34 +484,7 @@ def extras(args, wl, dev_batches, cams_t, gt_grid, opts, timed_loop, st32, ms32)
 
     # ---- full-frame renders: 25 held-out 800x800 views, FP32 and BF16-SH
     if wl["test_cams"]:
-        tc = synth.cameras_config(wl["test_cams"])
-        tc_t = torch.from_numpy(tc).to(dev)
-        npx = W * H
-        frames = []
-        for v in range(tc.shape[0]):
-            pix = torch.arange(v * npx, (v + 1) * npx, dtype=torch.int64, device=dev)
-            frames.append(gen_rays(tc_t, pix, W, H))
-        rgb = torch.empty((npx, 3), device=dev)
-        res["render"] = {}
-        for form, name in ((0, "f32"), (1, "bf16_sh")):
-            g = Grid.from_host(R, wl["gt"].idx, wl["gt"].rows, sh_form=form)
-            for o, d in frames[:3]:
-                g.render(o, d, opts, rgb)
-            times = []
-            for rep in range(args.render_reps):
-                for o, d in frames:
-                    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-                    e0.record(stream)
-                    g.render(o, d, opts, rgb)
-                    e1.record(stream)
-                    times.append((e0, e1))
-            torch.cuda.synchronize()
-            ms = np.array([x.elapsed_time(y) for x, y in times])
-            res["render"][name] = {"p50_ms": float(np.percentile(ms, 50)), "p99_ms": float(np.percentile(ms, 99)),
-                                   "mean_ms": float(ms.mean()), "frames": int(ms.size),
-                                   "Mrays_per_s": npx / (ms.mean() / 1e3) / 1e6, "resolution": f"{W}x{H}"}
-            del g
-        del frames
+        res["render"] = frame_renders(args, wl, dev, opts)
         torch.cuda.empty_cache()
 
     # ---- fwd+bwd at 2^18-ray batches (a 5000-ray batch underfills the GPU)
@@ -583,6 +566,48 @@ def extras(args, wl, dev_batches, cams_t, gt_grid, opts, timed_loop, st32, ms32)
     return res
 
 
+def frame_renders(args, wl, dev, opts, forms=((0, "f32"), (1, "bf16_sh"))):
+    """Full frames of the held-out views, one launch of plx_render per 800x800 frame (rays generated
+    beforehand), three untimed frames first, then render_reps passes over all views, each frame timed with
+    CUDA events on the launching stream."""
+    import torch
+
+    import synth
+    from paper_2112_05131_gb300.grid import Grid, gen_rays
+
+    R, W, H = wl["R"], wl["W"], wl["H"]
+    stream = torch.cuda.current_stream()
+    tc = synth.cameras_config(wl["test_cams"])
+    tc_t = torch.from_numpy(tc).to(dev)
+    npx = W * H
+    frames = []
+    for v in range(tc.shape[0]):
+        pix = torch.arange(v * npx, (v + 1) * npx, dtype=torch.int64, device=dev)
+        frames.append(gen_rays(tc_t, pix, W, H))
+    rgb = torch.empty((npx, 3), device=dev)
+    out = {}
+    for form, name in forms:
+        g = Grid.from_host(R, wl["gt"].idx, wl["gt"].rows, sh_form=form)
+        for o, d in frames[:3]:
+            g.render(o, d, opts, rgb)
+        times = []
+        for rep in range(args.render_reps):
+            for o, d in frames:
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                g.render(o, d, opts, rgb)
+                e1.record(stream)
+                times.append((e0, e1))
+        torch.cuda.synchronize()
+        g.check()
+        ms = np.array([x.elapsed_time(y) for x, y in times])
+        out[name] = {"p50_ms": float(np.percentile(ms, 50)), "p99_ms": float(np.percentile(ms, 99)),
+                     "mean_ms": float(ms.mean()), "frames": int(ms.size),
+                     "Mrays_per_s": npx / (ms.mean() / 1e3) / 1e6, "resolution": f"{W}x{H}"}
+        del g
+    return out
+
+
 def large_batch(args, wl, cams_t, gt_grid, opts, n=1 << 18, steps=8, warmup=3):
     """The same optimisation step on 2^18-ray batches of the workload (FP32 rows)."""
     import torch
@@ -641,16 +666,22 @@ def coarse_to_fine(args, wl, cams_t, gt_grid, opts):
     test_t = torch.from_numpy(synth.cameras_config(wl["test_cams"])).to(cams_t.device)
     truth = render_views(gt_grid, test_t, W, H, opts)
     prep = time.perf_counter() - t0
-    cfg = C2FConfig(steps=args.c2f_steps, upsample_at=(args.c2f_steps // 3, 2 * args.c2f_steps // 3),
-                    prune_by=args.c2f_prune, track_touched=True, touched_every=500)
+    if args.c2f_paper:
+        from paper_2112_05131_gb300.coarse_to_fine import paper_synthetic
+
+        cfg = paper_synthetic()
+        cfg.track_touched, cfg.touched_every = True, 4000
+    else:
+        cfg = C2FConfig(steps=args.c2f_steps, upsample_at=(args.c2f_steps // 3, 2 * args.c2f_steps // 3),
+                        prune_by=args.c2f_prune, track_touched=True, touched_every=500)
     log = []
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     g = train(images, cams_t, W, H, cfg, log)
     wall = time.perf_counter() - t0
     final = render_views(g, test_t, W, H, opts)
-    out = {"steps": cfg.steps, "batch": cfg.batch, "prune_by": cfg.prune_by, "wall_s": wall,
-           "steps_per_s": cfg.steps / wall,
+    out = {"steps": cfg.steps, "batch": cfg.batch, "start_reso": cfg.start_reso, "upsample_at": list(cfg.upsample_at),
+           "prune_by": cfg.prune_by, "tv_until": cfg.tv_until, "wall_s": wall, "steps_per_s": cfg.steps / wall,
            "stages": log, "final_reso": g.reso, "final_rows": g.M,
            "psnr_test_db": psnr(final, truth), "views": {"train": images.shape[0], "test": truth.shape[0]},
            "images_render_s": prep}
@@ -729,9 +760,26 @@ def cpu_baseline(args, wl, budget_s=15.0):
         spent += time.perf_counter() - t0
         rays += pix.shape[0]
         b += 1
-    return {"value": rays / spent, "unit": "rays/s", "cores": oracle.num_threads(), "kind": "oracle",
+    cores = oracle.num_threads()
+    # the same work on one core, on the first 1000 rays of a batch
+    pix = wl["batches"][0][0][:1000]
+    o64, d64 = oracle.gen_rays(cams64, pix)
+    tgt, _ = oracle.render(R, wl["gt"].idx, gt64, o64, d64)
+    oracle.set_num_threads(1)
+    try:
+        t0 = time.perf_counter()
+        o64, d64 = oracle.gen_rays(cams64, pix)
+        rgb, _ = oracle.render(R, sc.idx, rows64, o64, d64)
+        _, grgb = oracle.mse(rgb, tgt)
+        oracle.render_backward(R, sc.idx, rows64, o64, d64, grgb)
+        t1 = time.perf_counter() - t0
+    finally:
+        oracle.set_num_threads(cores)
+    return {"value": rays / spent, "unit": "rays/s", "cores": cores, "kind": "oracle",
             "sample": f"{b} batches of {args.batch} rays ({rays} rays) of the {R}^3 workload: ray generation, "
-                      "forward, MSE and adjoint in FP64, OpenMP over rays", "seconds": spent}
+                      "forward, MSE and adjoint in FP64, OpenMP over rays", "seconds": spent,
+            "single_core": {"value": pix.shape[0] / t1, "unit": "rays/s", "cores": 1,
+                            "sample": f"the first {pix.shape[0]} rays of one batch", "seconds": t1}}
 
 
 def run_reference(args, world, rank):

@@ -170,7 +170,7 @@ plx_status plx_render(const plx_grid *grid, const float *d_origins, const float 
                       const plx_render_opts *opts, float *d_rgb, float *d_T_end, void *stream);
 
 /* Adjoint of plx_render (Sec. 3.5: the renderer is differentiated end to end;
- * Supp. B.1 "gradient kernels").  d_grad_rgb float [n][3] = dL/dC.  Adds
+ * Supp. B.1, on its gradient kernels).  d_grad_rgb float [n][3] = dL/dC.  Adds
  * dL/d(row values) into d_grad_rows F32 [n_rows][32] (+=; padding columns
  * untouched) and marks the rows it touches in the grid's touched bitmask.
  * The march is recomputed (no per-sample state is stored).  Per sample:

@@ -70,6 +70,7 @@ def _load():
             "orc_upsample": (I64, [I64, P, P, I64, I64, P, P]),
             "orc_round_bf16": (None, [P, I64]),
             "orc_num_threads": (ctypes.c_int, []),
+            "orc_set_num_threads": (None, [ctypes.c_int]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(lib, name)
@@ -101,6 +102,11 @@ def _rows(rows):
 
 def num_threads() -> int:
     return int(_load().orc_num_threads())
+
+
+def set_num_threads(n: int) -> None:
+    """Threads of the OpenMP regions from now on (the default is every host core)."""
+    _load().orc_set_num_threads(int(n))
 
 
 def sh_basis(dirs):

@@ -19,7 +19,7 @@
  *   - a data row holds 28 values [sigma, R0..R8, G0..G8, B0..B8] at
  *     `row_stride` doubles per row (28 or more; FP32 inputs convert exactly);
  *   - NULL cells count as all-zero values (Supp. B.1);
- *   - values live on the lattice nodes ("each occupied voxel corner", Sec. 3);
+ *   - values live on the lattice nodes, the voxel corners (Sec. 3);
  *     node (i,j,k) sits at aabb_min + (i,j,k) * h, h = (aabb_max-aabb_min)/(R-1).
  *
  * Parity status of each function (what pins it, in tests/test_oracle_pins.py):
@@ -355,7 +355,7 @@ void orc_render(int64_t R, const int32_t *idx, const double *rows, int64_t row_s
 
 /*
  * Exported adjoint of orc_render (Sec. 3.5: the renderer is differentiable;
- * Supp. B.1 "gradient kernels").  grad_rgb [n,3] = dL/dC.  Accumulates
+ * Supp. B.1, on its gradient kernels).  grad_rgb [n,3] = dL/dC.  Accumulates
  * (+=) dL/d(row values) into grad_rows [M, 28] (FP64, dense 28 columns).
  *
  * Per sample s, with R_s = sum_{j>s} w_j c_j + T_end bg computed as an
@@ -825,5 +825,15 @@ int orc_num_threads(void)
     return omp_get_max_threads();
 #else
     return 1;
+#endif
+}
+
+/* Sets the number of threads later OpenMP regions use (no effect without OpenMP). */
+void orc_set_num_threads(int n)
+{
+#ifdef _OPENMP
+    if (n > 0) omp_set_num_threads(n);
+#else
+    (void)n;
 #endif
 }

@@ -14,7 +14,8 @@ and upsample are plx_grid_prune_* / plx_grid_upsample_*.
 The training images are the ground-truth grid rendered by plx_render for every training view and
 held in host memory; each step's 5000 pixels are drawn on the host with a seeded generator, their
 target colours gathered there, and both copied to the device (the role a data loader plays).
-The paper does not give the steps at which it upsamples; `upsample_at` defaults to thirds of the run.
+The paper does not give the steps at which it upsamples for a 128^3 start; `upsample_at` defaults to
+thirds of the run.  `paper_synthetic()` is the paper's own synthetic schedule (Supp. B.2).
 """
 from __future__ import annotations
 
@@ -42,6 +43,7 @@ class C2FConfig:
     lambda_tv_sh: float = 1e-3
     tv_fraction: float = 0.01
     tv_segment: int = 4096
+    tv_until: Optional[int] = None  # steps from which TV is off (Supp. B.2: synthetic scenes keep it for stage 1)
     init_sigma: float = 0.1
     opts: RenderOpts = field(default_factory=lambda: RenderOpts(0.5, (1.0, 1.0, 1.0), 0.0))
     chunk: int = 256  # steps whose pixel batches are prepared and uploaded together
@@ -50,6 +52,14 @@ class C2FConfig:
     # sparse within the first minutes); each stage's log entry then holds it every `touched_every` steps
     track_touched: bool = False
     touched_every: int = 100
+
+
+def paper_synthetic() -> C2FConfig:
+    """The paper's schedule for synthetic scenes (Supp. B.2): a 256^3 start, weight-threshold prune (0.256)
+    and upsample to 512^3 after 38400 steps, 128000 steps in all, TV (1e-5 density, 1e-3 SH) during the
+    first stage only."""
+    return C2FConfig(steps=128000, start_reso=256, upsample_at=(38400,), prune_by="weight", weight_tau=0.256,
+                     lambda_tv_sigma=1e-5, lambda_tv_sh=1e-3, tv_until=38400)
 
 
 def dense_grid(R: int, sigma: float, device="cuda") -> Grid:
@@ -79,7 +89,8 @@ def psnr(a: np.ndarray, b: np.ndarray) -> float:
 
 
 class _Batches:
-    """Pixel ids, targets and TV segments for `chunk` steps at a time, uploaded in one copy each."""
+    """Pixel ids, targets and TV segments for `chunk` steps at a time, each uploaded in one copy from
+    pinned memory, so that a step issues no host-to-device copy of its own."""
 
     def __init__(self, images: np.ndarray, cfg: C2FConfig, device):
         self.flat = images.reshape(-1, 3)
@@ -88,21 +99,25 @@ class _Batches:
         self.dev = device
         self.rng = np.random.default_rng(cfg.seed)
         self.step0 = -1
-        self.pix = self.tgt = None
+        self.R = -1
+        self.pix = self.tgt = self.ss = self.sl = None
 
     def get(self, step: int, R: int):
         import synth
 
         c = self.cfg
-        if self.pix is None or step >= self.step0 + c.chunk or step < self.step0:
-            self.step0 = step
+        if self.pix is None or R != self.R or step >= self.step0 + c.chunk or step < self.step0:
+            self.step0, self.R = step, R
             pix = self.rng.integers(0, self.n_pix, size=(c.chunk, c.batch), dtype=np.int64)
-            self.pix = torch.from_numpy(pix).pin_memory().to(self.dev, non_blocking=True)
-            self.tgt = torch.from_numpy(self.flat[pix]).pin_memory().to(self.dev, non_blocking=True)
+            segs = [synth.tv_segments(R, c.tv_fraction, min(c.tv_segment, R ** 3), seed=int(self.rng.integers(2 ** 31)))
+                    for _ in range(c.chunk)]
+            self.n_sel = [int(sl.sum()) for _, sl in segs]
+            ss = np.stack([a for a, _ in segs])  # every step has the same number of segments
+            sl = np.stack([b for _, b in segs])
+            up = lambda a: torch.from_numpy(a).pin_memory().to(self.dev, non_blocking=True)
+            self.pix, self.tgt, self.ss, self.sl = up(pix), up(self.flat[pix]), up(ss), up(sl)
         k = step - self.step0
-        ss, sl = synth.tv_segments(R, c.tv_fraction, min(c.tv_segment, R ** 3), seed=int(self.rng.integers(2 ** 31)))
-        return (self.pix[k], self.tgt[k], torch.from_numpy(ss).to(self.dev, non_blocking=True),
-                torch.from_numpy(sl).to(self.dev, non_blocking=True), int(sl.sum()))
+        return self.pix[k], self.tgt[k], self.ss[k], self.sl[k], self.n_sel[k]
 
 
 def train(train_images: np.ndarray, cams: torch.Tensor, W: int, H: int, cfg: C2FConfig = C2FConfig(),
@@ -143,6 +158,8 @@ def train(train_images: np.ndarray, cams: torch.Tensor, W: int, H: int, cfg: C2F
             t_stage = time.perf_counter()
             stage_start = step
         pix, tgt, ss, sl, nsel = batches.get(step, grid.reso)
+        if cfg.tv_until is not None and step >= cfg.tv_until:
+            ss = sl = None
         tr.step(pix, tgt, ss, sl, nsel, lr_sigma(step), lr_sh(step))
     tr.finish()
     torch.cuda.synchronize()

@@ -152,6 +152,8 @@ plx_status plx_grid_create(const plx_grid_desc *desc, const int32_t *d_idx, floa
     v.rows = d_rows_f32;
     v.rows_h = d_rows_bf16;
     v.occ = reinterpret_cast<const uint32_t *>(g->ws + g->layout.occ_off);
+    v.occ_coarse = reinterpret_cast<const uint32_t *>(g->ws + g->layout.coarse_off);
+    v.nb = (int)plx::coarse_blocks_per_axis(desc->reso);
     v.occ_box = reinterpret_cast<const int *>(g->ws + g->layout.status_off + plx::WorkspaceLayout::kOccBoxOff);
     v.touched = reinterpret_cast<uint32_t *>(g->ws + g->layout.touched_off);
     v.tlist = reinterpret_cast<int32_t *>(g->ws + g->layout.list_off);
@@ -174,7 +176,9 @@ plx_status plx_grid_create(const plx_grid_desc *desc, const int32_t *d_idx, floa
     cudaError_t e = cudaMemsetAsync(g->ws + g->layout.status_off, 0, 256, s);
     if (e == cudaSuccess)
         e = cudaMemsetAsync(g->ws + g->layout.touched_off, 0, g->layout.list_off - g->layout.touched_off, s);
-    if (e == cudaSuccess) e = plx::launch_build_occupancy(v, reinterpret_cast<uint32_t *>(g->ws + g->layout.occ_off), s);
+    if (e == cudaSuccess)
+        e = plx::launch_build_occupancy(v, reinterpret_cast<uint32_t *>(g->ws + g->layout.occ_off),
+                                        reinterpret_cast<uint32_t *>(g->ws + g->layout.coarse_off), s);
     if (e != cudaSuccess) {
         delete g;
         return cuda_status(e, "plx_grid_create");

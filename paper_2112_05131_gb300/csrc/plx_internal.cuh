@@ -26,17 +26,23 @@ enum : int { kDevOk = 0, kDevBadRow = 1, kDevTooManySamples = 2, kDevCountMismat
 // Workspace layout of a grid: [status block 256 B][occupancy bits][touched bits][touched-row list].
 // The status block holds the device status word at byte 0, the touched-list length at byte 64 and the
 // box of non-empty cells at byte 128 (six ints: R-1-lo per axis, then hi per axis).
+// Coarse blocks of 8^3 cells: one bit per block, set when a cell of the block has an occupied corner.
+constexpr int kBlockLog = 3;
+__host__ __device__ inline int64_t coarse_blocks_per_axis(int64_t R) { return ((R - 2) >> kBlockLog) + 1; }
+
 struct WorkspaceLayout {
-    size_t status_off, occ_off, touched_off, list_off, total;
+    size_t status_off, occ_off, coarse_off, touched_off, list_off, total;
     static constexpr size_t kListCountOff = 64;
     static constexpr size_t kOccBoxOff = 128;
     static size_t round256(size_t b) { return (b + 255) & ~size_t(255); }
     static WorkspaceLayout make(int64_t R, int64_t M) {
         WorkspaceLayout L;
         int64_t nodes = R * R * R;
+        const int64_t nb = coarse_blocks_per_axis(R);
         L.status_off = 0;
         L.occ_off = 256;
-        L.touched_off = L.occ_off + round256(size_t((nodes + 31) / 32) * 4);
+        L.coarse_off = L.occ_off + round256(size_t((nodes + 31) / 32) * 4);
+        L.touched_off = L.coarse_off + round256(size_t((nb * nb * nb + 31) / 32) * 4);
         L.list_off = L.touched_off + round256(size_t((M + 31) / 32 + 1) * 4);
         L.total = L.list_off + round256(size_t(M) * 4);
         return L;
@@ -48,6 +54,8 @@ struct GridView {
     const float *rows;          // F32 rows (may be null for a render-only BF16 grid)
     const uint16_t *rows_h;     // BF16-SH rows (null for the F32 form)
     const uint32_t *occ;        // bit per base node: 1 if any of the cell's 8 nodes is occupied
+    const uint32_t *occ_coarse; // bit per block of 8^3 cells: 1 if any of its cells is non-empty
+    int nb;                     // blocks per axis, coarse_blocks_per_axis(R)
     const int *occ_box;         // cells with an occupied corner lie in [R-1-box[a], box[3+a]] on axis a
     uint32_t *touched;          // bit per row: set when a gradient lands on the row
     int32_t *tlist;             // the touched rows as a list (built by the sparse RMSProp step)
@@ -405,7 +413,7 @@ cudaError_t launch_max_weight(const GridView &g, const float *o, const float *d,
 cudaError_t launch_count_touched(const GridView &g, int64_t *out, cudaStream_t s);
 cudaError_t launch_mse_grad(const float *rgb, const float *target, int64_t n, float *grad, float *loss,
                             cudaStream_t s);
-cudaError_t launch_build_occupancy(const GridView &g, uint32_t *occ, cudaStream_t s);
+cudaError_t launch_build_occupancy(const GridView &g, uint32_t *occ, uint32_t *occ_coarse, cudaStream_t s);
 cudaError_t launch_pack_bf16(const GridView &g, uint16_t *rows_h, cudaStream_t s);
 cudaError_t launch_tv(const GridView &g, const int64_t *seg_start, const int64_t *seg_len, int64_t n_seg,
                       int64_t n_selected, float scale_sigma, float scale_sh, float *grad_rows, float *loss,

@@ -127,12 +127,14 @@ __device__ __forceinline__ uint4 ldg4_pinned(const uint4 *p) {
 }
 
 // Full sample: interpolated values at grid point gc, whose cell the caller has
-// already found occupied (compaction).  rows_out/f_out receive the corners.
+// already found occupied (compaction).  rows_out/f_out (and base_out, if given)
+// receive the corners.
 __device__ __forceinline__ bool gather_sample(const GridView &g, int form, const DF gc[3], float acc[kNV],
-                                              int32_t rows_out[8], float f_out[3]) {
+                                              int32_t rows_out[8], float f_out[3], int64_t *base_out = nullptr) {
 #pragma unroll
     for (int q = 0; q < kNV; ++q) acc[q] = 0.0f;
     Cell c = locate(g, gc);
+    if (base_out) *base_out = c.base;
     f_out[0] = c.f[0];
     f_out[1] = c.f[1];
     f_out[2] = c.f[2];
@@ -325,6 +327,59 @@ __device__ __forceinline__ Cand test_candidate(const GridView &g, const RaySetup
     return c;
 }
 
+// --------------------------------------------------------------------------- coarse skipping
+// Before the per-sample test, candidates are screened in groups of kGroup consecutive samples
+// against the coarse mask (one bit per 8^3-cell block): a group none of whose samples can lie in a
+// non-empty cell is skipped whole.  A round of 32 kCand = 256 candidates is 32 groups, one per lane;
+// candidate 32 j + l of the round belongs to group 4 j + l / 8.
+constexpr int kGroup = 8;
+static_assert(32 * kCand == 32 * kGroup, "a round is one group per lane");
+
+// Can a sample with index in [s0, s0 + kGroup) lie in a cell with an occupied corner?  Never false
+// when one does.  The samples lie on the segment between the first and the last, whose FP32 grid
+// coordinates are within rs.feps of the exact ones (the bound holds a fortiori a few samples past
+// t_far, where the extra error is ~1e-6 of a cell against the bound's 25% slack), so their cells
+// lie in the box of cells of the two endpoints widened by feps, clamped as locate() clamps; the
+// coarse bits of that box's blocks (at most 2 per axis; a wider box answers yes) decide.
+__device__ __forceinline__ bool group_live(const GridView &g, const RaySetup &rs, const RenderParams &p, int s0) {
+    if (s0 >= rs.s_hi) return false;
+    const float ta = fmaf((float)s0, p.delta, rs.tn.hi);
+    const float tb = fmaf((float)(s0 + kGroup - 1), p.delta, rs.tn.hi);
+    const float cmax = (float)(g.R - 2);
+    int lo[3], hi[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        const float xa = fmaf(ta, rs.dg[a], rs.og[a]);
+        const float xb = fmaf(tb, rs.dg[a], rs.og[a]);
+        const float c0 = fminf(fmaxf(floorf(fminf(xa, xb) - rs.feps), 0.0f), cmax);
+        const float c1 = fminf(fmaxf(floorf(fmaxf(xa, xb) + rs.feps), 0.0f), cmax);
+        lo[a] = (int)c0 >> kBlockLog;
+        hi[a] = (int)c1 >> kBlockLog;
+    }
+    if (hi[0] - lo[0] > 1 || hi[1] - lo[1] > 1 || hi[2] - lo[2] > 1) return true;
+    for (int i = lo[0]; i <= hi[0]; ++i)
+        for (int j = lo[1]; j <= hi[1]; ++j)
+            for (int k = lo[2]; k <= hi[2]; ++k) {
+                const int b = (i * g.nb + j) * g.nb + k;
+                if ((__ldg(g.occ_coarse + (b >> 5)) >> (b & 31)) & 1u) return true;
+            }
+    return false;
+}
+
+// Tests the candidates of one round starting at sample `first` (candidate 32 j + lane in c[j]), the
+// ones in skipped groups answering (invalid, empty), and returns the ballot of live groups.
+__device__ __forceinline__ unsigned test_round(const GridView &g, const RaySetup &rs, const RenderParams &p, int first,
+                                               int end, int lane, Cand c[kCand]) {
+    const unsigned live = __ballot_sync(kFull, group_live(g, rs, p, first + kGroup * lane));
+#pragma unroll
+    for (int j = 0; j < kCand; ++j) {
+        const int s = first + 32 * j + lane;
+        c[j].valid = c[j].occ = false;
+        if (((live >> (4 * j + (lane >> 3))) & 1u) && s < end) c[j] = test_candidate(g, rs, p, s);
+    }
+    return live;
+}
+
 struct Stream {
     int next;   // next candidate sample index to test
     int head;   // ring read position (absolute)
@@ -332,23 +387,23 @@ struct Stream {
     bool exhausted;
 };
 
-// Append occupied candidates until 32 are queued or the ray has no candidates left.
+// Append occupied candidates until 32 are queued or the ray has no candidates left (none at or
+// beyond s_hi).
 __device__ __forceinline__ void refill(const GridView &g, const RaySetup &rs, const RenderParams &p, int *ring,
                                        Stream &st, int lane) {
     const unsigned lt = (1u << lane) - 1u;
     while (st.tail - st.head < 32 && !st.exhausted) {
         Cand c[kCand];
+        if (test_round(g, rs, p, st.next, rs.s_hi, lane, c)) {  // uniform
 #pragma unroll
-        for (int j = 0; j < kCand; ++j) c[j] = test_candidate(g, rs, p, st.next + 32 * j + lane);
-#pragma unroll
-        for (int j = 0; j < kCand; ++j) {
-            const unsigned m = __ballot_sync(kFull, c[j].occ);
-            if (c[j].occ) ring[(st.tail + __popc(m & lt)) & (kRing - 1)] = st.next + 32 * j + lane;
-            st.tail += __popc(m);
+            for (int j = 0; j < kCand; ++j) {
+                const unsigned m = __ballot_sync(kFull, c[j].occ);
+                if (c[j].occ) ring[(st.tail + __popc(m & lt)) & (kRing - 1)] = st.next + 32 * j + lane;
+                st.tail += __popc(m);
+            }
         }
-        // valid candidates form a prefix of the sample indices
-        st.exhausted = __ballot_sync(kFull, c[kCand - 1].valid) != kFull;
         st.next += 32 * kCand;
+        st.exhausted = st.next >= rs.s_hi;
     }
     __syncwarp();
 }
@@ -369,15 +424,7 @@ __device__ __forceinline__ int scan_range(const GridView &g, const RaySetup &rs,
     int cnt = 0;
     for (int base = first; base < end; base += 32 * kCand) {
         Cand c[kCand];
-#pragma unroll
-        for (int j = 0; j < kCand; ++j) {
-            const int s = base + 32 * j + lane;
-            if (s < end) {
-                c[j] = test_candidate(g, rs, p, s);
-            } else {
-                c[j].valid = c[j].occ = false;
-            }
-        }
+        if (!test_round(g, rs, p, base, end, lane, c)) continue;  // uniform
 #pragma unroll
         for (int j = 0; j < kCand; ++j) {
             const unsigned m = __ballot_sync(kFull, c[j].occ);
@@ -413,10 +460,19 @@ __device__ __forceinline__ float sparsity_prior(const RenderParams &p, bool take
 //   dL/dk_{ch,l} = g_ch w [pre_ch > 0] Y_l,
 // gsig_prior being the density gradient of a per-sample prior (sparsity_prior).
 // Rows are accumulated with float4 atomics and marked in the touched mask.
-__device__ __forceinline__ void scatter_sample(const GridView &g, const int32_t rr[8], const float ff[3],
-                                               const float Y[9], const float gr[3], const float pre[3],
-                                               const float col[3], float w, float Tn, const float Rs[3],
-                                               float delta, float gsig_prior, float *__restrict__ grad_rows) {
+//
+// scatter_chunk does this for the 32 samples of a chunk, called by all 32 lanes (`scat`: this lane's sample is taken
+// and has positive density).  Consecutive samples of a ray often share a cell (two per cell at half a
+// voxel's step), and then their gradients go to the same 8 rows: since Y is the ray's, a corner k
+// receives wk (gsig, gpre_0 Y, gpre_1 Y, gpre_2 Y), so four numbers per corner and sample carry all of it.
+// Lanes are paired within each run of equal cells (positions 0-1, 2-3, ... of the run); the even lane
+// adds its partner's 32 numbers (8 corners x 4, by shuffles) and scatters both, the odd lane nothing,
+// which halves the atomics of such runs.  `cell`: the sample's cell base node (any value when !scat).
+__device__ __forceinline__ void scatter_chunk(const GridView &g, bool scat, int64_t cell, const int32_t rr[8],
+                                              const float ff[3], const float Y[9], const float gr[3],
+                                              const float pre[3], const float col[3], float w, float Tn,
+                                              const float Rs[3], float delta, float gsig_prior,
+                                              float *__restrict__ grad_rows, int lane) {
     float gsig = 0.0f;
 #pragma unroll
     for (int ch = 0; ch < 3; ++ch) gsig = fmaf(gr[ch], Tn * col[ch] - Rs[ch], gsig);
@@ -424,19 +480,47 @@ __device__ __forceinline__ void scatter_sample(const GridView &g, const int32_t 
     float gpre[3];
 #pragma unroll
     for (int ch = 0; ch < 3; ++ch) gpre[ch] = pre[ch] > 0.0f ? gr[ch] * w : 0.0f;
+    float a[8], b[8][3];
+    unsigned wmask = 0u;  // corners with a non-zero trilinear weight and a row
 #pragma unroll
     for (int k = 0; k < 8; ++k) {
-        if (rr[k] < 0) continue;
-        const float wk = corner_weight(ff, k);
-        if (wk == 0.0f) continue;
-        float v[kNV];
-        v[0] = wk * gsig;
+        const float wk = scat && rr[k] >= 0 ? corner_weight(ff, k) : 0.0f;
+        if (wk != 0.0f) wmask |= 1u << k;
+        a[k] = wk * gsig;
+#pragma unroll
+        for (int ch = 0; ch < 3; ++ch) b[k][ch] = wk * gpre[ch];
+    }
+    // runs of equal cells among the scattering lanes; a lane continues a run when the previous one has
+    // its cell (the key of a lane that does not scatter is unique)
+    const int64_t key = scat ? cell : -1 - (int64_t)lane;
+    const int64_t prev_key = __shfl_up_sync(kFull, key, 1);
+    const unsigned cont = __ballot_sync(kFull, lane > 0 && prev_key == key);
+    const unsigned upto = lane == 31 ? kFull : ((2u << lane) - 1u);
+    const int start = 31 - __clz(~cont & upto);   // bit 0 of ~cont is always set
+    const bool odd = ((lane - start) & 1) != 0;
+    const bool absorb = !odd && lane < 31 && ((cont >> (lane + 1)) & 1u);
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+        const float an = __shfl_down_sync(kFull, a[k], 1);
+        if (absorb) a[k] += an;
 #pragma unroll
         for (int ch = 0; ch < 3; ++ch) {
-            const float gw = wk * gpre[ch];
-#pragma unroll
-            for (int l = 0; l < 9; ++l) v[1 + 9 * ch + l] = gw * Y[l];
+            const float bn = __shfl_down_sync(kFull, b[k][ch], 1);
+            if (absorb) b[k][ch] += bn;
         }
+    }
+    const unsigned wn = __shfl_down_sync(kFull, wmask, 1);
+    if (absorb) wmask |= wn;
+    if (!scat || odd) return;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+        if (!((wmask >> k) & 1u)) continue;
+        float v[kNV];
+        v[0] = a[k];
+#pragma unroll
+        for (int ch = 0; ch < 3; ++ch)
+#pragma unroll
+            for (int l = 0; l < 9; ++l) v[1 + 9 * ch + l] = b[k][ch] * Y[l];
         float4 *dst = reinterpret_cast<float4 *>(grad_rows + (int64_t)rr[k] * kRowF);
 #pragma unroll
         for (int q = 0; q < 7; ++q) atomicAdd(dst + q, make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]));

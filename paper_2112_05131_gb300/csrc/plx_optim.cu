@@ -65,7 +65,37 @@ __global__ void __launch_bounds__(256) occ_box_kernel(GridView g, const uint32_t
     if (threadIdx.x < 6 && s_box[threadIdx.x] > 0) atomicMax(&box[threadIdx.x], s_box[threadIdx.x]);
 }
 
-cudaError_t launch_build_occupancy(const GridView &g, uint32_t *occ, cudaStream_t s) {
+// The coarse mask: one thread per block of 8^3 cells ORs the cell bits of its 64 rows of up to 8 cells
+// (cells (i, j, k) with 0 <= i, j, k <= R - 2; the bit of cell (i, j, k) sits at node id (i R + j) R + k).
+__global__ void __launch_bounds__(256) coarse_occupancy_kernel(GridView g, const uint32_t *__restrict__ occ,
+                                                               uint32_t *__restrict__ coarse) {
+    const int64_t R = g.R, nb = g.nb;
+    const int64_t n_blocks = nb * nb * nb;
+    const int64_t n_words = (n_blocks + 31) / 32;
+    for (int64_t w = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); w < n_words;
+         w += (int64_t)gridDim.x * (blockDim.x >> 5)) {
+        const int64_t b = w * 32 + (threadIdx.x & 31);
+        bool any = false;
+        if (b < n_blocks) {
+            const int64_t bi = b / (nb * nb), bj = (b / nb) % nb, bk = b % nb;
+            const int64_t k0 = bk << kBlockLog, k1 = min(k0 + (1 << kBlockLog), R - 1);  // cells [k0, k1)
+            const uint64_t want = (k1 > k0) ? ((1ull << (k1 - k0)) - 1ull) : 0ull;
+            for (int64_t i = bi << kBlockLog; i < min((bi + 1) << kBlockLog, R - 1) && !any; ++i)
+                for (int64_t j = bj << kBlockLog; j < min((bj + 1) << kBlockLog, R - 1) && !any; ++j) {
+                    const int64_t n0 = (i * R + j) * R + k0;  // first cell bit of the row's run
+                    const int64_t w0 = n0 >> 5;
+                    const int sh = (int)(n0 & 31);
+                    uint64_t bits = __ldg(occ + w0);
+                    if (sh + (k1 - k0) > 32) bits |= (uint64_t)__ldg(occ + w0 + 1) << 32;
+                    any = ((bits >> sh) & want) != 0ull;
+                }
+        }
+        const unsigned word = __ballot_sync(kFull, any);
+        if ((threadIdx.x & 31) == 0) coarse[w] = word;
+    }
+}
+
+cudaError_t launch_build_occupancy(const GridView &g, uint32_t *occ, uint32_t *occ_coarse, cudaStream_t s) {
     const int64_t R = g.R;
     const int64_t n_words = (R * R * R + 31) / 32;
     const int threads = 256;
@@ -74,6 +104,10 @@ cudaError_t launch_build_occupancy(const GridView &g, uint32_t *occ, cudaStream_
     build_occupancy_kernel<<<(unsigned)blocks, threads, 0, s>>>(g, occ, n_words);
     const int64_t bblocks = std::min<int64_t>((n_words + 255) / 256, 152 * 8);
     occ_box_kernel<<<(unsigned)bblocks, 256, 0, s>>>(g, occ, n_words, const_cast<int *>(g.occ_box));
+    const int64_t nb = g.nb;
+    const int64_t c_words = (nb * nb * nb + 31) / 32;
+    const int64_t cblocks = std::max<int64_t>(1, std::min<int64_t>((c_words + 7) / 8, 152 * 64));
+    coarse_occupancy_kernel<<<(unsigned)cblocks, 256, 0, s>>>(g, occ, occ_coarse);
     return cudaGetLastError();
 }
 
@@ -118,6 +152,9 @@ cudaError_t launch_pack_bf16(const GridView &g, uint16_t *rows_h, cudaStream_t s
 // average segment length) as it has 256-node spans, so short and long runs
 // both fill the GPU.
 constexpr int kTvThreads = 256;
+constexpr int kTvBlocks = 4;       // CTAs per SM the register budget allows
+constexpr int kTvSpansPerWarp = 1; // 32-node spans a warp takes per item (more, with the next one's index loads prefetched, measured slower)
+constexpr int kTvGridPerSm = 32;  // at most this many CTAs per SM in the grid (a persistent grid measured slower)
 
 __device__ __forceinline__ float4 ld4(const float *p) { return __ldg(reinterpret_cast<const float4 *>(p)); }
 
@@ -167,16 +204,49 @@ __device__ __forceinline__ void tv_quarter(const GridView &g, int32_t rs, const 
         atomicAdd(reinterpret_cast<float4 *>(grad + (int64_t)rs * kRowF + 4 * q), make_float4(gs[0], gs[1], gs[2], gs[3]));
 }
 
-// A warp takes 32 consecutive selected nodes: lane l reads the index of node l and of its +x, +y, +z
-// neighbours; nodes with no occupied row among the four are skipped; the others are processed four
-// at a time with 8 lanes each (one float4 quarter per lane), so a node's rows take one round trip.
-__global__ void __launch_bounds__(kTvThreads) tv_kernel(GridView g, const int64_t *__restrict__ seg_start,
-                                                        const int64_t *__restrict__ seg_len, int64_t n_seg,
-                                                        int64_t parts, float lam_sigma, float lam_sh,
-                                                        float *__restrict__ grad, float *__restrict__ loss) {
+// The index entries of one lane's node of a 32-node span: the node's row and those of its +x, +y, +z
+// neighbours (-1: NULL, outside the grid, or outside the segment).
+struct TvSpan {
+    int32_t rs, rn[3];
+};
+
+// Lane l's entries for node start + off0 + l (off0: the span's offset in its segment of length len).
+// (i, j, k) of the span's first node by one division, then carried lane by lane.
+__device__ __forceinline__ TvSpan tv_load_span(const GridView &g, int64_t start, int64_t len, int64_t off0, int lane) {
     const int64_t R = g.R;
     const int64_t N = R * R * R;
-    const float scale = (float)R / 256.0f;
+    TvSpan t = {-1, {-1, -1, -1}};
+    const int64_t n0 = start + off0;
+    const int64_t n = n0 + lane;
+    if (off0 + lane >= len || n0 < 0 || n >= N) return t;
+    int64_t i = n0 / (R * R);
+    const int64_t rem = n0 - i * R * R;
+    int64_t j = rem / R;
+    int64_t k = rem - j * R + lane;
+    while (k >= R) {
+        k -= R;
+        if (++j == R) {
+            j = 0;
+            ++i;
+        }
+    }
+    t.rs = row_of(g, n);
+    t.rn[0] = i + 1 < R ? row_of(g, n + R * R) : -1;
+    t.rn[1] = j + 1 < R ? row_of(g, n + R) : -1;
+    t.rn[2] = k + 1 < R ? row_of(g, n + 1) : -1;
+    return t;
+}
+
+// A warp takes the 32-node spans of its (segment, part) item in turn, loading the next span's index
+// entries before it processes the current one, so the two memory round trips of a span (index, then
+// rows) overlap across spans.  Nodes with no occupied row among self and +x/+y/+z are skipped; the
+// others are processed four at a time with 8 lanes each (one float4 quarter per lane), so a node's
+// rows take one round trip.
+__global__ void __launch_bounds__(kTvThreads, kTvBlocks) tv_kernel(GridView g, const int64_t *__restrict__ seg_start,
+                                                                   const int64_t *__restrict__ seg_len, int64_t n_seg,
+                                                                   int64_t parts, float lam_sigma, float lam_sh,
+                                                                   float *__restrict__ grad, float *__restrict__ loss) {
+    const float scale = (float)g.R / 256.0f;
     const int lane = threadIdx.x & 31;
     const int q = lane & 7;
     const int grp = lane >> 3;
@@ -189,41 +259,20 @@ __global__ void __launch_bounds__(kTvThreads) tv_kernel(GridView g, const int64_
         const int64_t part = item % parts;
         const int64_t start = seg_start[sg];
         const int64_t len = seg_len[sg];
-        for (int64_t off0 = (part * kWarps + wid) * 32; off0 < len; off0 += parts * kWarps * 32) {
-            const int64_t off = off0 + lane;
-            const int64_t n = start + off;
-            // (i, j, k) of the warp's first node by one division, then carried lane by lane
-            const int64_t n0 = start + off0;
-            int64_t i = 0, j = 0, k = 0;
-            if (n0 >= 0 && n0 < N) {
-                i = n0 / (R * R);
-                const int64_t rem = n0 - i * R * R;
-                j = rem / R;
-                k = rem - j * R + lane;
-                while (k >= R) {
-                    k -= R;
-                    if (++j == R) {
-                        j = 0;
-                        ++i;
-                    }
-                }
-            }
-            int32_t rs = -1, rn[3] = {-1, -1, -1};
-            if (off < len && n0 >= 0 && n >= 0 && n < N) {
-                rs = row_of(g, n);
-                rn[0] = i + 1 < R ? row_of(g, n + R * R) : -1;
-                rn[1] = j + 1 < R ? row_of(g, n + R) : -1;
-                rn[2] = k + 1 < R ? row_of(g, n + 1) : -1;
-            }
-            unsigned mask = __ballot_sync(kFull, rs >= 0 || rn[0] >= 0 || rn[1] >= 0 || rn[2] >= 0);
+        const int64_t stride = parts * kWarps * 32;
+        int64_t off0 = (part * kWarps + wid) * 32;
+        TvSpan cur = tv_load_span(g, start, len, off0, lane);
+        for (; off0 < len; off0 += stride) {
+            const TvSpan nxt = tv_load_span(g, start, len, off0 + stride, lane);
+            unsigned mask = __ballot_sync(kFull, cur.rs >= 0 || cur.rn[0] >= 0 || cur.rn[1] >= 0 || cur.rn[2] >= 0);
             while (mask) {  // uniform
                 const int cnt = __popc(mask);
                 const bool active = grp < cnt;
                 const int src = active ? __fns(mask, 0, grp + 1) : 0;
-                const int32_t ms = __shfl_sync(kFull, rs, src);
+                const int32_t ms = __shfl_sync(kFull, cur.rs, src);
                 int32_t mn[3];
 #pragma unroll
-                for (int a = 0; a < 3; ++a) mn[a] = __shfl_sync(kFull, rn[a], src);
+                for (int a = 0; a < 3; ++a) mn[a] = __shfl_sync(kFull, cur.rn[a], src);
                 if (active && q < 7) {
                     tv_quarter(g, ms, mn, q, scale, lam_sigma, lam_sh, grad, loss_acc);
                     if (q == 0) {
@@ -235,6 +284,7 @@ __global__ void __launch_bounds__(kTvThreads) tv_kernel(GridView g, const int64_
                 }
                 for (int k = 0; k < 4 && mask; ++k) mask &= mask - 1u;
             }
+            cur = nxt;
         }
     }
     if (loss) {
@@ -247,12 +297,17 @@ cudaError_t launch_tv(const GridView &g, const int64_t *seg_start, const int64_t
                       int64_t n_selected, float lam_sigma, float lam_sh, float *grad_rows, float *loss,
                       cudaStream_t s) {
     if (n_seg == 0) return cudaSuccess;
-    // parts per segment: one 32-node span per warp of the average segment
-    constexpr int64_t kCtaNodes = kTvThreads;
+    // parts per segment: kTvSpansPerWarp spans per warp of the average segment; one CTA per item (the
+    // block scheduler balances the short-lived CTAs), at most 2^20 items
+    constexpr int64_t kCtaNodes = (int64_t)kTvThreads * kTvSpansPerWarp;
     const int64_t avg = (n_selected + n_seg - 1) / n_seg;
     const int64_t parts = std::max<int64_t>(1, std::min<int64_t>((avg + kCtaNodes - 1) / kCtaNodes, 1 << 20));
-    int64_t blocks = n_seg * parts;
-    if (blocks > 152 * 32) blocks = 152 * 32;
+    int sms = 152;
+    {
+        int dev = 0;
+        if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    }
+    const int64_t blocks = std::min<int64_t>(n_seg * parts, (int64_t)sms * kTvGridPerSm);
     tv_kernel<<<(unsigned)blocks, kTvThreads, 0, s>>>(g, seg_start, seg_len, n_seg, parts, lam_sigma, lam_sh,
                                                       grad_rows, loss);
     return cudaGetLastError();

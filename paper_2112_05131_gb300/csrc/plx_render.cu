@@ -330,12 +330,13 @@ __global__ void __launch_bounds__(kBwdWarps * 32, kGatherBlocks) render_bwd_kern
         float acc[kNV];
         int32_t rr[8];
         float ff[3];
+        int64_t cell = -1;
         float sig = 0.0f, pre[3] = {0.0f, 0.0f, 0.0f}, col[3] = {0.0f, 0.0f, 0.0f};
         bool occupied = false;
         if (valid) {
             DF gc[3];
             sample_coords(g, rs, sample_t(rs, p, s), gc);
-            occupied = gather_sample(g, FORM, gc, acc, rr, ff);
+            occupied = gather_sample(g, FORM, gc, acc, rr, ff, &cell);
             if (occupied) {
                 sig = fmaxf(acc[0], 0.0f);
                 colour_of(acc, rs.Y, pre, col);
@@ -355,8 +356,8 @@ __global__ void __launch_bounds__(kBwdWarps * 32, kGatherBlocks) render_bwd_kern
             Rsuf[ch] += __shfl_sync(kFull, suf, 0);
         }
         const float gprior = sparsity_prior(p, take && occupied, sig);
-        if (take && occupied && sig > 0.0f)
-            scatter_sample(g, rr, ff, rs.Y, gr, pre, col, w, cp.Tn, Rs, p.delta, gprior, grad_rows);
+        scatter_chunk(g, take && occupied && sig > 0.0f, cell, rr, ff, rs.Y, gr, pre, col, w, cp.Tn, Rs, p.delta,
+                      gprior, grad_rows, lane);
     }
 }
 

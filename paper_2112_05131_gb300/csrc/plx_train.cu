@@ -110,15 +110,7 @@ __global__ void __launch_bounds__(kPlanWarps * 32) march_plan_kernel(GridView g,
             for (int q = wid; q < nw; q += kPlanWarps) {
                 const int base = s_first + (w0 + q) * kSpan;
                 Cand c[kCand];
-#pragma unroll
-                for (int j = 0; j < kCand; ++j) {
-                    const int sidx = base + 32 * j + lane;
-                    if (sidx < L) {
-                        c[j] = test_candidate(g, rs, p, sidx);
-                    } else {
-                        c[j].valid = c[j].occ = false;
-                    }
-                }
+                test_round(g, rs, p, base, L, lane, c);
                 int cnt = 0;
 #pragma unroll
                 for (int j = 0; j < kCand; ++j) {
@@ -490,6 +482,7 @@ __global__ void __launch_bounds__(kChunkWarps * 32, VALS ? kBwdValsBlocks : kGat
         const bool valid = lane < cnt;
         int32_t rr[8];
         float ff[3];
+        int64_t cell = -1;
         float sig = 0.0f, pre[3] = {0.0f, 0.0f, 0.0f}, col[3] = {0.0f, 0.0f, 0.0f};
         if (valid) {
             DF gc[3];
@@ -497,6 +490,7 @@ __global__ void __launch_bounds__(kChunkWarps * 32, VALS ? kBwdValsBlocks : kGat
             if (VALS) {  // the forward's values; only the corners are looked up again
                 const float4 v = st.vals[(ray * mc + k) * 32 + lane];
                 const Cell c = locate(g, gc);
+                cell = c.base;
 #pragma unroll
                 for (int a = 0; a < 3; ++a) ff[a] = c.f[a];
 #pragma unroll
@@ -509,7 +503,7 @@ __global__ void __launch_bounds__(kChunkWarps * 32, VALS ? kBwdValsBlocks : kGat
                 for (int ch = 0; ch < 3; ++ch) col[ch] = fmaxf(pre[ch], 0.0f);
             } else {
                 float acc[kNV];
-                gather_sample(g, FORM, gc, acc, rr, ff);
+                gather_sample(g, FORM, gc, acc, rr, ff, &cell);
                 sig = fmaxf(acc[0], 0.0f);
                 colour_of(acc, rs.Y, pre, col);
             }
@@ -526,8 +520,8 @@ __global__ void __launch_bounds__(kChunkWarps * 32, VALS ? kBwdValsBlocks : kGat
             Rs[ch] = Ra[ch] + suf_ex;
         }
         const float gprior = sparsity_prior(p, cp.take, sig);
-        if (cp.take && sig > 0.0f)
-            scatter_sample(g, rr, ff, rs.Y, gr, pre, col, w, cp.Tn, Rs, p.delta, gprior, grad_rows);
+        scatter_chunk(g, cp.take && sig > 0.0f, cell, rr, ff, rs.Y, gr, pre, col, w, cp.Tn, Rs, p.delta, gprior,
+                      grad_rows, lane);
         __syncwarp();  // every lane is done with this slot before the next fetch overwrites it
     }
     asm volatile("cp.async.wait_all;\n" ::: "memory");

@@ -67,9 +67,10 @@ def tile_origins(W: int, H: int) -> Tuple[np.ndarray, np.ndarray]:
 
 
 def scene_device_bytes(R: int, M: int, form: int = 1) -> int:
-    """Device bytes of a render-only grid: index volume, rows, occupancy mask and workspace."""
+    """Device bytes of a render-only grid: index volume, rows, occupancy masks (cells and 8^3-cell blocks)
+    and the rest of the workspace (an upper bound)."""
     row = 64 if form == 1 else 128
-    return 4 * R ** 3 + row * M + R ** 3 // 8 + M // 8 + 4096
+    return 4 * R ** 3 + row * M + R ** 3 // 8 + R ** 3 // 4096 + M // 8 + 4 * M + 8192
 
 
 class TileServer:

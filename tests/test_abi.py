@@ -63,12 +63,15 @@ def test_workspace_sizes(lib):
     d.n_rows = 4_000_000
     d.sh_form = 0
     ws = lib.plx_grid_workspace_bytes(ctypes.byref(d))
-    # status block + one bit per node + one bit per row + a 4-byte list entry per row, each rounded to 256 bytes
+    # status block + one bit per node + one bit per 8^3-cell block (64 blocks per axis: cells 0..510) + one
+    # bit per row + a 4-byte list entry per row, each rounded to 256 bytes
 
     def up(b):
         return (b + 255) // 256 * 256
 
-    assert ws == 256 + up(512 ** 3 // 8) + up(((4_000_000 + 31) // 32 + 1) * 4) + up(4_000_000 * 4)
+    nb = (512 - 2) // 8 + 1
+    assert ws == 256 + up(512 ** 3 // 8) + up((nb ** 3 + 31) // 32 * 4) + up(((4_000_000 + 31) // 32 + 1) * 4) \
+        + up(4_000_000 * 4)
     assert ws % 256 == 0
     d.reso = 1
     assert lib.plx_grid_workspace_bytes(ctypes.byref(d)) == 0

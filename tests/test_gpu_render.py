@@ -163,13 +163,16 @@ def test_count_nodes_on_a_dense_grid(cuda_lib):
     assert np.all((counts[:, 0] > 0) == (aux[:, 1] > 0))
 
 
-@pytest.mark.parametrize("node", [(0, 0, 0), (9, 4, 13), (15, 15, 15), (0, 15, 7)])
-def test_render_single_occupied_node(cuda_lib, node):
+@pytest.mark.parametrize("R,node", [(16, (0, 0, 0)), (16, (9, 4, 13)), (16, (15, 15, 15)), (16, (0, 15, 7)),
+                                    (16, (8, 8, 8)), (16, (7, 8, 15)), (41, (24, 8, 32)), (41, (40, 16, 0)),
+                                    (41, (17, 23, 39))])
+def test_render_single_occupied_node(cuda_lib, R, node):
     """Only one node occupied: the march bounds each ray's candidates by the box of non-empty cells (the
-    cells around that node), so rays must still see the node from every direction and position."""
+    cells around that node) and screens groups of samples against the 8^3-cell block mask, so rays must
+    still see the node from every direction and position, including nodes on block faces (coordinates
+    multiple of 8, whose cells straddle two blocks) and at the far faces of the grid."""
     from paper_2112_05131_gb300.grid import Grid, RenderOpts
 
-    R = 16
     idx = np.full(R ** 3, -1, np.int32)
     i, j, k = node
     idx[(i * R + j) * R + k] = 0
@@ -194,3 +197,30 @@ def test_render_single_occupied_node(cuda_lib, node):
     ref, aux = oracle.render(R, idx, rows, o.astype(float), d.astype(float), bg=opts.bg)
     check_colours(rgb, ref, aux, rows, delta_of(R, 0.5), opts.bg)
     assert np.sum(np.abs(ref - np.float64(opts.bg)).max(1) > 1e-3) > 100  # many rays do see the node
+
+
+def test_render_sheets_on_block_faces(cuda_lib):
+    """Occupied node planes at i = 8, j = 16 and k = 24 of a 33^3 grid (cells on either side of a face of
+    the 8^3-cell blocks) and a thin diagonal line of nodes: every ray through them is checked against the
+    oracle, so a group of samples wrongly screened out would show as a missing sheet."""
+    from paper_2112_05131_gb300.grid import Grid, RenderOpts
+
+    R = 33
+    rng = np.random.default_rng(71)
+    occ = np.zeros((R, R, R), bool)
+    occ[8, :, :] = True
+    occ[:, 16, :] = True
+    occ[:, :, 24] = True
+    t = np.arange(R)
+    occ[t, (t * 7) % R, R - 1 - t] = True
+    occ = occ.reshape(-1) & (rng.uniform(size=R ** 3) < 0.7)
+    idx = np.full(R ** 3, -1, np.int32)
+    idx[occ] = np.arange(int(occ.sum()), dtype=np.int32)
+    rows = rng.normal(0, 0.4, size=(int(occ.sum()), 28)).astype(np.float32)
+    rows[:, 0] = rng.uniform(0.0, 20.0, size=rows.shape[0]).astype(np.float32)
+    sc = synth.Scene(R, idx, rows)
+    o, d = synth.random_rays(3000, seed=72, spread=0.9)
+    opts = RenderOpts(0.5, (1.0, 1.0, 1.0), 0.0)
+    rgb, _, ref, aux, rows_used = _render_both(sc, o, d, opts)
+    check_colours(rgb, ref, aux, rows_used, delta_of(R, 0.5), opts.bg)
+    assert np.sum(np.abs(ref - 1.0).max(1) > 1e-2) > 2000  # most rays cross a sheet

@@ -18,13 +18,15 @@ BG = (1.0, 1.0, 1.0)
 
 
 def _scene(R, frac, seed):
+    """Densities bounded away from 0, so that no interpolated density sits near the ReLU kink: there
+    FP32 and FP64 could disagree on its sign, and with it on whether a row receives anything."""
     rng = np.random.default_rng(seed)
     occ = rng.uniform(size=R ** 3) < frac
     idx = np.full(R ** 3, -1, np.int32)
     idx[occ] = np.arange(int(occ.sum()), dtype=np.int32)
     M = int(occ.sum())
     rows = rng.normal(0, 0.4, size=(M, 28)).astype(np.float32)
-    rows[:, 0] = rng.uniform(-3.0, 25.0, size=M).astype(np.float32)
+    rows[:, 0] = rng.uniform(0.5, 25.0, size=M).astype(np.float32)
     return synth.Scene(R, idx, rows)
 
 
@@ -33,7 +35,10 @@ def test_count_touched_equals_oracle_gradient_support(cuda_lib, with_tv):
     from paper_2112_05131_gb300.grid import Grid, RenderOpts
 
     sc = _scene(40, 0.15, 31)
-    o, d = synth.random_rays(1200, seed=32)
+    # rays from inside the box: a ray entering through a face has its first sample exactly on the face,
+    # where the oracle's corner weights on the far side are exactly 0 and the GPU's may be ~1e-9 (so the
+    # GPU would touch rows the oracle leaves at zero)
+    o, d = synth.random_rays(1200, seed=32, radius=0.7)
     _, aux = oracle.render(sc.R, sc.idx, sc.rows, o.astype(float), d.astype(float), bg=BG)
     keep = ~tie_flags(aux, delta_of(sc.R, 0.5))
     o, d = o[keep], d[keep]
