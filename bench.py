@@ -149,26 +149,32 @@ def barrier(world):
         dist.barrier()
 
 
-def max_over_ranks(x: float, world: int) -> float:
+def _reduce(x: float, world: int, op: str) -> float:
+    """x reduced over the ranks (MAX or SUM); a device tensor under NCCL, a host one under gloo."""
     if world == 1:
         return x
     import torch
     import torch.distributed as dist
 
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
-    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    device = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX if op == "max" else dist.ReduceOp.SUM)
     return float(t.item())
+
+
+def max_over_ranks(x: float, world: int) -> float:
+    return _reduce(x, world, "max")
 
 
 def sum_over_ranks(x: float, world: int) -> float:
-    if world == 1:
-        return x
-    import torch
-    import torch.distributed as dist
+    return _reduce(x, world, "sum")
 
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
-    dist.all_reduce(t, op=dist.ReduceOp.SUM)
-    return float(t.item())
+
+def whole_job_rate(units: float, ms: float, world: int):
+    """(units all ranks processed per second over the slowest rank's time, that time in ms): the replicas'
+    weak-scaling aggregate."""
+    ms_max = max_over_ranks(ms, world)
+    return sum_over_ranks(units, world) / (ms_max / 1e3), ms_max
 
 
 def load_peaks():
@@ -276,7 +282,8 @@ def run_ours(args, world, rank, local):
                             int(sl.sum())))
     torch.cuda.synchronize()
 
-    def timed_loop(grid, K, Wm, per_stage=True, overlap=True):
+    def timed_loop(grid, K, Wm, per_stage=True, overlap=True, ranks=world):
+        # ranks: the replicas that time this loop together (1 for rank 0's extras, which the others skip)
         tr = Trainer(grid, cams_t, W, H, StepConfig(batch=args.batch, opts=opts, overlap=overlap))
         nb = len(dev_batches)
         for s in range(Wm):
@@ -286,7 +293,7 @@ def run_ours(args, world, rank, local):
         torch.cuda.synchronize()
         evs = [[torch.cuda.Event(enable_timing=True) for _ in range(8)] for _ in range(K)] if per_stage else None
         start, stop = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        barrier(world)
+        barrier(ranks)
         torch.cuda.synchronize()
         clk = ClockSampler(local)
         clk.start()
@@ -299,7 +306,7 @@ def run_ours(args, world, rank, local):
         stop.record(stream)
         torch.cuda.synchronize()
         clocks = clk.stop()
-        barrier(world)
+        barrier(ranks)
         ms = start.elapsed_time(stop)
         stages = None
         if per_stage:  # stage names: "serial|overlapped"; "-" marks an empty interval
@@ -316,9 +323,7 @@ def run_ours(args, world, rank, local):
     train_s = Grid.from_host(R, wl["train"].idx, wl["train"].rows)
     ms_serial, st32, _, _ = timed_loop(train_s, args.steps, args.warmup, overlap=False)
     del train_s
-    ms32 = max_over_ranks(ms32, world)
-    rays_total = sum_over_ranks(float(args.steps * args.batch), world)
-    value = rays_total / (ms32 / 1e3)
+    value, ms32 = whole_job_rate(float(args.steps * args.batch), ms32, world)
     out = {
         "metric": METRIC, "value": value, "unit": "rays/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms32 / args.steps, "higher_is_better": True,
@@ -356,7 +361,7 @@ def extras(args, wl, dev_batches, cams_t, gt_grid, opts, timed_loop, st32, ms32)
 
     # ---- BF16-SH form of the same step
     train16 = Grid.from_host(R, wl["train"].idx, wl["train"].rows, sh_form=1)
-    ms16, st16, clocks16, _ = timed_loop(train16, args.steps, args.warmup)
+    ms16, st16, clocks16, _ = timed_loop(train16, args.steps, args.warmup, ranks=1)
     res["bf16_sh"] = {"value": args.steps * args.batch / (ms16 / 1e3), "unit": "rays/s",
                       "ms_per_step": ms16 / args.steps, "speedup_vs_f32": ms32 / ms16, "stage_ms": st16,
                       "clocks": clocks16}
