@@ -11,9 +11,10 @@ Every step is Trainer.step (ray generation, training march, MSE gradient, adjoin
 1% of the nodes in contiguous segments, sparse RMSProp); the weights are plx_max_weight, prune
 and upsample are plx_grid_prune_* / plx_grid_upsample_*.
 
-The training images are the ground-truth grid rendered by plx_render for every training view and
-held in host memory; each step's 5000 pixels are drawn on the host with a seeded generator, their
-target colours gathered there, and both copied to the device (the role a data loader plays).
+The training images are the ground-truth grid rendered by plx_render for every training view, copied
+once to the device; each step's 5000 pixels are drawn on the host with a seeded generator, 256 steps
+at a time, and uploaded in one copy, and their target colours are gathered from the device images
+(the role a data loader plays).
 The paper does not give the steps at which it upsamples for a 128^3 start; `upsample_at` defaults to
 thirds of the run.  `paper_synthetic()` is the paper's own synthetic schedule (Supp. B.2).
 """
@@ -89,11 +90,12 @@ def psnr(a: np.ndarray, b: np.ndarray) -> float:
 
 
 class _Batches:
-    """Pixel ids, targets and TV segments for `chunk` steps at a time, each uploaded in one copy from
-    pinned memory, so that a step issues no host-to-device copy of its own."""
+    """Pixel ids and TV segments for `chunk` steps at a time, each uploaded in one copy from pinned
+    memory, and the steps' target colours gathered from the images on the device, so that a step issues
+    no host-to-device copy of its own."""
 
     def __init__(self, images: np.ndarray, cfg: C2FConfig, device):
-        self.flat = images.reshape(-1, 3)
+        self.flat = torch.from_numpy(np.ascontiguousarray(images.reshape(-1, 3), np.float32)).to(device)
         self.n_pix = self.flat.shape[0]
         self.cfg = cfg
         self.dev = device
@@ -115,7 +117,8 @@ class _Batches:
             ss = np.stack([a for a, _ in segs])  # every step has the same number of segments
             sl = np.stack([b for _, b in segs])
             up = lambda a: torch.from_numpy(a).pin_memory().to(self.dev, non_blocking=True)
-            self.pix, self.tgt, self.ss, self.sl = up(pix), up(self.flat[pix]), up(ss), up(sl)
+            self.pix, self.ss, self.sl = up(pix), up(ss), up(sl)
+            self.tgt = self.flat.index_select(0, self.pix.view(-1)).view(c.chunk, c.batch, 3)
         k = step - self.step0
         return self.pix[k], self.tgt[k], self.ss[k], self.sl[k], self.n_sel[k]
 
