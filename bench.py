@@ -286,9 +286,12 @@ def run_ours(args, world, rank, local):
         # ranks: the replicas that time this loop together (1 for rank 0's extras, which the others skip)
         tr = Trainer(grid, cams_t, W, H, StepConfig(batch=args.batch, opts=opts, overlap=overlap))
         nb = len(dev_batches)
+        # every step but the last of each loop plans the next batch beside its march (Trainer.step's
+        # next_pix); so the timed region holds exactly K plans
         for s in range(Wm):
             b = dev_batches[s % nb]
-            tr.step(b[0], b[1], b[2], b[3], b[4], lr_sigma(s), lr_sh(s))
+            tr.step(b[0], b[1], b[2], b[3], b[4], lr_sigma(s), lr_sh(s),
+                    next_pix=dev_batches[(s + 1) % nb][0] if s + 1 < Wm else None)
         tr.finish()
         torch.cuda.synchronize()
         evs = [[torch.cuda.Event(enable_timing=True) for _ in range(8)] for _ in range(K)] if per_stage else None
@@ -301,7 +304,8 @@ def run_ours(args, world, rank, local):
         for s in range(K):
             b = dev_batches[(Wm + s) % nb]
             tr.step(b[0], b[1], b[2], b[3], b[4], lr_sigma(Wm + s), lr_sh(Wm + s),
-                    events=evs[s] if per_stage else None)
+                    events=evs[s] if per_stage else None,
+                    next_pix=dev_batches[(Wm + s + 1) % nb][0] if s + 1 < K else None)
         tr.finish()  # the last step's update is inside the timed region
         stop.record(stream)
         torch.cuda.synchronize()
@@ -348,12 +352,12 @@ def run_ours(args, world, rank, local):
     torch.cuda.empty_cache()
 
     if rank == 0 and not args.no_extras:
-        out.update(extras(args, wl, dev_batches, cams_t, gt_grid, opts, timed_loop, st32, ms32))
+        out.update(extras(args, wl, dev_batches, cams_t, gt_grid, opts, timed_loop, st32, ms32, st_overlap))
     if rank == 0:
         print(json.dumps(out), flush=True)
 
 
-def extras(args, wl, dev_batches, cams_t, gt_grid, opts, timed_loop, st32, ms32):
+def extras(args, wl, dev_batches, cams_t, gt_grid, opts, timed_loop, st32, ms32, st_overlap):
     import torch
 
     import synth
@@ -433,13 +437,19 @@ def extras(args, wl, dev_batches, cams_t, gt_grid, opts, timed_loop, st32, ms32)
     launches = {"render": "march_chunks_fwd + march_combine (with the MSE gradient)",
                 "render_backward": "march_chunks_bwd",
                 "rmsprop_step": "rms_compact + rms_apply", "tv_grad": "tv_kernel"}
-    dom = max(per_launch, key=lambda k: st32[k])
+    # the dominant kernel: the largest share of the timed (overlapped) step's critical path, from its stage
+    # events (the update, forward and adjoint run in sequence on the march stream; TV runs beside them and
+    # shows only as the wait for it); its bandwidth from its time alone in the serial run
+    on_path = {"rmsprop_step": st_overlap["prev_update"], "render": st_overlap["render"],
+               "render_backward": st_overlap["render_backward"], "tv_grad": st_overlap["tv_wait"]}
+    dom = max(on_path, key=on_path.get)
     ach = per_launch[dom] / (st32[dom] / 1e3) / 1e9
     traffic, traffic_note = profiled_traffic(dom, args.workload)
     res["roofline"] = {"kernel": f"{dom} ({launches[dom]})", "bound": "hbm", "achieved": ach, "peak": peak,
                        "unit": "GB/s", "frac": ach / peak,
                        "peak_source": f"{peak_kind} hbm_gbs (STREAM-style copy), burst",
                        "timing": "CUDA events around the stage on the launching stream, serial run",
+                       "selection": "largest stage on the overlapped step's critical path (stage_ms.overlapped)",
                        "algorithmic_bytes_per_launch": per_launch[dom], "traffic": traffic,
                        "traffic_source": traffic_note, "library_digest": library_digest()}
     res["algorithmic"] = {"distinct_nodes_per_ray": nodes / n, "occupied_nodes_per_ray": occ / n,
@@ -449,45 +459,64 @@ def extras(args, wl, dev_batches, cams_t, gt_grid, opts, timed_loop, st32, ms32)
                           "GBps": {k: per_launch[k] / (st32[k] / 1e3) / 1e9 for k in per_launch},
                           "frac_of_peak": {k: per_launch[k] / (st32[k] / 1e3) / 1e9 / peak for k in per_launch}}
 
-    # ---- end to end through the public API with host buffers (pinned), copies inside the timed region
+    # ---- end to end through the public API with host buffers (pinned), copies inside the timed region.
+    # Each batch's inputs (pixel ids, targets, TV segment starts and lengths) sit in one pinned host buffer
+    # and go to the device in one copy, one step ahead (two device buffers), so that the next batch is
+    # planned beside this step's march (Trainer.step's next_pix); the first step of a loop also copies its
+    # own.  Each step reads its loss back to pinned host memory.
     tr = Trainer(train32, cams_t, W, H, StepConfig(batch=args.batch, opts=opts))
+    n = args.batch
+    max_seg = max(ss.shape[0] for _, ss, _ in wl["batches"])
+    nbytes = n * 8 + n * 12 + 2 * max_seg * 8
     host = []
-    for pix, ss, sl in wl["batches"]:
-        host.append((torch.from_numpy(pix).pin_memory(),
-                     None, torch.from_numpy(ss).pin_memory(), torch.from_numpy(sl).pin_memory(), int(sl.sum())))
-    host = [(h[0], dev_batches[i][1].cpu().pin_memory(), h[2], h[3], h[4]) for i, h in enumerate(host)]
-    d_pix = torch.empty(args.batch, dtype=torch.int64, device=dev)
-    d_tgt = torch.empty((args.batch, 3), dtype=torch.float32, device=dev)
-    max_seg = max(h[2].shape[0] for h in host)
-    d_ss = torch.empty(max_seg, dtype=torch.int64, device=dev)
-    d_sl = torch.empty(max_seg, dtype=torch.int64, device=dev)
+    for i, (pix, ss, sl) in enumerate(wl["batches"]):
+        buf = torch.zeros(nbytes, dtype=torch.uint8).pin_memory()
+        # int64 parts first (8-byte aligned views), then the FP32 targets
+        parts = [torch.from_numpy(pix).view(torch.uint8),
+                 torch.from_numpy(np.pad(ss, (0, max_seg - ss.shape[0]))).view(torch.uint8),
+                 torch.from_numpy(np.pad(sl, (0, max_seg - sl.shape[0]))).view(torch.uint8),
+                 dev_batches[i][1].cpu().view(torch.uint8).reshape(-1)]
+        torch.cat(parts, out=buf)
+        host.append((buf, ss.shape[0], int(sl.sum())))
+    d_buf = [torch.empty(nbytes, dtype=torch.uint8, device=dev) for _ in range(2)]
+
+    def views(buf, ns):
+        o_ss, o_sl, o_tgt = n * 8, n * 8 + max_seg * 8, n * 8 + 2 * max_seg * 8
+        pix = buf[:o_ss].view(torch.int64)
+        ss = buf[o_ss:o_sl].view(torch.int64)[:ns]
+        sl = buf[o_sl:o_tgt].view(torch.int64)[:ns]
+        tgt = buf[o_tgt:].view(torch.float32).view(n, 3)
+        return pix, tgt, ss, sl
+
+    dv = [views(b, max_seg) for b in d_buf]
     loss_host = torch.empty(1, dtype=torch.float32).pin_memory()
     stream = torch.cuda.current_stream()
 
-    def e2e_step(s):
+    def e2e_step(s, first, last):
         h = host[s % nb]
-        ns = h[2].shape[0]
-        d_pix.copy_(h[0], non_blocking=True)
-        d_tgt.copy_(h[1], non_blocking=True)
-        d_ss[:ns].copy_(h[2], non_blocking=True)
-        d_sl[:ns].copy_(h[3], non_blocking=True)
+        cur, nxt = s % 2, (s + 1) % 2
+        if first:
+            d_buf[cur].copy_(h[0], non_blocking=True)
+        if not last:
+            d_buf[nxt].copy_(host[(s + 1) % nb][0], non_blocking=True)
+        pix, tgt, ss, sl = dv[cur]
         tr.loss.zero_()
-        tr.step(d_pix, d_tgt, d_ss[:ns], d_sl[:ns], h[4], lr_sigma(s), lr_sh(s))
+        tr.step(pix, tgt, ss[: h[1]], sl[: h[1]], h[2], lr_sigma(s), lr_sh(s), next_pix=None if last else dv[nxt][0])
         loss_host.copy_(tr.loss, non_blocking=True)
 
     for s in range(args.warmup):
-        e2e_step(s)
+        e2e_step(s, s == 0, s == args.warmup - 1)
     tr.finish()
     torch.cuda.synchronize()
     a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     a.record(stream)
     for s in range(K):
-        e2e_step(Wm + s)
+        e2e_step(Wm + s, s == 0, s == K - 1)
     tr.finish()
     b.record(stream)
     torch.cuda.synchronize()
     ms_e2e = a.elapsed_time(b)
-    h2d = args.batch * (8 + 12) + int(np.mean([h[2].shape[0] for h in host])) * 16
+    h2d = nbytes
     res["e2e"] = {"value": K * args.batch / (ms_e2e / 1e3), "unit": "rays/s", "h2d_bytes_per_step": h2d,
                   "d2h_bytes_per_step": 4, "ms_per_step": ms_e2e / K}
     del tr, train32
@@ -641,7 +670,8 @@ def large_batch(args, wl, cams_t, gt_grid, opts, n=1 << 18, steps=8, warmup=3):
     tr = Trainer(g, cams_t, W, H, StepConfig(batch=n, opts=opts))
     for s in range(warmup):
         b = batches[s % 4]
-        tr.step(b[0], b[1], b[2], b[3], b[4], lr_sigma(s), lr_sh(s))
+        tr.step(b[0], b[1], b[2], b[3], b[4], lr_sigma(s), lr_sh(s),
+                next_pix=batches[(s + 1) % 4][0] if s + 1 < warmup else None)
     tr.finish()
     stream = torch.cuda.current_stream()
     a, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -649,7 +679,8 @@ def large_batch(args, wl, cams_t, gt_grid, opts, n=1 << 18, steps=8, warmup=3):
     a.record(stream)
     for s in range(steps):
         b = batches[s % 4]
-        tr.step(b[0], b[1], b[2], b[3], b[4], lr_sigma(warmup + s), lr_sh(warmup + s))
+        tr.step(b[0], b[1], b[2], b[3], b[4], lr_sigma(warmup + s), lr_sh(warmup + s),
+                next_pix=batches[(s + 1) % 4][0] if s + 1 < steps else None)
     tr.finish()
     e.record(stream)
     torch.cuda.synchronize()

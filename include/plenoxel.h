@@ -22,10 +22,10 @@
  *   a code in the grid's device status word, skip the access and go on;
  *   plx_check() reports it.  No kernel traps or waits on another kernel.
  *
- * Grid layout (Sec. 3.2; Supp. B.1 "Implementation Details")
+ * Grid layout (Sec. 3.2; Supp. B.1)
  * ---------------------------------------------------------
- * - The grid is a dense R x R x R lattice of nodes ("each occupied voxel
- *   corner stores ...", Sec. 3).  Node (i,j,k) has linear id
+ * - The grid is a dense R x R x R lattice of nodes, the voxel corners that
+ *   hold the values (Sec. 3).  Node (i,j,k) has linear id
  *   n = (i*R + j)*R + k (k fastest, i along x) and sits at world position
  *   aabb_min + (i,j,k) * h, h = (aabb_max - aabb_min) / (R - 1).
  * - d_idx: int32 [R^3]; -1 marks an empty (NULL) node, otherwise the row of
@@ -423,6 +423,80 @@ plx_status plx_grid_upsample_apply(const plx_grid *grid, int32_t new_reso, const
  *   - all calls share the array, which keeps the last call's contents; calls
  *     whose work overlaps on the GPU (other streams or host threads on the same
  *     device) race on it and must be serialised by the caller. */
+/* ---------------------------------------------------------------- optimisation step
+ *
+ * One step of the optimisation (Sec. 3.5; Supp. B.1) in one call: rays for
+ * the batch's pixels (plx_gen_rays), plan and forward with the MSE gradient
+ * (plx_march_plan, plx_render_planned_mse), adjoint with the Cauchy prior
+ * when lambda_sparsity > 0 (plx_render_backward_train), TV on the given
+ * segments (plx_tv_grad) and RMSProp (plx_rmsprop_step), ordered on three
+ * streams the trainer owns (the march and the plan at the device's highest
+ * priority, TV at its lowest).  Each step's RMSProp update is deferred to the
+ * start of the next call (or to plx_trainer_finish), beside that batch's
+ * plan; TV runs beside the forward and adjoint.  The result equals the serial
+ * order of those calls up to the order of FP32 atomic additions.
+ *
+ * Rays and march state are kept in two sets in a caller workspace; passing
+ * the next call's pixel array as d_next_pix has that batch generated and
+ * planned during this step's march.  The next call uses that plan when it
+ * passes the same d_pix pointer and n with pix_is_ahead = 1, which asserts
+ * that the pixel ids there have not changed since; otherwise it plans again.
+ *
+ * Ordering with the caller's stream: the step starts after the work already
+ * enqueued on `stream` and `stream` waits for the step's end (colours, loss,
+ * gradient complete) and for the plan of d_next_pix (which has then read the
+ * pixel ids).  The deferred update is not included: call plx_trainer_finish
+ * before reading rows or v.  On an error the trainer must be destroyed. */
+typedef struct plx_trainer plx_trainer;
+typedef struct {
+    int32_t batch;            /* most rays in one step */
+    plx_render_opts opts;     /* stop_thresh > 0 makes the march recompute the adjoint's samples */
+    float lambda_tv_sigma;    /* TV weights (Sec. 3.5) */
+    float lambda_tv_sh;
+    float lambda_sparsity;    /* Cauchy prior weight (Sec. 3.7, Eq. 4); 0: none */
+    float beta;               /* RMSProp (Sec. 3.5) */
+    float eps;
+    int32_t sparse_rmsprop;   /* 1: update only rows marked touched (plx_rmsprop_step) */
+} plx_trainer_desc;
+
+/* Device workspace of a trainer for this grid and descriptor (0 for
+ * invalid arguments): two sets of rays and march state, colours and dL/dC. */
+size_t plx_trainer_workspace_bytes(const plx_grid *grid, const plx_trainer_desc *desc);
+
+/* d_cams: float [n_cams][18] cameras (plx_gen_rays), images W x H; pixel ids
+ * are view*H*W + v*W + u.  d_grad_rows, d_v: F32 [n_rows][32] gradient
+ * (zero) and RMSProp state, caller-owned, used by every step.  d_workspace:
+ * 256-byte aligned, at least plx_trainer_workspace_bytes bytes. */
+plx_status plx_trainer_create(plx_grid *grid, const plx_trainer_desc *desc, const float *d_cams, int32_t n_cams,
+                              int32_t W, int32_t H, float *d_grad_rows, float *d_v, void *d_workspace,
+                              size_t workspace_bytes, plx_trainer **out);
+plx_status plx_trainer_destroy(plx_trainer *trainer);
+
+/* One step on n (<= batch) pixels d_pix int64 [n] with targets d_target
+ * float [n][3]; TV on n_seg segments (d_seg_start/d_seg_len int64, n_selected
+ * nodes in all; NULL or 0 for none); lr_sigma/lr_sh for this step's update.
+ * d_loss (float [1], nullable) accumulates the MSE; d_loss_sparsity (nullable)
+ * the Cauchy prior; d_touched (int64 [1], nullable) receives the number of
+ * rows with a gradient this step (plx_count_touched, before the update).
+ * events: NULL, or 8 CUDA events recorded on the march stream around the
+ * stages (update, plan wait, forward, adjoint, TV wait), for timing.
+ * set_out (host, nullable) receives the set of rays and state the step used
+ * (see plx_trainer_buffers). */
+plx_status plx_trainer_step(plx_trainer *trainer, const int64_t *d_pix, int64_t n, const float *d_target,
+                            const int64_t *d_seg_start, const int64_t *d_seg_len, int64_t n_seg, int64_t n_selected,
+                            float lr_sigma, float lr_sh, const int64_t *d_next_pix, int32_t pix_is_ahead,
+                            float *d_loss, float *d_loss_sparsity, int64_t *d_touched, void *const *events,
+                            int32_t *set_out, void *stream);
+
+/* Applies the pending update on `stream`. */
+plx_status plx_trainer_finish(plx_trainer *trainer, void *stream);
+
+/* Device buffers of set 0 or 1: rays float [batch][3], the colours of the
+ * last step float [batch][3], the march state and its size (any output may
+ * be NULL). */
+plx_status plx_trainer_buffers(const plx_trainer *trainer, int32_t set, float **d_origins, float **d_dirs,
+                               float **d_rgb, void **d_state, size_t *state_bytes);
+
 #define PLX_PRUNE_NOALLOC_MAX_RESO 256
 #define PLX_PRUNE_NOALLOC_SCRATCH_BYTES 4325632 /* the prune workspace of a 256^3 grid */
 plx_status plx_grid_prune_noalloc(const plx_grid *grid, float tau, int32_t dilate, int32_t *d_idx_new,

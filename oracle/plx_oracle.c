@@ -12,7 +12,7 @@
  * eye: one loop per definition, FP64 arithmetic, no blocking, no skipping of
  * empty space, no early exits other than the ones the definition states.
  *
- * Grid semantics (Sec. 3.2; Supp. B.1 "Implementation Details"):
+ * Grid semantics (Sec. 3.2; Supp. B.1):
  *   - a dense int32 index volume idx[R*R*R]; idx[n] == -1 is a NULL cell,
  *     otherwise it is the row of that node in the data table;
  *   - node (i,j,k) has linear id n = (i*R + j)*R + k (k fastest, i <-> x);

@@ -36,6 +36,11 @@ class plx_render_opts(ctypes.Structure):
     _fields_ = [("step_vox", c_float), ("bg", c_float * 3), ("stop_thresh", c_float)]
 
 
+class plx_trainer_desc(ctypes.Structure):
+    _fields_ = [("batch", c_int32), ("opts", plx_render_opts), ("lambda_tv_sigma", c_float), ("lambda_tv_sh", c_float),
+                ("lambda_sparsity", c_float), ("beta", c_float), ("eps", c_float), ("sparse_rmsprop", c_int32)]
+
+
 # name -> (restype, argtypes); every name here is declared in include/plenoxel.h
 SIGNATURES = {
     "plx_status_str": (ctypes.c_char_p, [c_int32]),
@@ -69,6 +74,16 @@ SIGNATURES = {
     "plx_count_nodes": (c_int32, [c_void_p, c_void_p, c_void_p, c_int64, ctypes.POINTER(plx_render_opts), c_void_p,
                                   c_void_p]),
     "plx_count_touched": (c_int32, [c_void_p, c_void_p, c_void_p]),
+    "plx_trainer_workspace_bytes": (c_size_t, [c_void_p, ctypes.POINTER(plx_trainer_desc)]),
+    "plx_trainer_create": (c_int32, [c_void_p, ctypes.POINTER(plx_trainer_desc), c_void_p, c_int32, c_int32, c_int32,
+                                     c_void_p, c_void_p, c_void_p, c_size_t, ctypes.POINTER(c_void_p)]),
+    "plx_trainer_destroy": (c_int32, [c_void_p]),
+    "plx_trainer_step": (c_int32, [c_void_p, c_void_p, c_int64, c_void_p, c_void_p, c_void_p, c_int64, c_int64, c_float,
+                                   c_float, c_void_p, c_int32, c_void_p, c_void_p, c_void_p, c_void_p,
+                                   ctypes.POINTER(c_int32), c_void_p]),
+    "plx_trainer_finish": (c_int32, [c_void_p, c_void_p]),
+    "plx_trainer_buffers": (c_int32, [c_void_p, c_int32, ctypes.POINTER(c_void_p), ctypes.POINTER(c_void_p),
+                                      ctypes.POINTER(c_void_p), ctypes.POINTER(c_void_p), ctypes.POINTER(c_size_t)]),
     "plx_max_weight": (c_int32, [c_void_p, c_void_p, c_void_p, c_int64, ctypes.POINTER(plx_render_opts), c_void_p,
                                  c_void_p]),
     "plx_mse_grad": (c_int32, [c_void_p, c_void_p, c_int64, c_void_p, c_void_p, c_void_p]),

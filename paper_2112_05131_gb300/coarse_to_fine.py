@@ -163,7 +163,11 @@ def train(train_images: np.ndarray, cams: torch.Tensor, W: int, H: int, cfg: C2F
         pix, tgt, ss, sl, nsel = batches.get(step, grid.reso)
         if cfg.tv_until is not None and step >= cfg.tv_until:
             ss = sl = None
-        tr.step(pix, tgt, ss, sl, nsel, lr_sigma(step), lr_sh(step))
+        # the next batch is planned during this step, unless a prune and upsample come first
+        nxt = None
+        if step + 1 < cfg.steps and not (ups and step + 1 == ups[0]):
+            nxt = batches.get(step + 1, grid.reso)[0]
+        tr.step(pix, tgt, ss, sl, nsel, lr_sigma(step), lr_sh(step), next_pix=nxt)
     tr.finish()
     torch.cuda.synchronize()
     grid.check()

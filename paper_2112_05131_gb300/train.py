@@ -7,20 +7,23 @@ One step (Supp. B.1: 5000-ray batches, RMSProp, stochastic TV on contiguous segm
 all libplenoxel calls with no host synchronisation.  The training march splits rays into chunk work
 items and hands the march state from the forward to the adjoint.
 
-With overlap (the default) the calls use three streams and RMSProp is deferred to the start of the next
-step (or to finish()): ray generation and the plan read no rows, so the next batch's are computed while
-the previous update runs; TV reads rows only and adds to the gradient with atomics, so it runs beside
-the forward and adjoint.  Every step computes exactly what the serial order computes.
+With overlap (the default) a step is one native call, plx_trainer_step, which orders the same calls on
+three streams and defers RMSProp to the start of the next step (or to finish()): ray generation and
+the plan read no rows, so they run beside the previous update, or during the previous step when its
+call was given this batch as `next_pix`; TV reads rows only and adds to the gradient with atomics, so it
+runs beside the forward and adjoint.  Every step computes what the serial order computes.
 """
 from __future__ import annotations
 
+import ctypes
 import math
 from dataclasses import dataclass, field
 from typing import List, Optional
 
 import torch
 
-from .grid import ROW, Grid, RenderOpts, gen_rays
+from . import _lib as L
+from .grid import ROW, Grid, RenderOpts, _need, _p, _stream, gen_rays
 
 # kernels one step enqueues with stop_thresh = 0: gen_rays, march_plan (header, setup, plan),
 # render_planned_mse (chunks, combine with the MSE gradient), backward_train, tv, rmsprop (compact, apply)
@@ -68,7 +71,11 @@ class StepConfig:
 
 
 class Trainer:
-    """Holds the optimiser state (gradient rows, RMSProp running average) and the step's scratch buffers."""
+    """Holds the optimiser state (gradient rows, RMSProp running average) and the step's scratch buffers.
+
+    Overlap mode (the default) is one native call per step, plx_trainer_step (three streams, deferred
+    update, the next batch planned ahead: see include/plenoxel.h); serial mode issues the same library
+    calls from here, in order, on one stream."""
 
     def __init__(self, grid: Grid, cams: torch.Tensor, W: int, H: int, cfg: StepConfig = StepConfig()):
         dev = grid.idx.device
@@ -79,38 +86,66 @@ class Trainer:
         self.grad = torch.zeros((grid.M, ROW), dtype=torch.float32, device=dev)
         self.v = torch.zeros((grid.M, ROW), dtype=torch.float32, device=dev)
         n = cfg.batch
-        self.o = torch.empty((n, 3), dtype=torch.float32, device=dev)
-        self.d = torch.empty((n, 3), dtype=torch.float32, device=dev)
-        self.rgb = torch.empty((n, 3), dtype=torch.float32, device=dev)
-        self.grad_rgb = torch.empty((n, 3), dtype=torch.float32, device=dev)
         self.loss = torch.zeros(1, dtype=torch.float32, device=dev)
         self.loss_sparsity = torch.zeros(1, dtype=torch.float32, device=dev)
-        self.state = grid.new_march_state(n, cfg.opts)  # fits every batch of up to n rays
-        if cfg.overlap:
-            # the march (update, forward, MSE, adjoint) and the plan on high-priority streams, TV on a
-            # low-priority one: when both have blocks waiting, the scheduler starts the march's first
-            # and TV fills what is left
-            self.march_stream = torch.cuda.Stream(device=dev, priority=-1)
-            self.plan_stream = torch.cuda.Stream(device=dev, priority=-1)
-            self.tv_stream = torch.cuda.Stream(device=dev, priority=0)
-        self._ev = {k: torch.cuda.Event() for k in ("start", "plan", "rms", "tv", "bwd", "end")}
-        self._bwd_recorded = False
-        self.pending = None  # (lr_sigma, lr_sh) of an update not yet applied
         self._touched = torch.zeros(1 << 16 if cfg.track_touched else 0, dtype=torch.int64, device=dev)
         self._n_touched = 0
+        self._native = None
+        if cfg.overlap:
+            _need(cams, torch.float32, "cams")
+            desc = L.plx_trainer_desc()
+            desc.batch = n
+            desc.opts = cfg.opts.c()
+            desc.lambda_tv_sigma, desc.lambda_tv_sh = float(cfg.lambda_tv_sigma), float(cfg.lambda_tv_sh)
+            desc.lambda_sparsity = float(cfg.lambda_sparsity)
+            desc.beta, desc.eps = float(cfg.beta), float(cfg.eps)
+            desc.sparse_rmsprop = 1 if cfg.sparse_rmsprop else 0
+            nbytes = int(L.load().plx_trainer_workspace_bytes(grid.handle, ctypes.byref(desc)))
+            if nbytes == 0:
+                raise ValueError("no trainer workspace for this grid and batch")
+            self._ws = torch.empty(nbytes, dtype=torch.uint8, device=dev)
+            handle = ctypes.c_void_p()
+            L.call("plx_trainer_create", grid.handle, ctypes.byref(desc), _p(cams), cams.shape[0], self.W, self.H,
+                   _p(self.grad), _p(self.v), _p(self._ws), nbytes, ctypes.byref(handle))
+            self._native = handle
+            # views of the two sets of rays and march state inside the workspace
+            self._o, self._d, self._state = [], [], []
+            base = self._ws.data_ptr()
+            for k in range(2):
+                po, pd, prgb, pst = (ctypes.c_void_p() for _ in range(4))
+                sb = ctypes.c_size_t()
+                L.call("plx_trainer_buffers", handle, k, ctypes.byref(po), ctypes.byref(pd), ctypes.byref(prgb),
+                       ctypes.byref(pst), ctypes.byref(sb))
+                view = lambda ptr, size: self._ws[ptr.value - base: ptr.value - base + size]
+                self._o.append(view(po, 12 * n).view(torch.float32).view(n, 3))
+                self._d.append(view(pd, 12 * n).view(torch.float32).view(n, 3))
+                self._state.append(view(pst, sb.value))
+                self.rgb = view(prgb, 12 * n).view(torch.float32).view(n, 3)
+            self._ahead = None  # (key, tensor) of the batch planned ahead
+        else:
+            self._o = [torch.empty((n, 3), dtype=torch.float32, device=dev)]
+            self._d = [torch.empty((n, 3), dtype=torch.float32, device=dev)]
+            self._state = [grid.new_march_state(n, cfg.opts)]  # fits every batch of up to n rays
+            self.rgb = torch.empty((n, 3), dtype=torch.float32, device=dev)
+            self.grad_rgb = torch.empty((n, 3), dtype=torch.float32, device=dev)
+        self.o, self.d, self.state = self._o[0], self._d[0], self._state[0]
 
-    def _count_touched(self, stream):
-        """Appends this step's touched-row count (before the update clears the mask) to the log."""
+    def __del__(self):
+        if getattr(self, "_native", None) is not None:
+            L.load().plx_trainer_destroy(self._native)
+            self._native = None
+
+    def _touched_slot(self, stream) -> Optional[torch.Tensor]:
+        """The log entry for this step's touched-row count (plx_count_touched), growing the log on `stream`."""
         if not self.cfg.track_touched:
-            return
-        if self._n_touched == self._touched.numel():  # grow the log; ordered on `stream` like its writes
+            return None
+        if self._n_touched == self._touched.numel():
             with torch.cuda.stream(stream):
                 grown = torch.zeros(2 * self._touched.numel(), dtype=torch.int64, device=self._touched.device)
                 grown[: self._n_touched].copy_(self._touched)
-            self._touched.record_stream(stream)  # its memory is not reused before `stream` is past the copy
             self._touched = grown
-        self.grid.count_touched(self._touched[self._n_touched:self._n_touched + 1], stream=stream)
         self._n_touched += 1
+        return self._touched[self._n_touched - 1:self._n_touched]
 
     def touched_counts(self):
         """Rows that received a gradient in each recorded step (host int64 array; synchronises)."""
@@ -123,95 +158,86 @@ class Trainer:
 
     def finish(self, stream=None):
         """Applies the pending RMSProp update (overlap mode defers each step's update to the next call)."""
-        if self.pending is not None:
-            main = stream if stream is not None else torch.cuda.current_stream()
-            self._update(main, self.pending)
-            self.pending = None
+        if self._native is not None:
+            L.call("plx_trainer_finish", self._native, _stream(stream))
+
+    @staticmethod
+    def _key(pix: torch.Tensor):
+        # identifies a pixel batch and its contents: views of the same memory compare equal, and an
+        # in-place change through any of them bumps the shared version (the planned-ahead tensor is kept
+        # referenced, so its memory cannot be reused by another tensor meanwhile)
+        return (pix.data_ptr(), tuple(pix.shape), tuple(pix.stride()), pix._version)
 
     def step(self, pix: torch.Tensor, target: torch.Tensor, seg_start: Optional[torch.Tensor],
              seg_len: Optional[torch.Tensor], n_selected: int, lr_s: float, lr_h: float,
-             events: Optional[List[torch.cuda.Event]] = None, stream=None):
-        """One optimisation step.  `events`, if given, holds 8 events recorded on the main stream; the 7
-        intervals between them are the stages named in STAGES (serial mode: rays and plan, -, forward with
-        the MSE gradient, -, adjoint, TV, update; overlap mode: the previous step's update, the wait for this
-        step's plan, forward with the MSE gradient, -, adjoint, the wait for TV, -).  In overlap mode call finish() after the last step."""
+             events: Optional[List[torch.cuda.Event]] = None, stream=None, next_pix: Optional[torch.Tensor] = None):
+        """One optimisation step.  `events`, if given, holds 8 events recorded on the march (serial mode:
+        the only) stream; the 7 intervals between them are the stages named in STAGES (serial mode: rays and
+        plan, -, forward with the MSE gradient, -, adjoint, TV, update; overlap mode: the previous step's
+        update, the wait for this step's plan, forward with the MSE gradient, -, adjoint, the wait for TV,
+        -).  In overlap mode call finish() after the last step.
+
+        `next_pix` (overlap mode): the pixel batch of the next call, whose rays and plan are then computed
+        during this step, beside its march, and used by the next call if it passes the same, unchanged
+        tensor as `pix` (otherwise they are computed again)."""
         g, c = self.grid, self.cfg
         n = pix.shape[0]
-        o, d, rgb, grgb = self.o[:n], self.d[:n], self.rgb[:n], self.grad_rgb[:n]
         main = stream if stream is not None else torch.cuda.current_stream()
         do_tv = seg_start is not None and n_selected > 0
-        ev = self._ev
+
+        if self._native is not None:
+            _need(pix, torch.int64, "pix", (n,))
+            _need(target, torch.float32, "target", (n, 3))
+            if next_pix is not None:
+                _need(next_pix, torch.int64, "next_pix", (n,))
+            if do_tv:
+                _need(seg_start, torch.int64, "seg_start")
+                _need(seg_len, torch.int64, "seg_len", tuple(seg_start.shape))
+            ahead = self._ahead is not None and self._ahead[0] == self._key(pix)
+            ev = None
+            if events is not None:
+                for e in events:  # the native call records them; each must exist first
+                    if not e.cuda_event:
+                        e.record(main)
+                ev = ctypes.cast((ctypes.c_void_p * 8)(*[e.cuda_event for e in events]), ctypes.c_void_p)
+            touched = self._touched_slot(main)
+            used = ctypes.c_int32()
+            L.call("plx_trainer_step", self._native, _p(pix), n, _p(target),
+                   _p(seg_start) if do_tv else None, _p(seg_len) if do_tv else None,
+                   seg_start.shape[0] if do_tv else 0, int(n_selected) if do_tv else 0, float(lr_s), float(lr_h),
+                   _p(next_pix), 1 if ahead else 0, _p(self.loss),
+                   _p(self.loss_sparsity) if c.lambda_sparsity > 0 else None, _p(touched), ev, ctypes.byref(used),
+                   _stream(main))
+            self._ahead = (self._key(next_pix), next_pix) if next_pix is not None else None
+            k = used.value
+            self.o, self.d, self.state = self._o[k], self._d[k], self._state[k]
+            return self.rgb[:n]
+
+        o, d, rgb, grgb = self.o[:n], self.d[:n], self.rgb[:n], self.grad_rgb[:n]
 
         def mark(i):
             if events is not None:
                 events[i].record(main)
 
-        if not c.overlap:
-            mark(0)
-            gen_rays(self.cams, pix, self.W, self.H, o, d, stream=main)
-            g.march_plan(o, d, c.opts, self.state, stream=main)
-            mark(1)
-            mark(2)
-            g.render_planned_mse(o, d, c.opts, self.state, target, rgb, grgb, self.loss, stream=main)
-            mark(3)
-            mark(4)
-            g.render_backward_train(o, d, grgb, c.opts, self.state, self.grad, c.lambda_sparsity,
-                                    self.loss_sparsity if c.lambda_sparsity > 0 else None, stream=main)
-            mark(5)
-            if do_tv:
-                g.tv_grad(seg_start, seg_len, n_selected, c.lambda_tv_sigma, c.lambda_tv_sh, self.grad, stream=main)
-            self._count_touched(main)
-            mark(6)
-            self._update(main, (lr_s, lr_h))
-            mark(7)
-            return rgb
-
-        # the march stream starts after everything the caller enqueued (inputs, the loss reset)
-        caller = main
-        ms = self.march_stream
-        ev["start"].record(caller)
-        ms.wait_event(ev["start"])
-        main = ms  # the stage events follow the march stream
-        # rays and plan of this batch on the plan stream, once the last adjoint is done with rays and state
-        ps = self.plan_stream
-        ps.wait_event(ev["start"])
-        if self._bwd_recorded:
-            ps.wait_event(ev["bwd"])
-        gen_rays(self.cams, pix, self.W, self.H, o, d, stream=ps)
-        g.march_plan(o, d, c.opts, self.state, stream=ps)
-        ev["plan"].record(ps)
-        # the previous step's update, concurrently
         mark(0)
-        if self.pending is not None:
-            self._update(ms, self.pending)
-            self.pending = None
+        gen_rays(self.cams, pix, self.W, self.H, o, d, stream=main)
+        g.march_plan(o, d, c.opts, self.state, stream=main)
         mark(1)
-        # TV of this step after that update, beside the march
-        if do_tv:
-            ev["rms"].record(ms)
-            self.tv_stream.wait_event(ev["rms"])
-            g.tv_grad(seg_start, seg_len, n_selected, c.lambda_tv_sigma, c.lambda_tv_sh, self.grad,
-                      stream=self.tv_stream)
-            ev["tv"].record(self.tv_stream)
-        ms.wait_event(ev["plan"])
         mark(2)
-        g.render_planned_mse(o, d, c.opts, self.state, target, rgb, grgb, self.loss, stream=ms)
+        g.render_planned_mse(o, d, c.opts, self.state, target, rgb, grgb, self.loss, stream=main)
         mark(3)
         mark(4)
         g.render_backward_train(o, d, grgb, c.opts, self.state, self.grad, c.lambda_sparsity,
-                                self.loss_sparsity if c.lambda_sparsity > 0 else None, stream=ms)
-        ev["bwd"].record(ms)
-        self._bwd_recorded = True
+                                self.loss_sparsity if c.lambda_sparsity > 0 else None, stream=main)
         mark(5)
         if do_tv:
-            ms.wait_event(ev["tv"])
-        self._count_touched(ms)
-        self.pending = (lr_s, lr_h)
+            g.tv_grad(seg_start, seg_len, n_selected, c.lambda_tv_sigma, c.lambda_tv_sh, self.grad, stream=main)
+        touched = self._touched_slot(main)
+        if touched is not None:
+            g.count_touched(touched, stream=main)
         mark(6)
+        self._update(main, (lr_s, lr_h))
         mark(7)
-        # the caller's stream resumes after the step (colours, loss and gradient are then complete)
-        ev["end"].record(ms)
-        caller.wait_event(ev["end"])
         return rgb
 
     # the 7 intervals between step()'s 8 events: serial mode | overlap mode

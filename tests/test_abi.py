@@ -128,5 +128,18 @@ def test_host_validation_rejects_bad_arguments(lib):
     n = ctypes.c_int64()
     _einval(lib, lib.plx_grid_prune_count(null, 5.0, 1, null, ctypes.byref(n), null))
     _einval(lib, lib.plx_grid_upsample_count(null, 64, null, ctypes.byref(n), null))
+    # the trainer: no grid, no handle, bad descriptor
+    td = _lib.plx_trainer_desc()
+    td.batch, td.opts, td.beta, td.eps, td.sparse_rmsprop = 5000, opts, 0.95, 1e-8, 1
+    assert lib.plx_trainer_workspace_bytes(null, ctypes.byref(td)) == 0
+    tr = ctypes.c_void_p()
+    _einval(lib, lib.plx_trainer_create(null, ctypes.byref(td), null, 1, 8, 8, null, null, null, 0, ctypes.byref(tr)))
+    _einval(lib, lib.plx_trainer_create(null, ctypes.byref(td), null, 1, 8, 8, null, null, null, 0, null))
+    assert tr.value is None
+    used = ctypes.c_int32()
+    _einval(lib, lib.plx_trainer_step(null, null, 10, null, null, null, 0, 0, 1.0, 1.0, null, 0, null, null, null,
+                                      null, ctypes.byref(used), null))
+    _einval(lib, lib.plx_trainer_finish(null, null))
+    assert lib.plx_trainer_destroy(null) == 0
     _einval(lib, lib.plx_check(null, null))
     _einval(lib, lib.plx_grid_get_desc(null, null))

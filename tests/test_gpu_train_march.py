@@ -280,12 +280,15 @@ def test_overlapped_trainer_matches_serial(cuda_lib, form):
     tb = Trainer(gb, cams, 64, 64, StepConfig(overlap=False, **cfg))
     tb.step(*b, lr_sigma(1000), lr_sh(1000))
     # further steps: the losses of the two runs agree
+    # (the overlapped run plans each next batch during the step before it, except that the batch it is
+    # told comes after the second step is not the one the third step gets: then it plans again)
     losses = {}
+    nxt = [batches[2][0], batches[1][0], None]
     for t, key in ((ta, "a"), (tb, "b")):
         out = []
         for s, bb in enumerate(batches[1:]):
             t.loss.zero_()
-            t.step(*bb, lr_sigma(1001 + s), lr_sh(1001 + s))
+            t.step(*bb, lr_sigma(1001 + s), lr_sh(1001 + s), next_pix=nxt[s] if t is ta else None)
             out.append(t.loss.item())
         t.finish()
         losses[key] = out
