@@ -467,7 +467,9 @@ __device__ __forceinline__ float sparsity_prior(const RenderParams &p, bool take
 // receives wk (gsig, gpre_0 Y, gpre_1 Y, gpre_2 Y), so four numbers per corner and sample carry all of it.
 // Lanes are paired within each run of equal cells (positions 0-1, 2-3, ... of the run); the even lane
 // adds its partner's 32 numbers (8 corners x 4, by shuffles) and scatters both, the odd lane nothing,
-// which halves the atomics of such runs.  `cell`: the sample's cell base node (any value when !scat).
+// which halves the atomics of such runs; then pairs of the remaining lanes whose cells are one step
+// apart merge their 4 shared corners the same way.  `cell`: the sample's cell base node (any value when
+// !scat).
 __device__ __forceinline__ void scatter_chunk(const GridView &g, bool scat, int64_t cell, const int32_t rr[8],
                                               const float ff[3], const float Y[9], const float gr[3],
                                               const float pre[3], const float col[3], float w, float Tn,
@@ -511,6 +513,66 @@ __device__ __forceinline__ void scatter_chunk(const GridView &g, bool scat, int6
     }
     const unsigned wn = __shfl_down_sync(kFull, wmask, 1);
     if (absorb) wmask |= wn;
+    // Second level: the lanes left to scatter ("heads"), in lane order, are usually in cells one step
+    // apart along an axis, which share 4 corners.  Heads are paired by rank (0-1, 2-3, ...); when a pair's
+    // cells are one step apart, the even one adds the odd one's values for the 4 shared corners and the
+    // odd one leaves them out.  Corner k = 4 cx + 2 cy + cz; along axis a the shared corners differ in
+    // bit 4 >> a.
+    const bool head = scat && !odd;
+    const unsigned heads = __ballot_sync(kFull, head);
+    const unsigned above = lane == 31 ? 0u : heads & ~((2u << lane) - 1u);
+    const unsigned below = heads & ((1u << lane) - 1u);
+    const int next_head = above ? __ffs(above) - 1 : lane;
+    const int prev_head = below ? 31 - __clz(below) : lane;
+    const bool even_rank = (__popc(below) & 1) == 0;
+    // this head's partner: the next head (even rank) or the previous one (odd rank)
+    const int partner = even_rank ? next_head : prev_head;
+    const int64_t pcell = __shfl_sync(kFull, cell, partner);
+    int bit = 0;       // the axis bit of the shared corners, 0: the cells are not one step apart
+    bool up = false;   // the odd head's cell is the even head's plus one step
+    if (head && partner != lane) {
+        const int64_t R = g.R;
+        const int64_t dlt = even_rank ? pcell - cell : cell - pcell;  // odd head's cell minus even head's
+        const int64_t st = dlt < 0 ? -dlt : dlt;
+        bit = st == 1 ? 1 : st == R ? 2 : st == R * R ? 4 : 0;
+        up = dlt > 0;
+    }
+    float pa[8], pb[8][3];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+        pa[k] = __shfl_sync(kFull, a[k], next_head);
+#pragma unroll
+        for (int ch = 0; ch < 3; ++ch) pb[k][ch] = __shfl_sync(kFull, b[k][ch], next_head);
+    }
+    const unsigned pw = __shfl_sync(kFull, wmask, next_head);
+    if (bit != 0 && even_rank) {
+        // corner k (with bit set iff up) is the odd head's corner k ^ bit
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            const bool shared = up ? (k & bit) != 0 : (k & bit) == 0;
+            if (!shared) continue;
+            const int src = bit == 4 ? (k ^ 4) : bit == 2 ? (k ^ 2) : (k ^ 1);
+            float sa = 0.0f, sb[3] = {0.0f, 0.0f, 0.0f};
+#pragma unroll
+            for (int j = 0; j < 8; ++j)
+                if (j == src) {
+                    sa = pa[j];
+#pragma unroll
+                    for (int ch = 0; ch < 3; ++ch) sb[ch] = pb[j][ch];
+                }
+            a[k] += sa;
+#pragma unroll
+            for (int ch = 0; ch < 3; ++ch) b[k][ch] += sb[ch];
+            wmask |= ((pw >> src) & 1u) << k;
+        }
+    } else if (bit != 0) {
+        // the odd head leaves out its shared corners: those with bit clear iff up
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            const bool shared = up ? (k & bit) == 0 : (k & bit) != 0;
+            if (shared) wmask &= ~(1u << k);
+        }
+    }
     if (!scat || odd) return;
 #pragma unroll
     for (int k = 0; k < 8; ++k) {

@@ -427,7 +427,7 @@ __global__ void __launch_bounds__(kCombineWarps * 32) march_combine_kernel(GridV
 
 // With the forward's stored values (VALS) the adjoint gathers no rows: half the registers, twice the
 // resident warps to hide the index loads and atomics.
-constexpr int kBwdValsBlocks = 6;
+constexpr int kBwdValsBlocks = 5;
 
 template <int FORM, bool VALS>
 __global__ void __launch_bounds__(kChunkWarps * 32, VALS ? kBwdValsBlocks : kGatherBlocks) march_chunks_bwd_kernel(
