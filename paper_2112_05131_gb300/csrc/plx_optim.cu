@@ -418,7 +418,10 @@ __global__ void __launch_bounds__(256) rms_compact_kernel(GridView g, int64_t n_
 }
 
 // Pass 2: rows from the list (sparse) or all rows (dense).  A warp takes 32 rows at a time, 8 lanes per
-// row (quarters 0..6, lane 7 idle), two groups of 4 rows per round so six float4 loads are in flight.
+// row (quarters 0..6, lane 7 idle), kRmsGroups groups of 4 rows per round so that 3 kRmsGroups float4
+// loads of each lane are in flight together.
+constexpr int kRmsGroups = 2;
+constexpr int kRmsGridPerSm = 8;  // CTAs per SM in the grid (warps loop over 32-row slices)
 template <bool SPARSE>
 __global__ void __launch_bounds__(256) rms_apply_kernel(GridView g, float *__restrict__ rows,
                                                         uint16_t *__restrict__ rows_h, float *__restrict__ grad,
@@ -434,24 +437,25 @@ __global__ void __launch_bounds__(256) rms_apply_kernel(GridView g, float *__res
         const int64_t li = base + lane;
         const int32_t mine = li < total ? (SPARSE ? g.tlist[li] : (int32_t)li) : -1;
 #pragma unroll 1
-        for (int sub = 0; sub < 8; sub += 2) {
-            const int32_t r0 = __shfl_sync(kFull, mine, 4 * sub + grp);
-            const int32_t r1 = __shfl_sync(kFull, mine, 4 * (sub + 1) + grp);
+        for (int sub = 0; sub < 8; sub += kRmsGroups) {
+            int32_t r[kRmsGroups];
+#pragma unroll
+            for (int j = 0; j < kRmsGroups; ++j) r[j] = __shfl_sync(kFull, mine, 4 * (sub + j) + grp);
             if (q == 7) continue;
             const float4 z = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
-            float4 g0 = z, x0 = z, v0 = z, g1 = z, x1 = z, v1 = z;
-            if (r0 >= 0) {
-                g0 = reinterpret_cast<const float4 *>(grad + (int64_t)r0 * kRowF)[q];
-                x0 = reinterpret_cast<const float4 *>(rows + (int64_t)r0 * kRowF)[q];
-                v0 = reinterpret_cast<const float4 *>(v + (int64_t)r0 * kRowF)[q];
+            float4 gg[kRmsGroups], xx[kRmsGroups], vv[kRmsGroups];
+#pragma unroll
+            for (int j = 0; j < kRmsGroups; ++j) {
+                gg[j] = xx[j] = vv[j] = z;
+                if (r[j] >= 0) {
+                    gg[j] = reinterpret_cast<const float4 *>(grad + (int64_t)r[j] * kRowF)[q];
+                    xx[j] = reinterpret_cast<const float4 *>(rows + (int64_t)r[j] * kRowF)[q];
+                    vv[j] = reinterpret_cast<const float4 *>(v + (int64_t)r[j] * kRowF)[q];
+                }
             }
-            if (r1 >= 0) {
-                g1 = reinterpret_cast<const float4 *>(grad + (int64_t)r1 * kRowF)[q];
-                x1 = reinterpret_cast<const float4 *>(rows + (int64_t)r1 * kRowF)[q];
-                v1 = reinterpret_cast<const float4 *>(v + (int64_t)r1 * kRowF)[q];
-            }
-            if (r0 >= 0) rms_update(r0, q, g0, x0, v0, rows, rows_h, grad, v, lr_sigma, lr_sh, beta, eps);
-            if (r1 >= 0) rms_update(r1, q, g1, x1, v1, rows, rows_h, grad, v, lr_sigma, lr_sh, beta, eps);
+#pragma unroll
+            for (int j = 0; j < kRmsGroups; ++j)
+                if (r[j] >= 0) rms_update(r[j], q, gg[j], xx[j], vv[j], rows, rows_h, grad, v, lr_sigma, lr_sh, beta, eps);
         }
     }
 }
@@ -465,7 +469,7 @@ cudaError_t launch_rmsprop(const GridView &g, float *rows, uint16_t *rows_h, flo
         int dev = 0;
         if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     }
-    const int64_t apply_blocks = std::min<int64_t>((g.M + 255) / 256, (int64_t)sms * 8);
+    const int64_t apply_blocks = std::min<int64_t>((g.M + 255) / 256, (int64_t)sms * kRmsGridPerSm);
     if (sparse) {
         cudaError_t e = cudaMemsetAsync(g.tcount, 0, sizeof(int), s);
         if (e != cudaSuccess) return e;
