@@ -12,9 +12,9 @@ Every step is Trainer.step (ray generation, training march, MSE gradient, adjoin
 and upsample are plx_grid_prune_* / plx_grid_upsample_*.
 
 The training images are the ground-truth grid rendered by plx_render for every training view, copied
-once to the device; each step's 5000 pixels are drawn on the host with a seeded generator, 256 steps
-at a time, and uploaded in one copy, and their target colours are gathered from the device images
-(the role a data loader plays).
+once to the device; each step's 5000 pixels and its TV segments are drawn on the device with a seeded
+generator, 256 steps at a time, and the pixels' target colours gathered from the device images (the
+role a data loader plays).
 The paper does not give the steps at which it upsamples for a 128^3 start; `upsample_at` defaults to
 thirds of the run.  `paper_synthetic()` is the paper's own synthetic schedule (Supp. B.2).
 """
@@ -90,37 +90,41 @@ def psnr(a: np.ndarray, b: np.ndarray) -> float:
 
 
 class _Batches:
-    """Pixel ids and TV segments for `chunk` steps at a time, each uploaded in one copy from pinned
-    memory, and the steps' target colours gathered from the images on the device, so that a step issues
-    no host-to-device copy of its own."""
+    """Pixel ids, targets and TV segments for `chunk` steps at a time, drawn on the device with a seeded
+    generator, so that a step issues no host work beyond slicing and no copy of its own: pixel ids
+    uniform over all pixels of all training views, their target colours gathered from the images on the
+    device, and each step's TV segments as a uniformly random set of whole `tv_segment`-node slots of
+    the node order (the same distribution as synth.tv_segments), sorted."""
 
     def __init__(self, images: np.ndarray, cfg: C2FConfig, device):
         self.flat = torch.from_numpy(np.ascontiguousarray(images.reshape(-1, 3), np.float32)).to(device)
         self.n_pix = self.flat.shape[0]
         self.cfg = cfg
         self.dev = device
-        self.rng = np.random.default_rng(cfg.seed)
+        self.gen = torch.Generator(device=device)
+        self.gen.manual_seed(cfg.seed)
         self.step0 = -1
         self.R = -1
         self.pix = self.tgt = self.ss = self.sl = None
 
     def get(self, step: int, R: int):
-        import synth
-
         c = self.cfg
         if self.pix is None or R != self.R or step >= self.step0 + c.chunk or step < self.step0:
             self.step0, self.R = step, R
-            pix = self.rng.integers(0, self.n_pix, size=(c.chunk, c.batch), dtype=np.int64)
-            segs = [synth.tv_segments(R, c.tv_fraction, min(c.tv_segment, R ** 3), seed=int(self.rng.integers(2 ** 31)))
-                    for _ in range(c.chunk)]
-            self.n_sel = [int(sl.sum()) for _, sl in segs]
-            ss = np.stack([a for a, _ in segs])  # every step has the same number of segments
-            sl = np.stack([b for _, b in segs])
-            up = lambda a: torch.from_numpy(a).pin_memory().to(self.dev, non_blocking=True)
-            self.pix, self.ss, self.sl = up(pix), up(ss), up(sl)
+            self.pix = torch.randint(0, self.n_pix, (c.chunk, c.batch), generator=self.gen, device=self.dev,
+                                     dtype=torch.int64)
             self.tgt = self.flat.index_select(0, self.pix.view(-1)).view(c.chunk, c.batch, 3)
+            N = R ** 3
+            seg = min(c.tv_segment, N)
+            n_slots = max(1, N // seg)  # whole slots only, so every segment has `seg` nodes
+            n_seg = max(1, min(n_slots, int(round(c.tv_fraction * N / seg))))
+            keys = torch.rand((c.chunk, n_slots), generator=self.gen, device=self.dev)
+            slots = keys.topk(n_seg, dim=1, sorted=False).indices.sort(dim=1).values
+            self.ss = slots.to(torch.int64) * seg
+            self.sl = torch.full((c.chunk, n_seg), seg, dtype=torch.int64, device=self.dev)
+            self.n_sel = n_seg * seg
         k = step - self.step0
-        return self.pix[k], self.tgt[k], self.ss[k], self.sl[k], self.n_sel[k]
+        return self.pix[k], self.tgt[k], self.ss[k], self.sl[k], self.n_sel
 
 
 def train(train_images: np.ndarray, cams: torch.Tensor, W: int, H: int, cfg: C2FConfig = C2FConfig(),
