@@ -130,10 +130,17 @@ class Trainer:
             self.grad_rgb = torch.empty((n, 3), dtype=torch.float32, device=dev)
         self.o, self.d, self.state = self._o[0], self._d[0], self._state[0]
 
-    def __del__(self):
+    def close(self):
+        """Destroys the native trainer (its streams and events); the buffers stay with this object."""
         if getattr(self, "_native", None) is not None:
             L.load().plx_trainer_destroy(self._native)
             self._native = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:  # interpreter shutdown: the binding may already be gone
+            pass
 
     def _touched_slot(self, stream) -> Optional[torch.Tensor]:
         """The log entry for this step's touched-row count (plx_count_touched), growing the log on `stream`."""
@@ -158,7 +165,9 @@ class Trainer:
 
     def finish(self, stream=None):
         """Applies the pending RMSProp update (overlap mode defers each step's update to the next call)."""
-        if self._native is not None:
+        if self.cfg.overlap:
+            if self._native is None:
+                raise RuntimeError("the trainer is closed")
             L.call("plx_trainer_finish", self._native, _stream(stream))
 
     @staticmethod
@@ -185,7 +194,9 @@ class Trainer:
         main = stream if stream is not None else torch.cuda.current_stream()
         do_tv = seg_start is not None and n_selected > 0
 
-        if self._native is not None:
+        if c.overlap:
+            if self._native is None:
+                raise RuntimeError("the trainer is closed")
             _need(pix, torch.int64, "pix", (n,))
             _need(target, torch.float32, "target", (n, 3))
             if next_pix is not None:
