@@ -327,3 +327,52 @@ def test_planned_mse_matches_oracle(cuda_lib):
     gref = oracle.render_backward(sc.R, sc.idx, sc.rows, o.astype(float), d.astype(float),
                                   grad.cpu().numpy().astype(np.float64), bg=BG)
     check_grads(gr.cpu().numpy(), gref)
+
+
+@pytest.mark.parametrize("stop,lam_s", [(1e-3, 0.0), (0.0, 1e-4)])
+def test_native_step_matches_serial_calls(cuda_lib, stop, lam_s):
+    """plx_trainer_step with early termination (the recomputing march) and with the Cauchy prior: its
+    first step's gradient and both losses equal the serial Trainer's (the same library calls in order),
+    up to the order of atomic additions."""
+    from paper_2112_05131_gb300.grid import Grid, RenderOpts, gen_rays
+    from paper_2112_05131_gb300.train import StepConfig, Trainer
+
+    gt = synth.scene_config("dense32")
+    sc = synth.perturb(gt, 0.05, seed=3)
+    cams = torch.from_numpy(synth.cameras_config("sphere8_64")).cuda()
+    opts = RenderOpts(0.5, (1.0, 1.0, 1.0), stop)
+    g_gt = Grid.from_host(gt.R, gt.idx, gt.rows)
+    pix = torch.from_numpy(synth.pixel_batch(8, 64, 64, 1500, seed=61)).cuda()
+    o, d = gen_rays(cams, pix, 64, 64)
+    target = g_gt.render(o, d, opts)
+    ss, sl = synth.tv_segments(gt.R, 0.2, 256, seed=62)
+    ss_t, sl_t = torch.from_numpy(ss).cuda(), torch.from_numpy(sl).cuda()
+    out = {}
+    for overlap in (True, False):
+        g = Grid.from_host(sc.R, sc.idx, sc.rows)
+        tr = Trainer(g, cams, 64, 64, StepConfig(batch=1500, opts=opts, overlap=overlap, lambda_sparsity=lam_s,
+                                                 lambda_tv_sigma=1e-3, lambda_tv_sh=1e-3))
+        tr.step(pix, target, ss_t, sl_t, int(sl.sum()), 0.0, 0.0)  # zero rates: the update leaves rows as they are
+        torch.cuda.synchronize()
+        grad = tr.grad[:, :28].cpu().numpy().copy() if overlap else None
+        if not overlap:  # the serial step has already applied (and cleared) it: recompute by the calls
+            g2 = Grid.from_host(sc.R, sc.idx, sc.rows)
+            st = g2.new_march_state(1500, opts)
+            o2, d2 = gen_rays(cams, pix, 64, 64)
+            g2.march_plan(o2, d2, opts, st)
+            rgb = g2.render_planned(o2, d2, opts, st)
+            from paper_2112_05131_gb300.grid import mse_grad
+            gr = g2.render_backward_train(o2, d2, mse_grad(rgb, target), opts, st, lambda_sparsity=lam_s)
+            g2.tv_grad(ss_t, sl_t, int(sl.sum()), 1e-3, 1e-3, gr)
+            grad = gr[:, :28].cpu().numpy()
+        tr.finish()
+        torch.cuda.synchronize()
+        g.check()
+        out[overlap] = (grad, tr.loss.item(), tr.loss_sparsity.item())
+    ga, gb = out[True][0], out[False][0]
+    gmax = np.abs(gb).max()
+    assert gmax > 0 and np.allclose(ga, gb, rtol=1e-5, atol=1e-6 * gmax)
+    assert out[True][1] == pytest.approx(out[False][1], rel=1e-5)
+    assert out[True][2] == pytest.approx(out[False][2], rel=1e-5, abs=1e-30)
+    if lam_s > 0:
+        assert out[True][2] > 0
