@@ -106,6 +106,11 @@ cudaError_t launch_mse_grad(const float *rgb, const float *target, int64_t n, fl
 
 // --------------------------------------------------------------------------- forward
 constexpr int kFwdWarps = 4;
+// Resident CTAs per SM the one-warp-per-ray render kernels are compiled for, per row form: the
+// register cap it implies trades a few spilled bytes for more warps to hide the gathers' latency.
+constexpr int kFwdBlocksF32 = 6;
+constexpr int kFwdBlocksBF16 = 5;
+constexpr int fwd_blocks(int form) { return form == PLX_SH_BF16 ? kFwdBlocksBF16 : kFwdBlocksF32; }
 
 // The forward march of one ray by one warp (Eq. 1 over the compacted samples, chunk by chunk):
 // returns, in every lane, the composited colour without the background and the final
@@ -153,7 +158,7 @@ __device__ __forceinline__ void march_forward(const GridView &g, const RenderPar
 }
 
 template <int FORM>
-__global__ void __launch_bounds__(kFwdWarps * 32, kGatherBlocks) render_fwd_kernel(GridView g, const float *__restrict__ ro,
+__global__ void __launch_bounds__(kFwdWarps * 32, fwd_blocks(FORM)) render_fwd_kernel(GridView g, const float *__restrict__ ro,
                                                                     const float *__restrict__ rd, int64_t n,
                                                                     RenderParams p, float *__restrict__ rgb,
                                                                     float *__restrict__ T_out) {
@@ -196,7 +201,7 @@ struct SceneTable {
 };
 
 template <int FORM>
-__global__ void __launch_bounds__(kFwdWarps * 32, kGatherBlocks) render_tiles_kernel(
+__global__ void __launch_bounds__(kFwdWarps * 32, fwd_blocks(FORM)) render_tiles_kernel(
     const __grid_constant__ SceneTable tab, int n_scenes, const float *__restrict__ cams, int n_cams,
     const plx_tile *__restrict__ tiles, int64_t n_rays) {
     __shared__ int s_ring[kFwdWarps][kRing];
