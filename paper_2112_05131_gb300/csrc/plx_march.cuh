@@ -126,6 +126,24 @@ __device__ __forceinline__ uint4 ldg4_pinned(const uint4 *p) {
     return v;
 }
 
+// Packed FP32 arithmetic (fma.rn.f32x2): one instruction computes two independent fmaf, each
+// rounded once as fmaf is, so results equal the scalar code's bit for bit.
+__device__ __forceinline__ uint64_t f32x2(float a, float b) {
+    uint64_t r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
+    return r;
+}
+// (a0, a1) += (w, w) * (x0, x1), with ww = f32x2(w, w)
+__device__ __forceinline__ void fma2(float &a0, float &a1, uint64_t ww, float x0, float x1) {
+    asm("{\n\t.reg .b64 acc, xx;\n\t"
+        "mov.b64 acc, {%0, %1};\n\t"
+        "mov.b64 xx, {%3, %4};\n\t"
+        "fma.rn.f32x2 acc, %2, xx, acc;\n\t"
+        "mov.b64 {%0, %1}, acc;\n\t}"
+        : "+f"(a0), "+f"(a1)
+        : "l"(ww), "f"(x0), "f"(x1));
+}
+
 // Full sample: interpolated values at grid point gc, whose cell the caller has
 // already found occupied (compaction).  rows_out/f_out (and base_out, if given)
 // receive the corners.
@@ -160,6 +178,8 @@ __device__ __forceinline__ bool gather_sample(const GridView &g, int form, const
                 asm volatile("" : "+f"(v[k][q].x), "+f"(v[k][q].y), "+f"(v[k][q].z), "+f"(v[k][q].w));
 #pragma unroll
         for (int k = 0; k < 8; ++k) {
+            // scalar FMAs here: the packed form needs register pairs, and at the FP32 render kernels'
+            // register cap it spilled more and measured slower
             const float w = corner_weight(c.f, k);
 #pragma unroll
             for (int q = 0; q < 7; ++q) {
@@ -187,13 +207,14 @@ __device__ __forceinline__ bool gather_sample(const GridView &g, int form, const
             const uint32_t wd[16] = {v[k][0].x, v[k][0].y, v[k][0].z, v[k][0].w, v[k][1].x, v[k][1].y,
                                      v[k][1].z, v[k][1].w, v[k][2].x, v[k][2].y, v[k][2].z, v[k][2].w,
                                      v[k][3].x, v[k][3].y, v[k][3].z, v[k][3].w};
+            const uint64_t ww = f32x2(w, w);
             acc[0] = fmaf(w, __uint_as_float(wd[0]), acc[0]);
+            // SH pairs (2i, 2i+1) share word 1 + i: low half, then high half
 #pragma unroll
-            for (int sh = 0; sh < 27; ++sh) {
-                const uint32_t word = wd[1 + (sh >> 1)];
-                const uint32_t bits = (sh & 1) ? (word & 0xffff0000u) : (word << 16);
-                acc[1 + sh] = fmaf(w, __uint_as_float(bits), acc[1 + sh]);
-            }
+            for (int i = 0; i < 13; ++i)
+                fma2(acc[1 + 2 * i], acc[2 + 2 * i], ww, __uint_as_float(wd[1 + i] << 16),
+                     __uint_as_float(wd[1 + i] & 0xffff0000u));
+            acc[27] = fmaf(w, __uint_as_float(wd[14] << 16), acc[27]);
         }
     }
 #pragma unroll
