@@ -11,6 +11,8 @@
 #include <cuda_bf16.h>
 #include <stdint.h>
 
+#include <utility>
+
 #include "plenoxel.h"
 
 namespace plx {
@@ -19,6 +21,34 @@ constexpr int kNV = 28;          // values per node: density + 27 SH
 constexpr int kRowF = 32;        // floats per F32 row (128 bytes)
 constexpr int kRowH = 32;        // uint16 per BF16 row (64 bytes)
 constexpr unsigned kFull = 0xffffffffu;
+
+// Chained launches (programmatic dependent launch).  A kernel started by launch_chained may be
+// scheduled while the kernel before it in the stream is still finishing; its first statement is
+// chain_wait(), which returns once every earlier kernel of the stream has completed and its memory
+// is visible, so no thread touches global memory before the stream order allows (launched plainly,
+// chain_wait() returns at once).  chain_release() lets the next chained kernel be scheduled once
+// every CTA of this grid has issued it.  Only the launch latency and CTA ramp are overlapped.
+// Used for the RMSProp update after its compaction; chaining the march kernels as well made each
+// faster alone but took from the TV kernel beside them the SM slots it fills between launches, and
+// the overlapped step measured slower.
+__device__ __forceinline__ void chain_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void chain_release() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_chained(void (*kernel)(KArgs...), unsigned grid, unsigned block, cudaStream_t s,
+                                  Args &&...args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(block);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
+}
 
 // device status codes (stored in the grid workspace's first word)
 enum : int { kDevOk = 0, kDevBadRow = 1, kDevTooManySamples = 2, kDevCountMismatch = 3, kDevStateMismatch = 4, kDevBadTile = 5 };

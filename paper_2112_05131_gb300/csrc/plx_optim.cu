@@ -386,6 +386,7 @@ __global__ void __launch_bounds__(1024) count_touched_kernel(GridView g, int64_t
 // Sparse mode, pass 1: the rows marked in the touched bitmask, as a list, and the mask cleared.  A
 // warp takes 32 mask words at a time; the order of the list does not matter (rows update independently).
 __global__ void __launch_bounds__(256) rms_compact_kernel(GridView g, int64_t n_words) {
+    chain_release();  // the update (chained) may be scheduled as this pass drains
     const int lane = threadIdx.x & 31;
     const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t n_warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
@@ -427,6 +428,8 @@ __global__ void __launch_bounds__(256) rms_apply_kernel(GridView g, float *__res
                                                         uint16_t *__restrict__ rows_h, float *__restrict__ grad,
                                                         float *__restrict__ v, float lr_sigma, float lr_sh, float beta,
                                                         float eps) {
+    chain_wait();
+    chain_release();
     const int lane = threadIdx.x & 31;
     const int q = lane & 7;
     const int grp = lane >> 3;
@@ -475,15 +478,13 @@ cudaError_t launch_rmsprop(const GridView &g, float *rows, uint16_t *rows_h, flo
         if (e != cudaSuccess) return e;
         const int64_t blocks = std::min<int64_t>((n_words + 255) / 256, (int64_t)sms * 8);
         rms_compact_kernel<<<(unsigned)blocks, 256, 0, s>>>(g, n_words);
-        rms_apply_kernel<true><<<(unsigned)apply_blocks, 256, 0, s>>>(g, rows, rows_h, grad, v, lr_sigma, lr_sh,
-                                                                      beta, eps);
-    } else {
-        rms_apply_kernel<false><<<(unsigned)apply_blocks, 256, 0, s>>>(g, rows, rows_h, grad, v, lr_sigma, lr_sh,
-                                                                       beta, eps);
-        cudaError_t e = cudaMemsetAsync(g.touched, 0, (size_t)n_words * 4, s);
-        if (e != cudaSuccess) return e;
+        return launch_chained(rms_apply_kernel<true>, (unsigned)apply_blocks, 256, s, g, rows, rows_h, grad, v,
+                              lr_sigma, lr_sh, beta, eps);
     }
-    return cudaGetLastError();
+    cudaError_t e = launch_chained(rms_apply_kernel<false>, (unsigned)apply_blocks, 256, s, g, rows, rows_h, grad, v,
+                                   lr_sigma, lr_sh, beta, eps);
+    if (e != cudaSuccess) return e;
+    return cudaMemsetAsync(g.touched, 0, (size_t)n_words * 4, s);
 }
 
 cudaError_t launch_count_touched(const GridView &g, int64_t *out, cudaStream_t s) {
