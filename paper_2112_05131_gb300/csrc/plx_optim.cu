@@ -230,6 +230,9 @@ __device__ __forceinline__ TvSpan tv_load_span(const GridView &g, int64_t start,
             ++i;
         }
     }
+    // an interior node and its +x, +y, +z neighbours are four corners of the cell based at the node: if
+    // the occupancy mask has that cell empty, all four entries are NULL and no index entry is read
+    if (i + 1 < R && j + 1 < R && k + 1 < R && !cell_occupied(g, n)) return t;
     t.rs = row_of(g, n);
     t.rn[0] = i + 1 < R ? row_of(g, n + R * R) : -1;
     t.rn[1] = j + 1 < R ? row_of(g, n + R) : -1;
