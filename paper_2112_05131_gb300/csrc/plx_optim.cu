@@ -152,7 +152,7 @@ cudaError_t launch_pack_bf16(const GridView &g, uint16_t *rows_h, cudaStream_t s
 // average segment length) as it has 256-node spans, so short and long runs
 // both fill the GPU.
 constexpr int kTvThreads = 256;
-constexpr int kTvBlocks = 4;       // CTAs per SM the register budget allows
+constexpr int kTvBlocks = 5;       // CTAs per SM (48 registers, a few spilled bytes; 4 CTAs at 60 registers measured slower)
 constexpr int kTvSpansPerWarp = 1; // 32-node spans a warp takes per item (more, with the next one's index loads prefetched, measured slower)
 constexpr int kTvGridPerSm = 32;  // at most this many CTAs per SM in the grid (a persistent grid measured slower)
 
