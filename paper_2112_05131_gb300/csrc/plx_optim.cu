@@ -148,13 +148,13 @@ cudaError_t launch_pack_bf16(const GridView &g, uint16_t *rows_h, cudaStream_t s
 // one float4 quarter of the (up to) four rows and scattering float4 gradients:
 //   D_a = (V_d(v+e_a) - V_d(v)) * R/256; t = |D|; L += lam_d t;
 //   missing neighbour (NULL or outside): density 0, SH = V_d(v).
-// Each segment is split over as many CTAs ("parts", sized on the host from the
-// average segment length) as it has 256-node spans, so short and long runs
-// both fill the GPU.
-constexpr int kTvThreads = 256;
-constexpr int kTvBlocks = 5;       // CTAs per SM (48 registers, a few spilled bytes; 4 CTAs at 60 registers measured slower)
-constexpr int kTvSpansPerWarp = 1; // 32-node spans a warp takes per item (more, with the next one's index loads prefetched, measured slower)
-constexpr int kTvGridPerSm = 32;  // at most this many CTAs per SM in the grid (a persistent grid measured slower)
+// A CTA takes a region of kTvRegion consecutive nodes of a segment at a time; each
+// segment is split over as many CTAs ("parts", sized on the host from the average
+// segment length) as it has regions, so short and long runs both fill the GPU.
+constexpr int kTvThreads = 128;
+constexpr int kTvLaneNodes = 16;                 // nodes each lane of the first warp screens (4, 8, 32 measured slower)
+constexpr int kTvRegion = 32 * kTvLaneNodes;    // nodes a CTA takes at once
+constexpr int kTvGridPerSm = 16;  // at most this many CTAs per SM in the grid
 
 __device__ __forceinline__ float4 ld4(const float *p) { return __ldg(reinterpret_cast<const float4 *>(p)); }
 
@@ -204,90 +204,136 @@ __device__ __forceinline__ void tv_quarter(const GridView &g, int32_t rs, const 
         atomicAdd(reinterpret_cast<float4 *>(grad + (int64_t)rs * kRowF + 4 * q), make_float4(gs[0], gs[1], gs[2], gs[3]));
 }
 
-// The index entries of one lane's node of a 32-node span: the node's row and those of its +x, +y, +z
-// neighbours (-1: NULL, outside the grid, or outside the segment).
-struct TvSpan {
+// The row entries TV needs for one node: its own and those of its +x, +y, +z neighbours (-1: NULL or
+// outside the grid).
+struct TvNode {
     int32_t rs, rn[3];
 };
 
-// Lane l's entries for node start + off0 + l (off0: the span's offset in its segment of length len).
-// (i, j, k) of the span's first node by one division, then carried lane by lane.
-__device__ __forceinline__ TvSpan tv_load_span(const GridView &g, int64_t start, int64_t len, int64_t off0, int lane) {
+// Candidates among the (up to) 32 nodes n_a .. n_a + cnt - 1 of one lane: bit t set when node n_a + t may
+// have an occupied row among self and +x/+y/+z.  An interior node and those neighbours are four corners
+// of the cell based at the node, so the cell's occupancy bit decides; a node on a far face (i, j or k =
+// R - 1) is the base of no cell and stays a candidate, to be decided by its index entries.
+__device__ __forceinline__ uint32_t tv_candidates(const GridView &g, int64_t n_a, int cnt) {
     const int64_t R = g.R;
-    const int64_t N = R * R * R;
-    TvSpan t = {-1, {-1, -1, -1}};
-    const int64_t n0 = start + off0;
-    const int64_t n = n0 + lane;
-    if (off0 + lane >= len || n0 < 0 || n >= N) return t;
-    int64_t i = n0 / (R * R);
-    const int64_t rem = n0 - i * R * R;
+    const int64_t n_words = (R * R * R + 31) >> 5;
+    const int64_t w = n_a >> 5;
+    const int sh = (int)(n_a & 31);
+    uint32_t bits = __ldg(g.occ + w) >> sh;
+    if (sh && w + 1 < n_words) bits |= __ldg(g.occ + w + 1) << (32 - sh);
+    int64_t i = n_a / (R * R);
+    const int64_t rem = n_a - i * R * R;
     int64_t j = rem / R;
-    int64_t k = rem - j * R + lane;
-    while (k >= R) {
-        k -= R;
+    int64_t k = rem - j * R;
+    uint32_t face = 0u;
+    for (int t = 0; t < cnt;) {  // one pass per grid row the nodes touch
+        const int run = (int)min((int64_t)(cnt - t), R - k);
+        if (i == R - 1 || j == R - 1)
+            face |= (run == 32 ? kFull : ((1u << run) - 1u)) << t;
+        else if (k + run == R)
+            face |= 1u << (t + run - 1);
+        t += run;
+        k = 0;
         if (++j == R) {
             j = 0;
             ++i;
         }
     }
-    // an interior node and its +x, +y, +z neighbours are four corners of the cell based at the node: if
-    // the occupancy mask has that cell empty, all four entries are NULL and no index entry is read
-    if (i + 1 < R && j + 1 < R && k + 1 < R && !cell_occupied(g, n)) return t;
-    t.rs = row_of(g, n);
-    t.rn[0] = i + 1 < R ? row_of(g, n + R * R) : -1;
-    t.rn[1] = j + 1 < R ? row_of(g, n + R) : -1;
-    t.rn[2] = k + 1 < R ? row_of(g, n + 1) : -1;
-    return t;
+    const uint32_t valid = cnt == 32 ? kFull : ((1u << cnt) - 1u);
+    return (bits | face) & valid;
 }
 
-// A warp takes the 32-node spans of its (segment, part) item in turn, loading the next span's index
-// entries before it processes the current one, so the two memory round trips of a span (index, then
-// rows) overlap across spans.  Nodes with no occupied row among self and +x/+y/+z are skipped; the
-// others are processed four at a time with 8 lanes each (one float4 quarter per lane), so a node's
-// rows take one round trip.
-__global__ void __launch_bounds__(kTvThreads, kTvBlocks) tv_kernel(GridView g, const int64_t *__restrict__ seg_start,
-                                                                   const int64_t *__restrict__ seg_len, int64_t n_seg,
-                                                                   int64_t parts, float lam_sigma, float lam_sh,
-                                                                   float *__restrict__ grad, float *__restrict__ loss) {
+// Per region of a segment, three phases separated by CTA barriers: (1) the first warp screens the
+// region's nodes against the occupancy bit map (one bit per node instead of four index entries) and
+// lists the candidates in shared memory; (2) every thread reads the index entries of one candidate at a
+// time and keeps, in a second list, the nodes with an occupied row among self and +x/+y/+z; (3) each
+// warp takes the kept nodes four at a time with 8 lanes per node (one float4 quarter each), so a node's
+// rows take one memory round trip.  Only occupied nodes' neighbourhoods cost index reads, and all kept
+// nodes of a region are in flight at once.
+__global__ void __launch_bounds__(kTvThreads) tv_kernel(GridView g, const int64_t *__restrict__ seg_start,
+                                                        const int64_t *__restrict__ seg_len, int64_t n_seg,
+                                                        int64_t parts, float lam_sigma, float lam_sh,
+                                                        float *__restrict__ grad, float *__restrict__ loss) {
+    __shared__ uint16_t s_cand[kTvRegion];
+    __shared__ TvNode s_node[kTvRegion];
+    __shared__ int s_ncand, s_nnode;
     const float scale = (float)g.R / 256.0f;
     const int lane = threadIdx.x & 31;
     const int q = lane & 7;
     const int grp = lane >> 3;
     const int wid = threadIdx.x >> 5;
     constexpr int kWarps = kTvThreads / 32;
+    const int64_t R = g.R;
+    const int64_t N = R * R * R;
     float loss_acc = 0.0f;
-    // item = (segment, part): the parts of a segment interleave their 32-node spans
     for (int64_t item = blockIdx.x; item < n_seg * parts; item += gridDim.x) {
         const int64_t sg = item / parts;
         const int64_t part = item % parts;
         const int64_t start = seg_start[sg];
         const int64_t len = seg_len[sg];
-        const int64_t stride = parts * kWarps * 32;
-        int64_t off0 = (part * kWarps + wid) * 32;
-        TvSpan cur = tv_load_span(g, start, len, off0, lane);
-        for (; off0 < len; off0 += stride) {
-            const TvSpan nxt = tv_load_span(g, start, len, off0 + stride, lane);
-            unsigned mask = __ballot_sync(kFull, cur.rs >= 0 || cur.rn[0] >= 0 || cur.rn[1] >= 0 || cur.rn[2] >= 0);
-            while (mask) {  // uniform
-                const int cnt = __popc(mask);
-                const bool active = grp < cnt;
-                const int src = active ? __fns(mask, 0, grp + 1) : 0;
-                const int32_t ms = __shfl_sync(kFull, cur.rs, src);
-                int32_t mn[3];
+        for (int64_t r0 = part * kTvRegion; r0 < len; r0 += parts * kTvRegion) {  // uniform over the CTA
+            if (wid == 0) {
+                const int64_t off = r0 + lane * kTvLaneNodes;
+                const int64_t n_a = start + off;
+                uint32_t cand = 0u;
+                if (off < len && n_a >= 0 && n_a < N)
+                    cand = tv_candidates(g, n_a, (int)min((int64_t)kTvLaneNodes, min(len - off, N - n_a)));
+                const int c = __popc(cand);
+                int incl = c;
 #pragma unroll
-                for (int a = 0; a < 3; ++a) mn[a] = __shfl_sync(kFull, cur.rn[a], src);
-                if (active && q < 7) {
-                    tv_quarter(g, ms, mn, q, scale, lam_sigma, lam_sh, grad, loss_acc);
+                for (int o = 1; o < 32; o <<= 1) {
+                    const int t = __shfl_up_sync(kFull, incl, o);
+                    if (lane >= o) incl += t;
+                }
+                int pos = incl - c;
+                while (cand) {
+                    const int bit = __ffs(cand) - 1;
+                    cand &= cand - 1u;
+                    s_cand[pos++] = (uint16_t)(lane * kTvLaneNodes + bit);
+                }
+                if (lane == 31) s_ncand = incl;
+                if (lane == 0) s_nnode = 0;
+            }
+            __syncthreads();
+            const int ncand = s_ncand;
+            for (int c = threadIdx.x; c < ncand; c += kTvThreads) {
+                const int64_t n = start + r0 + s_cand[c];
+                int64_t i, j, k;
+                if (N <= (int64_t)UINT32_MAX) {  // 32-bit divisions where the ids fit
+                    const uint32_t n32 = (uint32_t)n, R32 = (uint32_t)R;
+                    const uint32_t ij = n32 / R32;
+                    k = n32 - ij * R32;
+                    i = ij / R32;
+                    j = ij - (uint32_t)i * R32;
+                } else {
+                    i = n / (R * R);
+                    const int64_t rem = n - i * R * R;
+                    j = rem / R;
+                    k = rem - j * R;
+                }
+                TvNode t;
+                t.rs = row_of(g, n);
+                t.rn[0] = i + 1 < R ? row_of(g, n + R * R) : -1;
+                t.rn[1] = j + 1 < R ? row_of(g, n + R) : -1;
+                t.rn[2] = k + 1 < R ? row_of(g, n + 1) : -1;
+                if (t.rs >= 0 || t.rn[0] >= 0 || t.rn[1] >= 0 || t.rn[2] >= 0) s_node[atomicAdd(&s_nnode, 1)] = t;
+            }
+            __syncthreads();
+            const int nn = s_nnode;
+            for (int b = wid * 4; b < nn; b += kWarps * 4) {  // uniform over the warp
+                const int m = b + grp;
+                if (m < nn && q < 7) {
+                    const TvNode t = s_node[m];
+                    tv_quarter(g, t.rs, t.rn, q, scale, lam_sigma, lam_sh, grad, loss_acc);
                     if (q == 0) {
-                        if (ms >= 0) mark_touched(g, ms);
+                        if (t.rs >= 0) mark_touched(g, t.rs);
 #pragma unroll
                         for (int a = 0; a < 3; ++a)
-                            if (mn[a] >= 0) mark_touched(g, mn[a]);
+                            if (t.rn[a] >= 0) mark_touched(g, t.rn[a]);
                     }
                 }
-                for (int k = 0; k < 4 && mask; ++k) mask &= mask - 1u;
             }
-            cur = nxt;
+            __syncthreads();  // the lists are rewritten by the next region
         }
     }
     if (loss) {
@@ -300,11 +346,10 @@ cudaError_t launch_tv(const GridView &g, const int64_t *seg_start, const int64_t
                       int64_t n_selected, float lam_sigma, float lam_sh, float *grad_rows, float *loss,
                       cudaStream_t s) {
     if (n_seg == 0) return cudaSuccess;
-    // parts per segment: kTvSpansPerWarp spans per warp of the average segment; one CTA per item (the
-    // block scheduler balances the short-lived CTAs), at most 2^20 items
-    constexpr int64_t kCtaNodes = (int64_t)kTvThreads * kTvSpansPerWarp;
+    // parts per segment: the regions of the average segment; one CTA per item (the block scheduler
+    // balances the short-lived CTAs), at most 2^20 items
     const int64_t avg = (n_selected + n_seg - 1) / n_seg;
-    const int64_t parts = std::max<int64_t>(1, std::min<int64_t>((avg + kCtaNodes - 1) / kCtaNodes, 1 << 20));
+    const int64_t parts = std::max<int64_t>(1, std::min<int64_t>((avg + kTvRegion - 1) / kTvRegion, 1 << 20));
     int sms = 152;
     {
         int dev = 0;
