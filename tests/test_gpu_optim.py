@@ -41,6 +41,45 @@ def test_tv_parity(cuda_lib, R, frac, seg_len):
     assert abs(loss.item() - L_ref) <= 1e-5 * abs(L_ref) + 1e-12
 
 
+def _random_segments(R, n_seg, max_len, seed):
+    """Non-overlapping runs at random (unaligned) starts with random lengths, sorted."""
+    rng = np.random.default_rng(seed)
+    N = R ** 3
+    cuts = np.sort(rng.choice(np.arange(1, N), size=min(2 * n_seg, N - 1), replace=False))
+    starts, lens = [], []
+    for a, b in zip(cuts[0::2], cuts[1::2]):
+        ln = int(min(b - a, rng.integers(1, max_len + 1)))
+        starts.append(int(a))
+        lens.append(ln)
+    return np.array(starts, np.int64), np.array(lens, np.int64)
+
+
+@pytest.mark.parametrize("R,frac,n_seg,max_len", [(2, 0.5, 2, 8), (3, 0.3, 3, 9), (9, 0.1, 6, 200),
+                                                  (40, 0.02, 12, 1500), (40, 0.4, 12, 1500)])
+def test_tv_parity_unaligned_segments(cuda_lib, R, frac, n_seg, max_len):
+    """TV on runs that start and end anywhere (across regions, far faces and the last node), on
+    sparse scenes whose empty cells the kernel skips by the occupancy mask and on dense ones."""
+    from paper_2112_05131_gb300.grid import Grid
+
+    sc = _scene(R, frac, 100 + R)
+    starts, lens = _random_segments(R, n_seg, max_len, seed=R)
+    starts = np.append(starts, R ** 3 - 1)  # the last node alone: every neighbour outside
+    lens = np.append(lens, 1)
+    keep = np.ones(starts.shape[0], bool)
+    keep[:-1] = starts[:-1] + lens[:-1] <= R ** 3 - 1
+    starts, lens = starts[keep], lens[keep]
+    g = Grid.from_host(sc.R, sc.idx, sc.rows)
+    grad = torch.zeros((sc.M, 32), device="cuda")
+    loss = torch.zeros(1, device="cuda")
+    g.tv_grad(torch.from_numpy(starts).cuda(), torch.from_numpy(lens).cuda(), int(lens.sum()), 1e-2, 3e-3, grad,
+              loss)
+    g.check()
+    L_ref, g_ref = oracle.tv(sc.R, sc.idx, sc.rows, starts, lens, 1e-2, 3e-3)
+    check_grads(grad.cpu().numpy(), g_ref)
+    assert abs(loss.item() - L_ref) <= 1e-5 * abs(L_ref) + 1e-12
+    assert np.array_equal((grad.cpu().numpy()[:, :28] != 0).any(1), (g_ref != 0).any(1))
+
+
 def test_rmsprop_parity_dense(cuda_lib):
     from paper_2112_05131_gb300.grid import Grid
 
