@@ -471,9 +471,8 @@ __global__ void __launch_bounds__(256) rms_compact_kernel(GridView g, int64_t n_
 // loads of each lane are in flight together.
 constexpr int kRmsGroups = 2;
 constexpr int kRmsGridPerSm = 8;  // CTAs per SM in the grid (warps loop over 32-row slices)
-constexpr int kRmsBlocks = 4;     // resident CTAs per SM the update is compiled for (56 registers)
 template <bool SPARSE>
-__global__ void __launch_bounds__(256, kRmsBlocks) rms_apply_kernel(GridView g, float *__restrict__ rows,
+__global__ void __launch_bounds__(256) rms_apply_kernel(GridView g, float *__restrict__ rows,
                                                         uint16_t *__restrict__ rows_h, float *__restrict__ grad,
                                                         float *__restrict__ v, float lr_sigma, float lr_sh, float beta,
                                                         float eps) {
