@@ -142,10 +142,10 @@ cudaError_t launch_pack_bf16(const GridView &g, uint16_t *rows_h, cudaStream_t s
 }
 
 // --------------------------------------------------------------------------- TV
-// A warp takes 32 consecutive selected nodes.  A node whose own row and
-// +x/+y/+z neighbours are all empty has t = 0 for every value and is skipped;
-// the others are handled four at a time, 8 lanes per node, each lane loading
-// one float4 quarter of the (up to) four rows and scattering float4 gradients:
+// A node whose own row and +x/+y/+z neighbours are all empty has t = 0 for every
+// value and is skipped; the others are handled four at a time, 8 lanes per node,
+// each lane loading one float4 quarter of the (up to) four rows and scattering
+// float4 gradients:
 //   D_a = (V_d(v+e_a) - V_d(v)) * R/256; t = |D|; L += lam_d t;
 //   missing neighbour (NULL or outside): density 0, SH = V_d(v).
 // A CTA takes a region of kTvRegion consecutive nodes of a segment at a time; each
@@ -370,14 +370,14 @@ cudaError_t launch_tv(const GridView &g, const int64_t *seg_start, const int64_t
 // gradient keep x and v; a row with any update is re-packed into its BF16-SH
 // form when the grid has one.
 // RMSProp (Sec. 3.5) on one float4 quarter q (< 7) of a row: for every entry with g != 0,
-// v <- beta v + (1 - beta) g^2, x <- x - lr g / (sqrt(v) + eps), then g <- 0; the BF16-SH
-// shadow of the quarter is refreshed.  g4, x4, v4 were loaded by the caller.
-__device__ __forceinline__ void rms_update(int64_t r, int q, float4 g4, float4 x4, float4 v4, float *__restrict__ rows,
-                                           uint16_t *__restrict__ rows_h, float *__restrict__ grad,
-                                           float *__restrict__ v, float lr_sigma, float lr_sh, float beta,
-                                           float eps) {
+// v <- beta v + (1 - beta) g^2, x <- x - lr g / (sqrt(v) + eps), then g <- 0.  g4, x4, v4 were
+// loaded by the caller; x4 returns updated, and the result says whether any entry changed (the caller
+// then refreshes the row's BF16-SH shadow).
+__device__ __forceinline__ bool rms_update(int64_t r, int q, float4 g4, float4 &x4, float4 v4, float *__restrict__ rows,
+                                           float *__restrict__ grad, float *__restrict__ v, float lr_sigma,
+                                           float lr_sh, float beta, float eps) {
     const bool nz = g4.x != 0.0f || g4.y != 0.0f || g4.z != 0.0f || g4.w != 0.0f;
-    if (!nz) return;
+    if (!nz) return false;
     float *xe = &x4.x, *ve = &v4.x;
     const float *ge = &g4.x;
 #pragma unroll
@@ -393,18 +393,7 @@ __device__ __forceinline__ void rms_update(int64_t r, int q, float4 g4, float4 x
     reinterpret_cast<float4 *>(rows + r * kRowF)[q] = x4;
     reinterpret_cast<float4 *>(v + r * kRowF)[q] = v4;
     reinterpret_cast<float4 *>(grad + r * kRowF)[q] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
-    if (rows_h) {
-        // column col sits in BF16 slot col + 1 (SH), density bits in slots 0-1
-        uint16_t *hp = rows_h + r * kRowH;
-#pragma unroll
-        for (int c = 0; c < 4; ++c) {
-            const int col = 4 * q + c;
-            if (col == 0)
-                *reinterpret_cast<uint32_t *>(hp) = __float_as_uint(xe[0]);
-            else
-                hp[col + 1] = bf16_bits_rn(xe[c]);
-        }
-    }
+    return true;
 }
 
 // plx_count_touched: the number of rows marked in the touched bitmask, i.e. the rows that received a
@@ -492,21 +481,35 @@ __global__ void __launch_bounds__(256) rms_apply_kernel(GridView g, float *__res
             int32_t r[kRmsGroups];
 #pragma unroll
             for (int j = 0; j < kRmsGroups; ++j) r[j] = __shfl_sync(kFull, mine, 4 * (sub + j) + grp);
-            if (q == 7) continue;
             const float4 z = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
             float4 gg[kRmsGroups], xx[kRmsGroups], vv[kRmsGroups];
 #pragma unroll
             for (int j = 0; j < kRmsGroups; ++j) {
                 gg[j] = xx[j] = vv[j] = z;
-                if (r[j] >= 0) {
+                if (r[j] >= 0 && q < 7) {
                     gg[j] = reinterpret_cast<const float4 *>(grad + (int64_t)r[j] * kRowF)[q];
                     xx[j] = reinterpret_cast<const float4 *>(rows + (int64_t)r[j] * kRowF)[q];
                     vv[j] = reinterpret_cast<const float4 *>(v + (int64_t)r[j] * kRowF)[q];
                 }
             }
 #pragma unroll
-            for (int j = 0; j < kRmsGroups; ++j)
-                if (r[j] >= 0) rms_update(r[j], q, gg[j], xx[j], vv[j], rows, rows_h, grad, v, lr_sigma, lr_sh, beta, eps);
+            for (int j = 0; j < kRmsGroups; ++j) {
+                bool nz = false;
+                if (r[j] >= 0 && q < 7) nz = rms_update(r[j], q, gg[j], xx[j], vv[j], rows, grad, v, lr_sigma, lr_sh, beta, eps);
+                if (rows_h) {  // uniform over the warp
+                    // The row's BF16 shadow, rewritten whole when any quarter changed, 8 aligned bytes per
+                    // lane: slots 4q..4q+3 hold column 4q - 1 (lane q - 1's fourth value) and columns
+                    // 4q..4q+2 (density bits in slots 0-1, column c in slot c + 1, slots 29-31 zero).
+                    const float prev = __shfl_up_sync(kFull, xx[j].w, 1, 8);
+                    const unsigned row_nz = (__ballot_sync(kFull, nz) >> (8 * grp)) & 0xffu;
+                    if (r[j] >= 0 && row_nz) {
+                        const uint32_t lo = q == 0 ? __float_as_uint(xx[j].x)
+                                                   : (uint32_t)bf16_bits_rn(prev) | ((uint32_t)bf16_bits_rn(xx[j].x) << 16);
+                        const uint32_t hi = (uint32_t)bf16_bits_rn(xx[j].y) | ((uint32_t)bf16_bits_rn(xx[j].z) << 16);
+                        reinterpret_cast<uint2 *>(rows_h + (int64_t)r[j] * kRowH)[q] = make_uint2(lo, hi);
+                    }
+                }
+            }
         }
     }
 }

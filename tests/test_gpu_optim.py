@@ -161,6 +161,48 @@ def test_pack_bf16_bit_exact(cuda_lib):
     assert np.all(h[:, 29:] == 0)
 
 
+def _check_bf16_shadow(g):
+    """The grid's BF16-SH rows are the bit-exact packing of its FP32 rows (density bits, SH rounded to
+    nearest even, padding zero)."""
+    x = g.rows[:, :28].cpu().numpy()
+    h = g.rows_h.cpu().numpy().view(np.uint16)
+    assert np.array_equal(h[:, 0:2].copy().view(np.float32)[:, 0].view(np.uint32), x[:, 0].view(np.uint32))
+    sh = (h[:, 2:29].astype(np.uint32) << 16).view(np.float32)
+    assert np.array_equal(sh, oracle.round_bf16(x[:, 1:]))
+    assert np.all(h[:, 29:] == 0)
+
+
+@pytest.mark.parametrize("sparse", [False, True])
+def test_rmsprop_refreshes_bf16_shadow(cuda_lib, sparse):
+    """After an update of a BF16-SH grid, every row's BF16 shadow equals the packing of its updated
+    FP32 row: rows with a gradient in one quarter only, in several, and rows without any."""
+    from paper_2112_05131_gb300.grid import Grid, RenderOpts
+
+    sc = _scene(24, 0.25, 80)
+    g = Grid.from_host(sc.R, sc.idx, sc.rows, sh_form=1)
+    M = sc.M
+    grad = torch.zeros((M, 32), device="cuda")
+    v = torch.full((M, 32), 1e-6, device="cuda")
+    if sparse:  # marked by the adjoint
+        o, d = synth.random_rays(500, seed=81)
+        gw = torch.from_numpy(np.random.default_rng(82).normal(size=(500, 3)).astype(np.float32)).cuda()
+        g.render_backward(torch.from_numpy(o).cuda(), torch.from_numpy(d).cuda(), gw, RenderOpts(), grad)
+    else:
+        rng = np.random.default_rng(83)
+        g_np = rng.normal(0, 1e-2, size=(M, 28)).astype(np.float32)
+        kind = rng.integers(0, 4, size=M)
+        g_np[kind == 0] = 0.0                      # no gradient
+        g_np[kind == 1, 4:] = 0.0                  # the first quarter only (density and 3 SH)
+        g_np[kind == 2, :24] = 0.0                 # the last quarter only
+        grad[:, :28] = torch.from_numpy(g_np).cuda()
+    assert torch.count_nonzero(grad.abs().sum(1)) > 0
+    rows0 = g.rows.clone()
+    g.rmsprop_step(grad, v, 30.0, 1e-2, sparse=sparse)
+    torch.cuda.synchronize()
+    assert not torch.equal(rows0, g.rows)
+    _check_bf16_shadow(g)
+
+
 def test_mse_grad(cuda_lib):
     from paper_2112_05131_gb300.grid import mse_grad
 
