@@ -1,7 +1,8 @@
 """A grid past the size where a node's linear id leaves 32 bits in the march's cheap candidate test
 (R = 1300: ids up to 2.2e9; the test switches to 64-bit ids above R = 1290), with the FP32 margin,
 the coarse block mask and the occupancy build at that size: forward, the recomputing adjoint and the
-training march against the oracle on rays through a blob of occupied nodes.  The index volume is
+training march against the oracle on rays through a blob of occupied nodes, and TV on runs of nodes
+through it.  The index volume is
 8.8 GB, on the host for the oracle and on the device; the test is skipped where either lacks room."""
 import os
 
@@ -86,3 +87,26 @@ def test_large_grid_render_and_adjoints(cuda_lib, big_scene):
     check_grads(grad_t, gref)
     assert np.sum(np.abs(ref - 1.0).max(1) > 1e-2) > n // 2  # most rays cross the blob
     print(f"R = {R}: {sc.M} rows, colour err/tol {w1:.3f}, grad err/tol {w2:.3f} on {n} rays")
+
+
+def test_large_grid_tv(cuda_lib, big_scene):
+    """TV on runs of nodes through the blob, whose linear ids straddle 2^31 (the kernel's 32-bit
+    coordinate division covers ids below 2^32): gradients and loss against the oracle."""
+    from paper_2112_05131_gb300.grid import Grid
+
+    sc, c = big_scene
+    di, dj = np.meshgrid(np.arange(-20, 21, 2), np.arange(-20, 21, 2), indexing="ij")
+    starts = (((c[0] + di.ravel()).astype(np.int64) * R + (c[1] + dj.ravel())) * R + (c[2] - 30)).astype(np.int64)
+    starts = np.sort(starts)
+    lens = np.full(starts.shape, 61, np.int64)
+    assert starts.min() < 2 ** 31 < starts.max()
+    g = Grid.from_host(R, sc.idx, sc.rows)
+    grad = torch.zeros((sc.M, 32), device="cuda")
+    loss = torch.zeros(1, device="cuda")
+    g.tv_grad(torch.from_numpy(starts).cuda(), torch.from_numpy(lens).cuda(), int(lens.sum()), 1e-2, 3e-3, grad, loss)
+    g.check()
+    L_ref, g_ref = oracle.tv(R, sc.idx, sc.rows, starts, lens, 1e-2, 3e-3)
+    w = check_grads(grad.cpu().numpy(), g_ref)
+    assert abs(loss.item() - L_ref) <= 1e-5 * abs(L_ref) + 1e-12
+    assert int((g_ref != 0).any(1).sum()) > 1000
+    print(f"R = {R} TV: {starts.shape[0]} runs, grad err/tol {w:.3f}")
