@@ -362,13 +362,13 @@ cudaError_t launch_tv(const GridView &g, const int64_t *seg_start, const int64_t
 }
 
 // --------------------------------------------------------------------------- RMSProp
-// One warp per word of the touched mask (32 rows): the word's marked rows (all
-// rows in dense mode) are updated four at a time with 8 lanes per row (lane q
-// owns values 4q..4q+3), so each warp instruction covers 4 whole rows.  The
-// grid has enough warps to keep every touched row's loads in flight at once,
-// which the scattered rows need to reach DRAM efficiently.  Entries with a zero
-// gradient keep x and v; a row with any update is re-packed into its BF16-SH
-// form when the grid has one.
+// Sparse mode lists the rows marked in the touched bitmask (rms_compact_kernel),
+// then a warp takes 32 listed rows (32 consecutive rows in dense mode) and updates
+// them four at a time with 8 lanes per row (lane q owns values 4q..4q+3), so each
+// warp instruction covers 4 whole rows.  The grid has enough warps to keep every
+// touched row's loads in flight at once, which the scattered rows need to reach
+// DRAM efficiently.  Entries with a zero gradient keep x and v; a row with any
+// update is re-packed into its BF16-SH form when the grid has one.
 // RMSProp (Sec. 3.5) on one float4 quarter q (< 7) of a row: for every entry with g != 0,
 // v <- beta v + (1 - beta) g^2, x <- x - lr g / (sqrt(v) + eps), then g <- 0.  g4, x4, v4 were
 // loaded by the caller; x4 returns updated, and the result says whether any entry changed (the caller
@@ -456,8 +456,8 @@ __global__ void __launch_bounds__(256) rms_compact_kernel(GridView g, int64_t n_
 }
 
 // Pass 2: rows from the list (sparse) or all rows (dense).  A warp takes 32 rows at a time, 8 lanes per
-// row (quarters 0..6, lane 7 idle), kRmsGroups groups of 4 rows per round so that 3 kRmsGroups float4
-// loads of each lane are in flight together.
+// row (quarters 0..6; lane 7 only stores the last 8 bytes of a BF16 shadow), kRmsGroups groups of 4 rows
+// per round so that 3 kRmsGroups float4 loads of each lane are in flight together.
 constexpr int kRmsGroups = 2;
 constexpr int kRmsGridPerSm = 8;  // CTAs per SM in the grid (warps loop over 32-row slices)
 template <bool SPARSE>
