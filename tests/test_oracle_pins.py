@@ -518,12 +518,55 @@ def test_backward_mag_dominates_abs_and_matches_it_without_cancellation():
     assert np.allclose(oracle.render_backward_mag(R, idx, rows, o, d, -g, bg=(0.3, 0.5, 0.7)), m, rtol=1e-12, atol=0)
 
 
-def test_mse_gradient():
+def test_mse_closed_form_constant_error():
+    """Eq. 3's reconstruction term is the mean over the batch of the squared 2-norm over RGB.  With
+    every channel of every ray off by the same c, each ray contributes ||(c, c, c)||^2 = 3 c^2, so the
+    mean is 3 c^2 whatever the batch size, and the loss scales as c^2; a loss normalised by 3n (a
+    per-channel mean) or not normalised at all gives c^2 or 3 n c^2 and fails here."""
     rng = np.random.default_rng(0)
-    p, t = rng.uniform(size=(10, 3)), rng.uniform(size=(10, 3))
+    for n in (1, 7, 64):
+        t = rng.uniform(size=(n, 3))
+        for c in (0.25, -0.5, 1e-3):
+            L, g = oracle.mse(t + c, t)
+            assert L == pytest.approx(3.0 * c * c, rel=1e-12)
+            # the gradient of 3 c^2 along the uniform direction, shared by the 3n inputs: 6 c / (3n) each
+            assert np.allclose(g, 2.0 * c / n, rtol=1e-12, atol=0)
+    L0, g0 = oracle.mse(t, t)
+    assert L0 == 0.0 and not np.any(g0)
+
+
+def test_mse_single_ray_error():
+    """Only ray r differs, by the vector e: the loss is ||e||^2 / n (one term of the batch mean), and only
+    ray r's three inputs get a gradient."""
+    rng = np.random.default_rng(1)
+    n, r = 9, 4
+    t = rng.uniform(size=(n, 3))
+    e = np.array([0.3, -0.1, 0.2])
+    p = t.copy()
+    p[r] += e
     L, g = oracle.mse(p, t)
-    assert L == pytest.approx(((p - t) ** 2).sum() / 10, rel=1e-15)
-    assert np.allclose(g, 2 * (p - t) / 10, rtol=1e-15)
+    assert L == pytest.approx(float(e @ e) / n, rel=1e-12)
+    assert np.all(g[np.arange(n) != r] == 0.0)
+    assert np.any(g[r] != 0.0)
+
+
+def test_mse_gradient_central_differences():
+    """The returned gradient is the derivative of the returned loss: central differences of oracle.mse's
+    own loss in every input (a dropped factor 2, or a gradient normalised differently from the loss,
+    fails here).  The loss is quadratic, so the central difference is exact up to rounding."""
+    rng = np.random.default_rng(2)
+    n = 6
+    p, t = rng.uniform(size=(n, 3)), rng.uniform(size=(n, 3))
+    _, g = oracle.mse(p, t)
+    h = 1e-5
+    fd = np.zeros_like(p)
+    for i in range(n):
+        for ch in range(3):
+            pp, pm = p.copy(), p.copy()
+            pp[i, ch] += h
+            pm[i, ch] -= h
+            fd[i, ch] = (oracle.mse(pp, t)[0] - oracle.mse(pm, t)[0]) / (2 * h)
+    assert np.allclose(g, fd, rtol=1e-7, atol=1e-10)
 
 
 # ----------------------------------------------------------------------------- TV
