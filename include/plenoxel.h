@@ -417,12 +417,17 @@ plx_status plx_grid_upsample_apply(const plx_grid *grid, int32_t new_reso, const
  *     return PLX_EUNSUPPORTED without launching anything;
  *   - every GPU that loads the library holds PLX_PRUNE_NOALLOC_SCRATCH_BYTES
  *     of device memory for it until the process exits;
- *   - the first call on a device resolves the array's device address
- *     (cudaGetSymbolAddress) with that device current: make that first call
- *     before any stream capture;
+ *   - every call looks up the array's device address on the current device
+ *     (cudaGetSymbolAddress, which allocates nothing); the first call on a
+ *     device may load the library's device code there, so make that first
+ *     call before any stream capture;
  *   - all calls share the array, which keeps the last call's contents; calls
  *     whose work overlaps on the GPU (other streams or host threads on the same
  *     device) race on it and must be serialised by the caller. */
+#define PLX_PRUNE_NOALLOC_MAX_RESO 256
+#define PLX_PRUNE_NOALLOC_SCRATCH_BYTES 4325632 /* the prune workspace of a 256^3 grid */
+plx_status plx_grid_prune_noalloc(const plx_grid *grid, float tau, int32_t dilate, int32_t *d_idx_new,
+                                  float *d_rows_new, int64_t *n_keep, void *stream);
 /* ---------------------------------------------------------------- optimisation step
  *
  * One step of the optimisation (Sec. 3.5; Supp. B.1) in one call: rays for
@@ -496,11 +501,6 @@ plx_status plx_trainer_finish(plx_trainer *trainer, void *stream);
  * be NULL). */
 plx_status plx_trainer_buffers(const plx_trainer *trainer, int32_t set, float **d_origins, float **d_dirs,
                                float **d_rgb, void **d_state, size_t *state_bytes);
-
-#define PLX_PRUNE_NOALLOC_MAX_RESO 256
-#define PLX_PRUNE_NOALLOC_SCRATCH_BYTES 4325632 /* the prune workspace of a 256^3 grid */
-plx_status plx_grid_prune_noalloc(const plx_grid *grid, float tau, int32_t dilate, int32_t *d_idx_new,
-                                  float *d_rows_new, int64_t *n_keep, void *stream);
 
 #ifdef __cplusplus
 }

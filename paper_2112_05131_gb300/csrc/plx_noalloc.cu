@@ -20,8 +20,6 @@
 //     zero;
 //   * two calls whose work overlaps on the GPU (different streams, or
 //     different host threads on one device) race on it.
-#include <mutex>
-
 #include "plx_internal.cuh"
 
 namespace {
@@ -30,26 +28,16 @@ constexpr size_t kScratchBytes = PLX_PRUNE_NOALLOC_SCRATCH_BYTES;
 
 __device__ __align__(256) unsigned char g_prune_scratch[kScratchBytes];
 
-// Device address of g_prune_scratch, resolved once per device with that device
-// current.  In host code the symbol names a host-side shadow, not device memory,
-// so only the address from cudaGetSymbolAddress may be passed to a kernel.
-constexpr int kMaxDevices = 64;
-void *g_scratch_ptr[kMaxDevices] = {};
-std::mutex g_scratch_mutex;
-
+// Device address of g_prune_scratch on the current device.  In host code the symbol names a
+// host-side shadow, not device memory, so only the address from cudaGetSymbolAddress may be
+// passed to a kernel.  It is looked up on every call (no allocation, no stream work), so an
+// address never outlives the context it came from: after a device reset the module is
+// reloaded, possibly elsewhere, and the next call sees the new address.
 cudaError_t scratch_for_current_device(void **out) {
-    int dev = -1;
-    cudaError_t e = cudaGetDevice(&dev);
+    void *p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_prune_scratch);
     if (e != cudaSuccess) return e;
-    if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
-    std::lock_guard<std::mutex> lock(g_scratch_mutex);
-    if (!g_scratch_ptr[dev]) {
-        void *p = nullptr;
-        e = cudaGetSymbolAddress(&p, g_prune_scratch);
-        if (e != cudaSuccess) return e;
-        g_scratch_ptr[dev] = p;
-    }
-    *out = g_scratch_ptr[dev];
+    *out = p;
     return cudaSuccess;
 }
 

@@ -40,10 +40,7 @@ def _noalloc(lib, g, tau, dilate):
     return idx_new.cpu().numpy(), rows_new[: n.value].cpu().numpy(), n.value
 
 
-@pytest.mark.parametrize("R,frac", [(40, 0.2), (64, 0.05)])
-def test_prune_noalloc_matches_prune_with_workspace(cuda_lib, R, frac):
-    lib = cuda_lib
-    calls = [(_grid(R, frac, 1), 6.0, True), (_grid(R, frac * 2, 2), 3.5, False)]  # two calls in a row
+def _check_against_workspace_prune(lib, calls):
     for g, tau, dilate in calls:
         idx_a, rows_a, n_a = _noalloc(lib, g, tau, dilate)
         ref = g.prune(tau, dilate)  # plx_grid_prune_count + plx_grid_prune_apply with a workspace
@@ -52,6 +49,20 @@ def test_prune_noalloc_matches_prune_with_workspace(cuda_lib, R, frac):
         assert np.array_equal(idx_a, ref.idx.cpu().numpy())
         assert np.array_equal(rows_a, ref.rows.cpu().numpy())
         g.check()
+
+
+@pytest.mark.parametrize("R,frac", [(40, 0.2), (64, 0.05)])
+def test_prune_noalloc_matches_prune_with_workspace(cuda_lib, R, frac):
+    calls = [(_grid(R, frac, 1), 6.0, True), (_grid(R, frac * 2, 2), 3.5, False)]  # two calls in a row
+    _check_against_workspace_prune(cuda_lib, calls)
+
+
+def test_prune_noalloc_at_its_limit_then_smaller(cuda_lib):
+    """A 256^3 grid, whose scratch layout fills the whole fixed array, then smaller grids: each later call
+    reads only what it wrote itself, so the larger call's leftovers beyond the small layouts change
+    nothing."""
+    calls = [(_grid(256, 0.01, 3), 6.0, True), (_grid(64, 0.05, 4), 5.0, True), (_grid(40, 0.2, 5), 3.5, False)]
+    _check_against_workspace_prune(cuda_lib, calls)
 
 
 def test_prune_noalloc_refuses_grids_beyond_its_fixed_scratch(cuda_lib):
