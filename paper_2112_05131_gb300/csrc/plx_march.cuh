@@ -14,73 +14,104 @@ namespace plx {
 constexpr int kGatherBlocks = 4;
 
 // --------------------------------------------------------------------------- per-ray setup
+// Sample s of a ray lies at t_s = t_near + s delta (Eq. 1's fixed step), i.e. at grid coordinates
+// g0 + s st per axis, with g0 = (o - lo + t_near d) / h the point where the ray enters the box and
+// st = delta d / h the step between samples.  Both are double-floats formed once per ray, so a
+// sample's coordinates cost one exact product and one double-float addition.
 struct __align__(16) RaySetup {  // 128 bytes: the training march keeps one per ray in its state
-    DF A[3];       // origin minus box corner, exact as a double-float
-    float d[3];    // unit direction as given
-    DF tn, tf;     // clipped parameter range
-    float og[3];   // FP32 grid-coordinate origin and direction, for the cheap candidate test
-    float dg[3];
+    DF g0[3];      // grid coordinates at t_near
+    DF st[3];      // grid-coordinate step between consecutive samples
     float Y[9];    // SH basis at the direction
-    float feps;    // bound on |FP32 - exact| grid coordinate of any sample of the ray (see test_candidate)
-    int hit;       // the ray meets the box
-    int s_lo, s_hi;  // samples outside [s_lo, s_hi) lie in empty cells (outside the box of non-empty cells)
+    float feps;    // bound on |FP32 - exact| grid coordinate of any candidate of the ray (see test_candidate)
+    int hit;       // the ray meets the box (1), misses it (0); < 0: no ray (a pixel outside its image)
+    int s_lo, s_hi;  // samples outside [s_lo, s_hi) are past t_far or lie in empty cells
+    int inner;     // every candidate's FP32 coordinate is inside the grid by more than feps on every axis
+    float pad_[6];
 };
 static_assert(sizeof(RaySetup) == 128, "RaySetup layout");
+
+// t_s = t_near + s * delta as a double-float (s * delta_hi is exact for s < 2^24).
+__device__ __forceinline__ DF sample_t(DF tn, const RenderParams &p, int s) {
+    DF sd = df_two_prod((float)s, p.delta);
+    sd.lo = fmaf((float)s, p.delta_lo, sd.lo);
+    return df_add(tn, sd);
+}
 
 __device__ __forceinline__ RaySetup ray_setup_od(const GridView &g, const RenderParams &p, const float o[3],
                                                  const float d[3]) {
     RaySetup rs;
+    DF tn, tf;
+    rs.hit = clip_box(g, o, d, tn, tf);
+    sh_basis(d, rs.Y);
+    rs.s_lo = rs.s_hi = 0;
+    rs.inner = 0;
+    rs.feps = 0.0f;
 #pragma unroll
-    for (int a = 0; a < 3; ++a) rs.d[a] = d[a];
-    rs.hit = clip_box(g, o, rs.d, rs.tn, rs.tf);
+    for (int q = 0; q < 6; ++q) rs.pad_[q] = 0.0f;
+    if (!rs.hit) {
+#pragma unroll
+        for (int a = 0; a < 3; ++a) rs.g0[a] = rs.st[a] = DF{0.0f, 0.0f};
+        return rs;
+    }
+    const DF del = {p.delta, p.delta_lo};
+    float gmax = 0.0f, smax = 0.0f;
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
-        rs.A[a] = df_two_sum(o[a], -g.lo[a]);
-        rs.og[a] = (o[a] - g.lo[a]) * g.inv_h[a];
-        rs.dg[a] = rs.d[a] * g.inv_h[a];
+        const DF ih = {g.inv_h[a], g.inv_h_lo[a]};
+        rs.g0[a] = df_mul(df_add(df_two_sum(o[a], -g.lo[a]), df_mul_f(tn, d[a])), ih);
+        rs.st[a] = df_mul(df_mul_f(del, d[a]), ih);
+        gmax = fmaxf(gmax, fabsf(rs.g0[a].hi));
+        smax = fmaxf(smax, fabsf(rs.st[a].hi));
     }
-    sh_basis(rs.d, rs.Y);
-    // The cheap test's coordinate x32 = fma(t32, dg, og) with t32 = fma(s, delta, t_near.hi) differs from
-    // the exact (o - lo + t d) / h by at most u (inv_h (3 |o - lo| + 5 t) + |x|), u = 2^-24: og carries
-    // 3 roundings, dg 2, t32 3 (t_near.lo, delta_lo, the fma), and the final fma 1.  Over the ray
-    // t <= t_far and |x| <= R; the margin is that bound plus a quarter.
-    float om = 0.0f, ih = 0.0f;
-#pragma unroll
-    for (int a = 0; a < 3; ++a) {
-        om = fmaxf(om, fabsf(o[a] - g.lo[a]));
-        ih = fmaxf(ih, g.inv_h[a]);
-    }
-    const float tmax = rs.hit ? fabsf(rs.tf.hi) : 0.0f;
-    rs.feps = 1.25f * 5.9604645e-8f * (ih * (3.0f * om + 5.0f * tmax) + (float)g.R);
+    // s_end: the number of samples with t_s < t_far, decided in double-float (the FP32 estimate is
+    // within one sample of it); samples beyond max_chunks * 32 do not exist.
+    const int cap = p.max_chunks * 32;
+    int k = (int)fminf(fmaxf(ceilf((tf.hi - tn.hi) / p.delta), 0.0f), (float)cap);
+    for (int it = 0; it < 8 && k > 0 && !df_lt(sample_t(tn, p, k - 1), tf); ++it) --k;
+    for (int it = 0; it < 8 && k < cap && df_lt(sample_t(tn, p, k), tf); ++it) ++k;
+    const int s_end = k;
+    // The cheap test's coordinate x32 = fma(s, st.hi, g0.hi) differs from the exact g0 + s st by at most
+    // u |x32| + |g0.lo| + s |st.lo| <= u (2 |g0| + 2 s |st|) with u = 2^-24 (one rounding; the lo parts
+    // are at most u of their hi parts).  Candidates, and the last sample of a candidate group, have
+    // s < s_end + 8; the margin is that bound plus a quarter.
+    rs.feps = 1.25f * 5.9604645e-8f * (2.0f * gmax + 2.0f * (float)(s_end + 8) * smax);
     // The candidate range: every cell with an occupied corner lies in the box of cells [lo, hi] (grid
     // coordinates [lo, hi + 1]); a sample whose coordinate is outside that box widened by one cell on
-    // every side (far more than the FP32 error) is in an empty cell.  Slab test in FP32, then sample
-    // indices widened by two on each side; samples beyond max_chunks * 32 do not exist.
-    rs.s_lo = 0;
-    rs.s_hi = 0;
-    if (rs.hit) {
-        float t0 = rs.tn.hi, t1 = rs.tf.hi;
-        bool any = true;
+    // every side (far more than the FP32 error) is in an empty cell.  Slab test in FP32 on the sample
+    // index, widened by two samples on each side, within [0, s_end).
+    float s0 = 0.0f, s1 = (float)s_end;
+    bool any = s_end > 0;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        const float blo = (float)(g.R - 1 - __ldg(g.occ_box + a)) - 1.0f;
+        const float bhi = (float)__ldg(g.occ_box + 3 + a) + 2.0f;
+        any = any && blo <= bhi;
+        if (rs.st[a].hi == 0.0f) {
+            any = any && rs.g0[a].hi >= blo && rs.g0[a].hi <= bhi;
+        } else {
+            const float inv = 1.0f / rs.st[a].hi;
+            const float ta = (blo - rs.g0[a].hi) * inv, tb = (bhi - rs.g0[a].hi) * inv;
+            s0 = fmaxf(s0, fminf(ta, tb));
+            s1 = fminf(s1, fmaxf(ta, tb));
+        }
+    }
+    if (any && s0 <= s1) {
+        rs.s_lo = (int)fminf(fmaxf(floorf(s0) - 2.0f, 0.0f), (float)s_end);
+        rs.s_hi = (int)fminf(fmaxf(ceilf(s1) + 3.0f, 0.0f), (float)s_end);
+    }
+    // Inner: the FP32 coordinates of the first and last candidates lie in [3 feps, R - 1 - 3 feps] on every
+    // axis; the exact points between them are on that segment, so every candidate's FP32 coordinate is in
+    // [feps, R - 1 - feps]: its floor is a valid cell and no clamp applies.
+    if (rs.s_lo < rs.s_hi) {
+        const float lo3 = 3.0f * rs.feps, hi3 = (float)(g.R - 1) - 3.0f * rs.feps;
+        bool in = true;
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
-            const float blo = (float)(g.R - 1 - __ldg(g.occ_box + a)) - 1.0f;
-            const float bhi = (float)__ldg(g.occ_box + 3 + a) + 2.0f;
-            any = any && blo <= bhi;
-            if (rs.dg[a] == 0.0f) {
-                any = any && rs.og[a] >= blo && rs.og[a] <= bhi;
-            } else {
-                const float ta = (blo - rs.og[a]) / rs.dg[a], tb = (bhi - rs.og[a]) / rs.dg[a];
-                t0 = fmaxf(t0, fminf(ta, tb));
-                t1 = fminf(t1, fmaxf(ta, tb));
-            }
+            const float xa = fmaf((float)rs.s_lo, rs.st[a].hi, rs.g0[a].hi);
+            const float xb = fmaf((float)(rs.s_hi - 1), rs.st[a].hi, rs.g0[a].hi);
+            in = in && fminf(xa, xb) >= lo3 && fmaxf(xa, xb) <= hi3;
         }
-        if (any && t0 <= t1) {
-            const float sa = floorf((t0 - rs.tn.hi) / p.delta) - 2.0f;
-            const float sb = ceilf((t1 - rs.tn.hi) / p.delta) + 3.0f;
-            const float smax = (float)(p.max_chunks * 32);
-            rs.s_lo = (int)fminf(fmaxf(sa, 0.0f), smax);
-            rs.s_hi = (int)fminf(fmaxf(sb, 0.0f), smax);
-        }
+        rs.inner = in ? 1 : 0;
     }
     return rs;
 }
@@ -96,20 +127,14 @@ __device__ __forceinline__ RaySetup ray_setup(const GridView &g, const RenderPar
     return ray_setup_od(g, p, o, d);
 }
 
-// t_s = t_near + s * delta as a double-float (s * delta_hi is exact for s < 2^24).
-__device__ __forceinline__ DF sample_t(const RaySetup &rs, const RenderParams &p, int s) {
-    DF sd = df_two_prod((float)s, p.delta);
-    sd.lo = fmaf((float)s, p.delta_lo, sd.lo);
-    return df_add(rs.tn, sd);
-}
-
-// Grid coordinates of the point at parameter t: ((o - lo) + t d) / h per axis.
-__device__ __forceinline__ void sample_coords(const GridView &g, const RaySetup &rs, DF t, DF gc[3]) {
+// Grid coordinates of sample s: g0 + s st per axis, as double-floats (s st.hi is exact).
+__device__ __forceinline__ void coords_at(const RaySetup &rs, int s, DF gc[3]) {
+    const float sf = (float)s;
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
-        DF td = df_two_prod(t.hi, rs.d[a]);
-        td.lo = fmaf(t.lo, rs.d[a], td.lo);
-        gc[a] = df_mul(df_add(rs.A[a], td), DF{g.inv_h[a], g.inv_h_lo[a]});
+        DF q = df_two_prod(sf, rs.st[a].hi);
+        q.lo = fmaf(sf, rs.st[a].lo, q.lo);
+        gc[a] = df_add(rs.g0[a], q);
     }
 }
 
@@ -124,6 +149,31 @@ __device__ __forceinline__ uint4 ldg4_pinned(const uint4 *p) {
     uint4 v;
     asm volatile("ld.global.nc.v4.u32 {%0, %1, %2, %3}, [%4];" : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w) : "l"(p));
     return v;
+}
+
+// 256-bit read-only loads (sm_100 and later): eight 32-bit values from a 32-byte aligned address in one
+// instruction, so a 128-byte F32 row takes four loads and a 64-byte BF16-SH row two.
+struct F8 {
+    float v[8];
+};
+struct U8 {
+    uint32_t v[8];
+};
+__device__ __forceinline__ F8 ldg8_pinned(const float *p) {
+    F8 r;
+    asm volatile("ld.global.nc.v8.f32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+                 : "=f"(r.v[0]), "=f"(r.v[1]), "=f"(r.v[2]), "=f"(r.v[3]), "=f"(r.v[4]), "=f"(r.v[5]), "=f"(r.v[6]),
+                   "=f"(r.v[7])
+                 : "l"(p));
+    return r;
+}
+__device__ __forceinline__ U8 ldg8_pinned(const uint32_t *p) {
+    U8 r;
+    asm volatile("ld.global.nc.v8.u32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+                 : "=r"(r.v[0]), "=r"(r.v[1]), "=r"(r.v[2]), "=r"(r.v[3]), "=r"(r.v[4]), "=r"(r.v[5]), "=r"(r.v[6]),
+                   "=r"(r.v[7])
+                 : "l"(p));
+    return r;
 }
 
 // Packed FP32 arithmetic (fma.rn.f32x2): one instruction computes two independent fmaf, each
@@ -162,51 +212,66 @@ __device__ __forceinline__ bool gather_sample(const GridView &g, int form, const
     // every corner's row is requested before any is used: one memory round trip per
     // chunk instead of eight (a NULL corner contributes w * 0, i.e. nothing)
     if (form == PLX_SH_F32) {
-        float4 v[8][7];
+        // four 256-bit loads per row (the last holds SH 23..26 and the row's 4 pad floats)
+        F8 v[8][4];
 #pragma unroll
         for (int k = 0; k < 8; ++k) {
-            const float4 *p = reinterpret_cast<const float4 *>(g.rows + (int64_t)max(r[k], 0) * kRowF);
+            const float *p = g.rows + (int64_t)max(r[k], 0) * kRowF;
 #pragma unroll
-            for (int q = 0; q < 7; ++q) v[k][q] = r[k] >= 0 ? ldg4_pinned(p + q) : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
-        }
-        // an empty volatile use of every loaded value, after all the loads: no FMA can be
-        // scheduled between two loads, so all 56 requests are in flight together
+            for (int q = 0; q < 4; ++q) {
+                if (r[k] >= 0) {
+                    v[k][q] = ldg8_pinned(p + 8 * q);
+                } else {
 #pragma unroll
-        for (int k = 0; k < 8; ++k)
-#pragma unroll
-            for (int q = 0; q < 7; ++q)
-                asm volatile("" : "+f"(v[k][q].x), "+f"(v[k][q].y), "+f"(v[k][q].z), "+f"(v[k][q].w));
-#pragma unroll
-        for (int k = 0; k < 8; ++k) {
-            // scalar FMAs here: the packed form needs register pairs, and at the FP32 render kernels'
-            // register cap it spilled more and measured slower
-            const float w = corner_weight(c.f, k);
-#pragma unroll
-            for (int q = 0; q < 7; ++q) {
-                acc[4 * q + 0] = fmaf(w, v[k][q].x, acc[4 * q + 0]);
-                acc[4 * q + 1] = fmaf(w, v[k][q].y, acc[4 * q + 1]);
-                acc[4 * q + 2] = fmaf(w, v[k][q].z, acc[4 * q + 2]);
-                acc[4 * q + 3] = fmaf(w, v[k][q].w, acc[4 * q + 3]);
+                    for (int e = 0; e < 8; ++e) v[k][q].v[e] = 0.0f;
+                }
             }
         }
-    } else {
-        uint4 v[8][4];
+        // an empty volatile use of every loaded value, after all the loads: no FMA can be
+        // scheduled between two loads, so all 32 requests are in flight together
+#pragma unroll
+        for (int k = 0; k < 8; ++k)
+#pragma unroll
+            for (int q = 0; q < 4; ++q)
+#pragma unroll
+                for (int e = 0; e < 8; e += 4)
+                    asm volatile("" : "+f"(v[k][q].v[e]), "+f"(v[k][q].v[e + 1]), "+f"(v[k][q].v[e + 2]),
+                                 "+f"(v[k][q].v[e + 3]));
 #pragma unroll
         for (int k = 0; k < 8; ++k) {
-            const uint4 *p = reinterpret_cast<const uint4 *>(g.rows_h + (int64_t)max(r[k], 0) * kRowH);
+            const float w = corner_weight(c.f, k);
 #pragma unroll
-            for (int q = 0; q < 4; ++q) v[k][q] = r[k] >= 0 ? ldg4_pinned(p + q) : make_uint4(0u, 0u, 0u, 0u);
+            for (int q = 0; q < kNV; ++q) acc[q] = fmaf(w, v[k][q >> 3].v[q & 7], acc[q]);
+        }
+    } else {
+        U8 v[8][2];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            const uint32_t *p = reinterpret_cast<const uint32_t *>(g.rows_h + (int64_t)max(r[k], 0) * kRowH);
+#pragma unroll
+            for (int q = 0; q < 2; ++q) {
+                if (r[k] >= 0) {
+                    v[k][q] = ldg8_pinned(p + 8 * q);
+                } else {
+#pragma unroll
+                    for (int e = 0; e < 8; ++e) v[k][q].v[e] = 0u;
+                }
+            }
         }
 #pragma unroll
         for (int k = 0; k < 8; ++k)
 #pragma unroll
-            for (int q = 0; q < 4; ++q) asm volatile("" : "+r"(v[k][q].x), "+r"(v[k][q].y), "+r"(v[k][q].z), "+r"(v[k][q].w));
+            for (int q = 0; q < 2; ++q)
+#pragma unroll
+                for (int e = 0; e < 8; e += 4)
+                    asm volatile("" : "+r"(v[k][q].v[e]), "+r"(v[k][q].v[e + 1]), "+r"(v[k][q].v[e + 2]),
+                                 "+r"(v[k][q].v[e + 3]));
 #pragma unroll
         for (int k = 0; k < 8; ++k) {
             const float w = corner_weight(c.f, k);
-            const uint32_t wd[16] = {v[k][0].x, v[k][0].y, v[k][0].z, v[k][0].w, v[k][1].x, v[k][1].y,
-                                     v[k][1].z, v[k][1].w, v[k][2].x, v[k][2].y, v[k][2].z, v[k][2].w,
-                                     v[k][3].x, v[k][3].y, v[k][3].z, v[k][3].w};
+            uint32_t wd[16];
+#pragma unroll
+            for (int e = 0; e < 16; ++e) wd[e] = v[k][e >> 3].v[e & 7];
             const uint64_t ww = f32x2(w, w);
             acc[0] = fmaf(w, __uint_as_float(wd[0]), acc[0]);
             // SH pairs (2i, 2i+1) share word 1 + i: low half, then high half
@@ -295,57 +360,34 @@ __device__ __forceinline__ Composite composite(float sig, bool valid, float Tc, 
 constexpr int kCand = 8;    // candidates per lane per refill
 constexpr int kRing = 512;  // ring capacity >= 31 + 32 kCand, a power of two
 
-struct Cand {
-    bool valid, occ;
-};
-
-// Is sample s inside the clipped ray (valid), and is its cell non-empty (occ)?
-// The answer must equal the double-float one exactly (it decides which samples
-// are marched).  Plain FP32 coordinates are within rs.feps of the exact ones
-// (the bound derived in ray_setup_od); a candidate whose FP32 coordinate lies
-// within rs.feps of a cell face or of the box on any axis, or whose t lies
-// within kTEps of t_far, is re-evaluated in double-float, so the cheap path is
-// taken only where both agree.
-
-__device__ __forceinline__ Cand test_candidate(const GridView &g, const RaySetup &rs, const RenderParams &p, int s) {
-    Cand c;
-    c.occ = false;
-    c.valid = false;
-    if (s >= rs.s_hi) return c;  // beyond the non-empty box (or past max_chunks * 32): no more samples
-    if (s < rs.s_lo) {            // before the non-empty box: valid and empty
-        c.valid = true;
-        return c;
-    }
-    const float t32 = fmaf((float)s, p.delta, rs.tn.hi);
-    const float kTEps = 1e-5f * (fabsf(rs.tf.hi) + 1.0f);
-    bool exact = fabsf(t32 - rs.tf.hi) <= kTEps;
-    if (!exact && t32 > rs.tf.hi) return c;  // clearly past t_far
+// Is the cell of sample s (s_lo <= s < s_hi: every such sample is before t_far) non-empty?  The answer
+// must equal the double-float one exactly (it decides which samples are marched).  Plain FP32
+// coordinates are within rs.feps of the exact ones (the bound derived in ray_setup_od); a candidate whose
+// FP32 coordinate lies within rs.feps of a cell face, or (unless the ray is inner) of the box, on any axis
+// is re-evaluated in double-float, so the cheap path is taken only where both agree.
+template <bool INNER>
+__device__ __forceinline__ bool test_candidate(const GridView &g, const RaySetup &rs, int s) {
+    const float sf = (float)s;
+    bool exact = false;
     int b[3];
-    // near a cell face: the fraction within feps of 0 or 1; near the box: x within feps of 0 or R-1
     const float half = 0.5f * (float)(g.R - 1);
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
-        const float x = fmaf(t32, rs.dg[a], rs.og[a]);
+        const float x = fmaf(sf, rs.st[a].hi, rs.g0[a].hi);
         const float fl = floorf(x);
-        exact = exact || fabsf((x - fl) - 0.5f) > 0.5f - rs.feps || fabsf(x - half) > half - rs.feps;
+        exact = exact || fabsf((x - fl) - 0.5f) > 0.5f - rs.feps;
+        if (!INNER) exact = exact || fabsf(x - half) > half - rs.feps;
         b[a] = (int)fl;
     }
     if (exact) {
-        const DF t = sample_t(rs, p, s);
-        c.valid = df_lt(t, rs.tf);
-        if (c.valid) {
-            DF gc[3];
-            sample_coords(g, rs, t, gc);
-            c.occ = cell_occupied(g, locate(g, gc).base);
-        }
-        return c;
+        DF gc[3];
+        coords_at(rs, s, gc);
+        return cell_occupied(g, locate(g, gc).base);
     }
-    c.valid = true;
     // here 0 <= b < R - 1 on every axis; the linear id fits 32 bits below R = 1291
     const int64_t base = g.R <= 1290 ? (int64_t)((b[0] * g.R + b[1]) * g.R + b[2])
                                      : ((int64_t)b[0] * g.R + b[1]) * g.R + b[2];
-    c.occ = cell_occupied(g, base);
-    return c;
+    return cell_occupied(g, base);
 }
 
 // --------------------------------------------------------------------------- coarse skipping
@@ -358,20 +400,18 @@ static_assert(32 * kCand == 32 * kGroup, "a round is one group per lane");
 
 // Can a sample with index in [s0, s0 + kGroup) lie in a cell with an occupied corner?  Never false
 // when one does.  The samples lie on the segment between the first and the last, whose FP32 grid
-// coordinates are within rs.feps of the exact ones (the bound holds a fortiori a few samples past
-// t_far, where the extra error is ~1e-6 of a cell against the bound's 25% slack), so their cells
+// coordinates are within rs.feps of the exact ones (the bound covers s < s_end + 8), so their cells
 // lie in the box of cells of the two endpoints widened by feps, clamped as locate() clamps; the
 // coarse bits of that box's blocks (at most 2 per axis; a wider box answers yes) decide.
-__device__ __forceinline__ bool group_live(const GridView &g, const RaySetup &rs, const RenderParams &p, int s0) {
+__device__ __forceinline__ bool group_live(const GridView &g, const RaySetup &rs, int s0) {
     if (s0 >= rs.s_hi) return false;
-    const float ta = fmaf((float)s0, p.delta, rs.tn.hi);
-    const float tb = fmaf((float)(s0 + kGroup - 1), p.delta, rs.tn.hi);
+    const float sa = (float)s0, sb = (float)(s0 + kGroup - 1);
     const float cmax = (float)(g.R - 2);
     int lo[3], hi[3];
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
-        const float xa = fmaf(ta, rs.dg[a], rs.og[a]);
-        const float xb = fmaf(tb, rs.dg[a], rs.og[a]);
+        const float xa = fmaf(sa, rs.st[a].hi, rs.g0[a].hi);
+        const float xb = fmaf(sb, rs.st[a].hi, rs.g0[a].hi);
         const float c0 = fminf(fmaxf(floorf(fminf(xa, xb) - rs.feps), 0.0f), cmax);
         const float c1 = fminf(fmaxf(floorf(fmaxf(xa, xb) + rs.feps), 0.0f), cmax);
         lo[a] = (int)c0 >> kBlockLog;
@@ -387,16 +427,23 @@ __device__ __forceinline__ bool group_live(const GridView &g, const RaySetup &rs
     return false;
 }
 
-// Tests the candidates of one round starting at sample `first` (candidate 32 j + lane in c[j]), the
-// ones in skipped groups answering (invalid, empty), and returns the ballot of live groups.
-__device__ __forceinline__ unsigned test_round(const GridView &g, const RaySetup &rs, const RenderParams &p, int first,
-                                               int end, int lane, Cand c[kCand]) {
-    const unsigned live = __ballot_sync(kFull, group_live(g, rs, p, first + kGroup * lane));
+// Tests the candidates of one round starting at sample `first` (candidate 32 j + lane in occ[j]; those
+// at or beyond `end` <= s_hi, or in skipped groups, answer empty) and returns the ballot of live groups.
+__device__ __forceinline__ unsigned test_round(const GridView &g, const RaySetup &rs, int first, int end, int lane,
+                                               bool occ[kCand]) {
+    const unsigned live = __ballot_sync(kFull, group_live(g, rs, first + kGroup * lane));
+    if (rs.inner) {  // uniform
 #pragma unroll
-    for (int j = 0; j < kCand; ++j) {
-        const int s = first + 32 * j + lane;
-        c[j].valid = c[j].occ = false;
-        if (((live >> (4 * j + (lane >> 3))) & 1u) && s < end) c[j] = test_candidate(g, rs, p, s);
+        for (int j = 0; j < kCand; ++j) {
+            const int s = first + 32 * j + lane;
+            occ[j] = ((live >> (4 * j + (lane >> 3))) & 1u) && s < end && test_candidate<true>(g, rs, s);
+        }
+    } else {
+#pragma unroll
+        for (int j = 0; j < kCand; ++j) {
+            const int s = first + 32 * j + lane;
+            occ[j] = ((live >> (4 * j + (lane >> 3))) & 1u) && s < end && test_candidate<false>(g, rs, s);
+        }
     }
     return live;
 }
@@ -410,16 +457,15 @@ struct Stream {
 
 // Append occupied candidates until 32 are queued or the ray has no candidates left (none at or
 // beyond s_hi).
-__device__ __forceinline__ void refill(const GridView &g, const RaySetup &rs, const RenderParams &p, int *ring,
-                                       Stream &st, int lane) {
+__device__ __forceinline__ void refill(const GridView &g, const RaySetup &rs, int *ring, Stream &st, int lane) {
     const unsigned lt = (1u << lane) - 1u;
     while (st.tail - st.head < 32 && !st.exhausted) {
-        Cand c[kCand];
-        if (test_round(g, rs, p, st.next, rs.s_hi, lane, c)) {  // uniform
+        bool occ[kCand];
+        if (test_round(g, rs, st.next, rs.s_hi, lane, occ)) {  // uniform
 #pragma unroll
             for (int j = 0; j < kCand; ++j) {
-                const unsigned m = __ballot_sync(kFull, c[j].occ);
-                if (c[j].occ) ring[(st.tail + __popc(m & lt)) & (kRing - 1)] = st.next + 32 * j + lane;
+                const unsigned m = __ballot_sync(kFull, occ[j]);
+                if (occ[j]) ring[(st.tail + __popc(m & lt)) & (kRing - 1)] = st.next + 32 * j + lane;
                 st.tail += __popc(m);
             }
         }
@@ -438,19 +484,19 @@ __device__ __forceinline__ int take_chunk(const int *ring, Stream &st, int lane,
     return cnt;
 }
 
-// The occupied samples with index in [first, end), in order, into buf (at most 32 are kept).
-__device__ __forceinline__ int scan_range(const GridView &g, const RaySetup &rs, const RenderParams &p, int first,
-                                          int end, int *buf, int lane) {
+// The occupied samples with index in [first, end) (end <= s_hi), in order, into buf (at most 32 are kept).
+__device__ __forceinline__ int scan_range(const GridView &g, const RaySetup &rs, int first, int end, int *buf,
+                                          int lane) {
     const unsigned lt = (1u << lane) - 1u;
     int cnt = 0;
     for (int base = first; base < end; base += 32 * kCand) {
-        Cand c[kCand];
-        if (!test_round(g, rs, p, base, end, lane, c)) continue;  // uniform
+        bool occ[kCand];
+        if (!test_round(g, rs, base, end, lane, occ)) continue;  // uniform
 #pragma unroll
         for (int j = 0; j < kCand; ++j) {
-            const unsigned m = __ballot_sync(kFull, c[j].occ);
+            const unsigned m = __ballot_sync(kFull, occ[j]);
             const int pos = cnt + __popc(m & lt);
-            if (c[j].occ && pos < 32) buf[pos] = base + 32 * j + lane;
+            if (occ[j] && pos < 32) buf[pos] = base + 32 * j + lane;
             cnt += __popc(m);
         }
     }

@@ -106,11 +106,23 @@ cudaError_t launch_mse_grad(const float *rgb, const float *target, int64_t n, fl
 
 // --------------------------------------------------------------------------- forward
 constexpr int kFwdWarps = 4;
-// Resident CTAs per SM the one-warp-per-ray render kernels are compiled for, per row form: the
+// Resident warps per SM the one-warp-per-ray render kernels are compiled for, per row form: the
 // register cap it implies trades a few spilled bytes for more warps to hide the gathers' latency.
-constexpr int kFwdBlocksF32 = 6;
-constexpr int kFwdBlocksBF16 = 5;
-constexpr int fwd_blocks(int form) { return form == PLX_SH_BF16 ? kFwdBlocksBF16 : kFwdBlocksF32; }
+constexpr int kFwdWarpsSMF32 = 24;
+constexpr int kFwdWarpsSMBF16 = 20;
+constexpr int fwd_blocks(int form) { return (form == PLX_SH_BF16 ? kFwdWarpsSMBF16 : kFwdWarpsSMF32) / kFwdWarps; }
+// Rays per warp in the render kernels: lanes 0 .. kRayBatch-1 set up that many consecutive rays at once
+// (double-float clip and anchor, SH basis, candidate range) into shared memory, and the warp then marches
+// them one after another, so the setup's cost is shared by kRayBatch rays instead of repeated in every
+// lane of every ray's warp.
+constexpr int kRayBatch = 4;
+// The CTA's kFwdWarps * kRayBatch consecutive rays are dealt to its warps in turn (ray r of warp w is the
+// CTA's ray r kFwdWarps + w), so that neighbouring rays, which cost about the same, are spread over the
+// warps and the CTA's warps finish together.
+constexpr bool kDealRays = true;
+__device__ __forceinline__ int64_t batch_ray(int64_t cta_ray0, int wid, int r) {
+    return cta_ray0 + (kDealRays ? (int64_t)r * kFwdWarps + wid : (int64_t)wid * kRayBatch + r);
+}
 
 // The forward march of one ray by one warp (Eq. 1 over the compacted samples, chunk by chunk):
 // returns, in every lane, the composited colour without the background and the final
@@ -120,10 +132,10 @@ __device__ __forceinline__ void march_forward(const GridView &g, const RenderPar
                                               int lane, float C[3], float &Tc) {
     C[0] = C[1] = C[2] = 0.0f;
     Tc = 1.0f;  // transmittance before the current chunk
-    if (rs.hit) {
+    if (rs.hit > 0) {
         Stream st = {rs.s_lo, rs.s_lo, rs.s_lo, false};
         for (;;) {
-            refill(g, rs, p, ring, st, lane);
+            refill(g, rs, ring, st, lane);
             int s;
             const int cnt = take_chunk(ring, st, lane, s);
             if (cnt == 0) break;
@@ -131,7 +143,7 @@ __device__ __forceinline__ void march_forward(const GridView &g, const RenderPar
             float sig = 0.0f, col[3] = {0.0f, 0.0f, 0.0f};
             if (valid) {
                 DF gc[3];
-                sample_coords(g, rs, sample_t(rs, p, s), gc);
+                coords_at(rs, s, gc);
                 float acc[kNV];
                 int32_t rr[8];
                 float ff[3];
@@ -163,25 +175,34 @@ __global__ void __launch_bounds__(kFwdWarps * 32, fwd_blocks(FORM)) render_fwd_k
                                                                     RenderParams p, float *__restrict__ rgb,
                                                                     float *__restrict__ T_out) {
     __shared__ int s_ring[kFwdWarps][kRing];
+    __shared__ RaySetup s_rs[kFwdWarps][kRayBatch];
     const int lane = threadIdx.x & 31;
     const int wid = threadIdx.x >> 5;
-    const int64_t ray = (int64_t)blockIdx.x * kFwdWarps + wid;
-    if (ray >= n) return;  // uniform per warp
-    const RaySetup rs = ray_setup(g, p, ro, rd, ray);
-    float C[3], Tc;
-    march_forward<FORM>(g, p, rs, s_ring[wid], lane, C, Tc);
-    if (lane == 0) {
-        rgb[3 * ray + 0] = fmaf(Tc, p.bg[0], C[0]);
-        rgb[3 * ray + 1] = fmaf(Tc, p.bg[1], C[1]);
-        rgb[3 * ray + 2] = fmaf(Tc, p.bg[2], C[2]);
-        if (T_out) T_out[ray] = Tc;
+    const int64_t cta_ray0 = (int64_t)blockIdx.x * kFwdWarps * kRayBatch;
+    if (lane < kRayBatch) {
+        const int64_t ray = batch_ray(cta_ray0, wid, lane);
+        if (ray < n) s_rs[wid][lane] = ray_setup(g, p, ro, rd, ray);
+    }
+    __syncwarp();
+    for (int r = 0; r < kRayBatch; ++r) {
+        const int64_t ray = batch_ray(cta_ray0, wid, r);
+        if (ray >= n) break;  // uniform per warp
+        float C[3], Tc;
+        march_forward<FORM>(g, p, s_rs[wid][r], s_ring[wid], lane, C, Tc);
+        if (lane == 0) {
+            rgb[3 * ray + 0] = fmaf(Tc, p.bg[0], C[0]);
+            rgb[3 * ray + 1] = fmaf(Tc, p.bg[1], C[1]);
+            rgb[3 * ray + 2] = fmaf(Tc, p.bg[2], C[2]);
+            if (T_out) T_out[ray] = Tc;
+        }
     }
 }
 
 cudaError_t launch_render(const GridView &g, const float *o, const float *d, int64_t n,
                           const RenderParams &p, float *rgb, float *T_end, cudaStream_t s) {
     if (n == 0) return cudaSuccess;
-    const int64_t blocks = (n + kFwdWarps - 1) / kFwdWarps;
+    const int64_t per_block = (int64_t)kFwdWarps * kRayBatch;
+    const int64_t blocks = (n + per_block - 1) / per_block;
     if (g.form == PLX_SH_F32)
         render_fwd_kernel<PLX_SH_F32><<<(unsigned)blocks, kFwdWarps * 32, 0, s>>>(g, o, d, n, p, rgb, T_end);
     else
@@ -191,10 +212,11 @@ cudaError_t launch_render(const GridView &g, const float *o, const float *d, int
 
 // --------------------------------------------------------------------------- serving
 // plx_render_tiles: image requests of several resident scenes in one launch.
-// Each tile is 16x16 pixels of one request; warp w renders pixel (w mod 256)
-// of tile w / 256, generating its ray in-kernel with the same code as
-// plx_gen_rays and marching it with the same code as plx_render, so a pixel's
-// value does not depend on what else is in the launch.
+// Each tile is 16x16 pixels of one request; ray w of the launch is pixel (w mod 256)
+// of tile w / 256.  Each warp takes kRayBatch consecutive rays: its lanes generate
+// them in-kernel with the same code as plx_gen_rays and set them up, and the warp
+// marches them with the same code as plx_render, so a pixel's value does not
+// depend on what else is in the launch.
 struct SceneTable {
     GridView g[PLX_TILES_MAX_SCENES];
     RenderParams p[PLX_TILES_MAX_SCENES];
@@ -205,31 +227,49 @@ __global__ void __launch_bounds__(kFwdWarps * 32, fwd_blocks(FORM)) render_tiles
     const __grid_constant__ SceneTable tab, int n_scenes, const float *__restrict__ cams, int n_cams,
     const plx_tile *__restrict__ tiles, int64_t n_rays) {
     __shared__ int s_ring[kFwdWarps][kRing];
+    __shared__ RaySetup s_rs[kFwdWarps][kRayBatch];
     const int lane = threadIdx.x & 31;
     const int wid = threadIdx.x >> 5;
-    const int64_t ray = (int64_t)blockIdx.x * kFwdWarps + wid;
-    if (ray >= n_rays) return;  // uniform per warp
-    const plx_tile tile = tiles[ray / (PLX_TILE_W * PLX_TILE_H)];
-    const int px = (int)(ray % (PLX_TILE_W * PLX_TILE_H));
-    const int x = tile.x0 + px % PLX_TILE_W;
-    const int y = tile.y0 + px / PLX_TILE_W;
-    if (x < 0 || y < 0 || x >= tile.W || y >= tile.H) return;  // a tile over the image's edge
-    if (tile.scene < 0 || tile.scene >= n_scenes || tile.camera < 0 || tile.camera >= n_cams || !tile.d_rgb) {
-        if (lane == 0) report(tab.g[0].status, kDevBadTile);
-        return;
+    const int64_t cta_ray0 = (int64_t)blockIdx.x * kFwdWarps * kRayBatch;
+    const int64_t my_ray = batch_ray(cta_ray0, wid, lane);
+    if (lane < kRayBatch && my_ray < n_rays) {
+        const int64_t ray = my_ray;
+        const plx_tile tile = tiles[ray / (PLX_TILE_W * PLX_TILE_H)];
+        const int px = (int)(ray % (PLX_TILE_W * PLX_TILE_H));
+        const int x = tile.x0 + px % PLX_TILE_W;
+        const int y = tile.y0 + px / PLX_TILE_W;
+        RaySetup &rs = s_rs[wid][lane];
+        if (x < 0 || y < 0 || x >= tile.W || y >= tile.H) {  // a tile over the image's edge
+            rs.hit = -1;
+        } else if (tile.scene < 0 || tile.scene >= n_scenes || tile.camera < 0 || tile.camera >= n_cams ||
+                   !tile.d_rgb) {
+            report(tab.g[0].status, kDevBadTile);
+            rs.hit = -1;
+        } else {
+            float o[3], d[3];
+            pixel_ray(cams + 18 * (int64_t)tile.camera, x, y, o, d);
+            rs = ray_setup_od(tab.g[tile.scene], tab.p[tile.scene], o, d);
+        }
     }
-    const GridView &g = tab.g[tile.scene];
-    const RenderParams &p = tab.p[tile.scene];
-    float o[3], d[3];
-    pixel_ray(cams + 18 * (int64_t)tile.camera, x, y, o, d);
-    const RaySetup rs = ray_setup_od(g, p, o, d);
-    float C[3], Tc;
-    march_forward<FORM>(g, p, rs, s_ring[wid], lane, C, Tc);
-    if (lane == 0) {
-        float *out = tile.d_rgb + ((int64_t)y * tile.W + x) * 3;
-        out[0] = fmaf(Tc, p.bg[0], C[0]);
-        out[1] = fmaf(Tc, p.bg[1], C[1]);
-        out[2] = fmaf(Tc, p.bg[2], C[2]);
+    __syncwarp();
+    for (int r = 0; r < kRayBatch; ++r) {
+        const int64_t ray = batch_ray(cta_ray0, wid, r);
+        if (ray >= n_rays) break;            // uniform per warp
+        if (s_rs[wid][r].hit < 0) continue;  // uniform
+        const plx_tile tile = tiles[ray / (PLX_TILE_W * PLX_TILE_H)];
+        const int px = (int)(ray % (PLX_TILE_W * PLX_TILE_H));
+        const int x = tile.x0 + px % PLX_TILE_W;
+        const int y = tile.y0 + px / PLX_TILE_W;
+        const GridView &g = tab.g[tile.scene];
+        const RenderParams &p = tab.p[tile.scene];
+        float C[3], Tc;
+        march_forward<FORM>(g, p, s_rs[wid][r], s_ring[wid], lane, C, Tc);
+        if (lane == 0) {
+            float *out = tile.d_rgb + ((int64_t)y * tile.W + x) * 3;
+            out[0] = fmaf(Tc, p.bg[0], C[0]);
+            out[1] = fmaf(Tc, p.bg[1], C[1]);
+            out[2] = fmaf(Tc, p.bg[2], C[2]);
+        }
     }
 }
 
@@ -243,7 +283,8 @@ cudaError_t launch_render_tiles(const GridView *g, const RenderParams *p, int n_
         tab.p[i] = p[i];
     }
     const int64_t n_rays = n_tiles * PLX_TILE_W * PLX_TILE_H;
-    const int64_t blocks = n_rays / kFwdWarps;
+    const int64_t per_block = (int64_t)kFwdWarps * kRayBatch;
+    const int64_t blocks = (n_rays + per_block - 1) / per_block;
     if (g[0].form == PLX_SH_F32)
         render_tiles_kernel<PLX_SH_F32><<<(unsigned)blocks, kFwdWarps * 32, 0, s>>>(tab, n_scenes, cams, n_cams, tiles,
                                                                                      n_rays);
@@ -281,7 +322,7 @@ __global__ void __launch_bounds__(kBwdWarps * 32, kGatherBlocks) render_bwd_kern
     const int64_t ray = (int64_t)blockIdx.x * kBwdWarps + wid;
     if (ray >= n) return;
     const RaySetup rs = ray_setup(g, p, ro, rd, ray);
-    if (!rs.hit) return;
+    if (rs.hit <= 0) return;
     for (int q = lane; q < kMaxChunks / 32; q += 32) s_live[wid][q] = 0u;
     __syncwarp();
     int *ring = s_ring[wid];
@@ -292,7 +333,7 @@ __global__ void __launch_bounds__(kBwdWarps * 32, kGatherBlocks) render_bwd_kern
     {
         Stream st = {rs.s_lo, rs.s_lo, rs.s_lo, false};
         for (;;) {
-            refill(g, rs, p, ring, st, lane);
+            refill(g, rs, ring, st, lane);
             int s;
             const int cnt = take_chunk(ring, st, lane, s);
             if (cnt == 0) break;
@@ -304,7 +345,7 @@ __global__ void __launch_bounds__(kBwdWarps * 32, kGatherBlocks) render_bwd_kern
             float sig = 0.0f;
             if (valid) {
                 DF gc[3];
-                sample_coords(g, rs, sample_t(rs, p, s), gc);
+                coords_at(rs, s, gc);
                 sig = fmaxf(gather_sigma(g, FORM, gc), 0.0f);
             }
             const Composite cp = composite(sig, valid, Tc, p, lane);
@@ -328,7 +369,7 @@ __global__ void __launch_bounds__(kBwdWarps * 32, kGatherBlocks) render_bwd_kern
     // ---- pass 2: reverse over chunks
     for (int chunk = n_chunks - 1; chunk >= 0; --chunk) {
         if (!((s_live[wid][chunk >> 5] >> (chunk & 31)) & 1u)) continue;  // uniform: no density, no gradient
-        const int cnt = scan_range(g, rs, p, s_first[wid][chunk], s_first[wid][chunk + 1], ring, lane);
+        const int cnt = scan_range(g, rs, s_first[wid][chunk], s_first[wid][chunk + 1], ring, lane);
         const bool valid = lane < min(cnt, 32);
         const int s = valid ? ring[lane] : 0;
         __syncwarp();
@@ -340,7 +381,7 @@ __global__ void __launch_bounds__(kBwdWarps * 32, kGatherBlocks) render_bwd_kern
         bool occupied = false;
         if (valid) {
             DF gc[3];
-            sample_coords(g, rs, sample_t(rs, p, s), gc);
+            coords_at(rs, s, gc);
             occupied = gather_sample(g, FORM, gc, acc, rr, ff, &cell);
             if (occupied) {
                 sig = fmaxf(acc[0], 0.0f);
@@ -405,13 +446,13 @@ __global__ void __launch_bounds__(kFwdWarps * 32) count_nodes_kernel(GridView g,
     if (ray >= n) return;
     const RaySetup rs = ray_setup(g, p, ro, rd, ray);
     int64_t nodes = 0, occ_nodes = 0, samples = 0;  // samples: uniform over the warp
-    if (rs.hit) {
+    if (rs.hit > 0) {
         int *ring = s_ring[wid];
         Stream st = {rs.s_lo, rs.s_lo, rs.s_lo, false};
         float Tc = 1.0f;
         int64_t carry = -1;  // cell of the last sample of the previous chunk
         for (;;) {
-            refill(g, rs, p, ring, st, lane);
+            refill(g, rs, ring, st, lane);
             int s;
             const int cnt = take_chunk(ring, st, lane, s);
             if (cnt == 0) break;
@@ -420,7 +461,7 @@ __global__ void __launch_bounds__(kFwdWarps * 32) count_nodes_kernel(GridView g,
             int64_t cell = -1;
             if (valid) {
                 DF gc[3];
-                sample_coords(g, rs, sample_t(rs, p, s), gc);
+                coords_at(rs, s, gc);
                 cell = locate(g, gc).base;
                 sig = fmaxf(gather_sigma(g, g.form, gc), 0.0f);
             }
@@ -479,12 +520,12 @@ __global__ void __launch_bounds__(kFwdWarps * 32) max_weight_kernel(GridView g, 
     const int64_t ray = (int64_t)blockIdx.x * kFwdWarps + wid;
     if (ray >= n) return;  // uniform per warp
     const RaySetup rs = ray_setup(g, p, ro, rd, ray);
-    if (!rs.hit) return;   // uniform per warp
+    if (rs.hit <= 0) return;   // uniform per warp
     int *ring = s_ring[wid];
     Stream st = {rs.s_lo, rs.s_lo, rs.s_lo, false};
     float Tc = 1.0f;
     for (;;) {
-        refill(g, rs, p, ring, st, lane);
+        refill(g, rs, ring, st, lane);
         int s;
         const int cnt = take_chunk(ring, st, lane, s);
         if (cnt == 0) break;
@@ -495,7 +536,7 @@ __global__ void __launch_bounds__(kFwdWarps * 32) max_weight_kernel(GridView g, 
         for (int k = 0; k < 8; ++k) r[k] = -1;
         if (valid) {
             DF gc[3];
-            sample_coords(g, rs, sample_t(rs, p, s), gc);
+            coords_at(rs, s, gc);
             const Cell c = locate(g, gc);
 #pragma unroll
             for (int k = 0; k < 8; ++k) r[k] = row_of(g, corner_node(g, c.base, k));

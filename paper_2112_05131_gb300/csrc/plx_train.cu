@@ -96,11 +96,8 @@ __global__ void __launch_bounds__(kPlanWarps * 32) march_plan_kernel(GridView g,
         const int mc = st.max_chunks;
         int2 *range = st.range + ray * mc;
         uint16_t *samp = st.samp ? st.samp + ray * mc * 32 : nullptr;  // chunk k's samples at [32 k, 32 k + 32)
-        // candidates beyond (t_far - t_near) / delta + 2 are invalid, and test_candidate admits fewer than
-        // max_chunks * 32 (so every rank / 32 < max_chunks)
-        int L = 0;
-        if (rs.hit) L = (int)fminf((float)(mc * 32), ceilf((rs.tf.hi - rs.tn.hi) / p.delta) + 2.0f);
-        L = min(L, rs.s_hi);   // candidates outside [s_lo, s_hi) are empty: spans start at s_lo
+        // s_hi <= max_chunks * 32, so every rank / 32 < max_chunks
+        const int L = rs.hit > 0 ? rs.s_hi : 0;  // candidates outside [s_lo, s_hi) are empty or past t_far
         const int s_first = rs.s_lo;
         const int n_spans = L > s_first ? (L - s_first + kSpan - 1) / kSpan : 0;
         int n_occ = 0;
@@ -109,12 +106,12 @@ __global__ void __launch_bounds__(kPlanWarps * 32) march_plan_kernel(GridView g,
             // phase 1: masks and counts of this window's spans
             for (int q = wid; q < nw; q += kPlanWarps) {
                 const int base = s_first + (w0 + q) * kSpan;
-                Cand c[kCand];
-                test_round(g, rs, p, base, L, lane, c);
+                bool occ[kCand];
+                test_round(g, rs, base, L, lane, occ);
                 int cnt = 0;
 #pragma unroll
                 for (int j = 0; j < kCand; ++j) {
-                    const unsigned m = __ballot_sync(kFull, c[j].occ);
+                    const unsigned m = __ballot_sync(kFull, occ[j]);
                     if (lane == 0) s_mask[q * kCand + j] = m;
                     cnt += __popc(m);
                 }
@@ -253,7 +250,7 @@ __device__ __forceinline__ int item_samples(const GridView &g, const RaySetup &r
         return expect;
     }
     const int2 r = st.range[(int64_t)in.ray * st.max_chunks + in.k];
-    const int cnt = scan_range(g, rs, p, r.x, r.y, buf, lane);
+    const int cnt = scan_range(g, rs, r.x, r.y, buf, lane);
     s = lane < cnt ? buf[lane] : 0;
     __syncwarp();
     if (cnt != expect) {
@@ -303,7 +300,7 @@ __global__ void __launch_bounds__(kChunkWarps * 32, kGatherBlocks) march_chunks_
         float sig = 0.0f, col[3] = {0.0f, 0.0f, 0.0f};
         if (valid) {
             DF gc[3];
-            sample_coords(g, rs, sample_t(rs, p, s), gc);
+            coords_at(rs, s, gc);
             float acc[kNV];
             int32_t rr[8];
             float ff[3];
@@ -486,7 +483,7 @@ __global__ void __launch_bounds__(kChunkWarps * 32, VALS ? kBwdValsBlocks : kGat
         float sig = 0.0f, pre[3] = {0.0f, 0.0f, 0.0f}, col[3] = {0.0f, 0.0f, 0.0f};
         if (valid) {
             DF gc[3];
-            sample_coords(g, rs, sample_t(rs, p, s), gc);
+            coords_at(rs, s, gc);
             if (VALS) {  // the forward's values; only the corners are looked up again
                 const float4 v = st.vals[(ray * mc + k) * 32 + lane];
                 const Cell c = locate(g, gc);

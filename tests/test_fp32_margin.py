@@ -1,8 +1,10 @@
 """The march's cheap occupancy test works on FP32 grid coordinates and falls back to double-float
-arithmetic within a per-ray margin of every cell face.  The margin is a bound on the FP32 coordinate
-error, u (inv_h (3 |o - lo| + 5 t) + |x|) with u = 2^-24, plus a quarter.  This test runs the same
-FP32 operations (ray setup, sample parameter, coordinate) in numpy and checks the bound against
-float64 coordinates over many rays, samples, grid sizes and camera distances."""
+arithmetic within a per-ray margin of every cell face.  Sample s of a ray sits at grid coordinates
+g0 + s st (g0: the point at t_near, st: the step between samples, both kept as double-floats); the
+cheap coordinate is fma(s, st_hi, g0_hi) and the margin is a bound on its error,
+u (2 max|g0| + 2 (s_end + 8) max|st|) with u = 2^-24, plus a quarter.  This test runs the same FP32
+operations in numpy and checks the bound against float64 coordinates over many rays, samples (up to
+8 past the last one, as the group screen evaluates), grid sizes and camera distances."""
 import numpy as np
 import pytest
 
@@ -41,22 +43,21 @@ def test_fp32_coordinate_error_within_margin(R, radius):
     hit = tf > tn
     o, d, tn, tf = o[hit], d[hit], tn[hit], tf[hit]
     delta = 0.5 * h
-    delta32 = np.float32(delta)
-    tn_hi = tn.astype(np.float32)
-    og = ((o - lo).astype(np.float32) * inv_h32).astype(np.float32)
-    dg = (d * inv_h32).astype(np.float32)
-    om = np.max(np.abs(o - lo), axis=1).astype(np.float64)
-    bound = U * (float(inv_h32) * (3.0 * om + 5.0 * np.abs(tf)) + R)
+    # the double-float anchor and step, rounded to their FP32 high parts
+    g0 = (o.astype(np.float64) - lo + tn[:, None] * d.astype(np.float64)) / h
+    st = delta * d.astype(np.float64) / h
+    g0_hi = g0.astype(np.float32)
+    st_hi = st.astype(np.float32)
+    s_end = np.ceil((tf - tn) / delta)
+    bound = U * (2.0 * np.abs(g0_hi).max(axis=1) + 2.0 * (s_end + 8) * np.abs(st_hi).max(axis=1))
     worst = 0.0
-    for s in range(0, int(np.ceil((tf - tn).max() / delta)) + 1, 7):
-        live = tn + s * delta < tf
+    for s in range(0, int(s_end.max()) + 8, 7):
+        live = s < s_end + 8
         if not live.any():
             break
-        t32 = fma32(np.float32(s), delta32, tn_hi)
-        t = tn + s * delta
         for a in range(3):
-            x32 = fma32(t32, dg[:, a], og[:, a]).astype(np.float64)
-            x = (o[:, a].astype(np.float64) - lo + t * d[:, a].astype(np.float64)) / h
+            x32 = fma32(np.float32(s), st_hi[:, a], g0_hi[:, a]).astype(np.float64)
+            x = (o[:, a].astype(np.float64) - lo + (tn + s * delta) * d[:, a].astype(np.float64)) / h
             err = np.abs(x32 - x)[live]
             ratio = err / bound[live]
             worst = max(worst, float(ratio.max()))
