@@ -249,6 +249,7 @@ __device__ __forceinline__ float warp_sum(float x) {
 struct Cell {
     int64_t base;   // linear id of the cell's (0,0,0) node
     float f[3];     // fractions
+    int par;        // parities of the cell's integer coordinates: bit 2 x, bit 1 y, bit 0 z
 };
 
 __device__ __forceinline__ Cell locate(const GridView &g, const DF gc[3]) {
@@ -269,7 +270,42 @@ __device__ __forceinline__ Cell locate(const GridView &g, const DF gc[3]) {
         c.f[a] = fminf(fmaxf(fr, 0.0f), 1.0f);
     }
     c.base = ((int64_t)b[0] * g.R + b[1]) * g.R + b[2];
+    c.par = ((b[0] & 1) << 2) | ((b[1] & 1) << 1) | (b[2] & 1);
     return c;
+}
+
+// The 8 corners of a cell in slot order.  Slot i takes, along each axis a, the node whose coordinate has
+// the parity of i's bit for a (bit 2 x, bit 1 y, bit 0 z): slot i of every cell is its one corner with
+// parity pattern i.  Two cells sharing a node then hold it in the same slot, so when a warp's lanes load
+// their cells' slot i in one instruction, every node shared by neighbouring samples is one address and
+// is fetched once.  Canonical order (par = 0) is slot i = corner i.
+struct Corners {
+    int64_t base;
+    int off[3][2];   // node offset along each axis for slot bit 0 / 1
+    float w[3][2];   // trilinear weight factor along each axis for slot bit 0 / 1
+};
+
+__device__ __forceinline__ Corners corners_of(const GridView &g, const Cell &c, int par) {
+    Corners k;
+    k.base = c.base;
+    const int stride[3] = {g.R * g.R, g.R, 1};
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        const int p = (par >> (2 - a)) & 1;  // slot bit b selects the node at offset b ^ p
+        k.off[a][0] = p ? stride[a] : 0;
+        k.off[a][1] = p ? 0 : stride[a];
+        k.w[a][0] = p ? c.f[a] : 1.0f - c.f[a];
+        k.w[a][1] = p ? 1.0f - c.f[a] : c.f[a];
+    }
+    return k;
+}
+
+__device__ __forceinline__ int64_t slot_node(const Corners &k, int i) {
+    return k.base + (k.off[0][(i >> 2) & 1] + k.off[1][(i >> 1) & 1] + k.off[2][i & 1]);
+}
+
+__device__ __forceinline__ float slot_weight(const Corners &k, int i) {
+    return k.w[0][(i >> 2) & 1] * k.w[1][(i >> 1) & 1] * k.w[2][i & 1];
 }
 
 __device__ __forceinline__ bool cell_occupied(const GridView &g, int64_t base) {

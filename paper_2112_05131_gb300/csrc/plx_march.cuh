@@ -25,8 +25,7 @@ struct __align__(16) RaySetup {  // 128 bytes: the training march keeps one per 
     float feps;    // bound on |FP32 - exact| grid coordinate of any candidate of the ray (see test_candidate)
     int hit;       // the ray meets the box (1), misses it (0); < 0: no ray (a pixel outside its image)
     int s_lo, s_hi;  // samples outside [s_lo, s_hi) are past t_far or lie in empty cells
-    int inner;     // every candidate's FP32 coordinate is inside the grid by more than feps on every axis
-    float pad_[6];
+    float pad_[7];
 };
 static_assert(sizeof(RaySetup) == 128, "RaySetup layout");
 
@@ -44,10 +43,9 @@ __device__ __forceinline__ RaySetup ray_setup_od(const GridView &g, const Render
     rs.hit = clip_box(g, o, d, tn, tf);
     sh_basis(d, rs.Y);
     rs.s_lo = rs.s_hi = 0;
-    rs.inner = 0;
     rs.feps = 0.0f;
 #pragma unroll
-    for (int q = 0; q < 6; ++q) rs.pad_[q] = 0.0f;
+    for (int q = 0; q < 7; ++q) rs.pad_[q] = 0.0f;
     if (!rs.hit) {
 #pragma unroll
         for (int a = 0; a < 3; ++a) rs.g0[a] = rs.st[a] = DF{0.0f, 0.0f};
@@ -98,20 +96,6 @@ __device__ __forceinline__ RaySetup ray_setup_od(const GridView &g, const Render
     if (any && s0 <= s1) {
         rs.s_lo = (int)fminf(fmaxf(floorf(s0) - 2.0f, 0.0f), (float)s_end);
         rs.s_hi = (int)fminf(fmaxf(ceilf(s1) + 3.0f, 0.0f), (float)s_end);
-    }
-    // Inner: the FP32 coordinates of the first and last candidates lie in [3 feps, R - 1 - 3 feps] on every
-    // axis; the exact points between them are on that segment, so every candidate's FP32 coordinate is in
-    // [feps, R - 1 - feps]: its floor is a valid cell and no clamp applies.
-    if (rs.s_lo < rs.s_hi) {
-        const float lo3 = 3.0f * rs.feps, hi3 = (float)(g.R - 1) - 3.0f * rs.feps;
-        bool in = true;
-#pragma unroll
-        for (int a = 0; a < 3; ++a) {
-            const float xa = fmaf((float)rs.s_lo, rs.st[a].hi, rs.g0[a].hi);
-            const float xb = fmaf((float)(rs.s_hi - 1), rs.st[a].hi, rs.g0[a].hi);
-            in = in && fminf(xa, xb) >= lo3 && fmaxf(xa, xb) <= hi3;
-        }
-        rs.inner = in ? 1 : 0;
     }
     return rs;
 }
@@ -196,19 +180,23 @@ __device__ __forceinline__ void fma2(float &a0, float &a1, uint64_t ww, float x0
 
 // Full sample: interpolated values at grid point gc, whose cell the caller has
 // already found occupied (compaction).  rows_out/f_out (and base_out, if given)
-// receive the corners.
+// receive the corners: rows_out[k] is corner k's row (canonical order), unless
+// SLOTS, when the corners are loaded and returned in slot order (corners_of), which
+// lets lanes share the loads of common nodes; forward-only callers use that.
+template <bool SLOTS = false>
 __device__ __forceinline__ bool gather_sample(const GridView &g, int form, const DF gc[3], float acc[kNV],
                                               int32_t rows_out[8], float f_out[3], int64_t *base_out = nullptr) {
 #pragma unroll
     for (int q = 0; q < kNV; ++q) acc[q] = 0.0f;
-    Cell c = locate(g, gc);
+    const Cell c = locate(g, gc);
+    const Corners cn = corners_of(g, c, SLOTS ? c.par : 0);
     if (base_out) *base_out = c.base;
     f_out[0] = c.f[0];
     f_out[1] = c.f[1];
     f_out[2] = c.f[2];
     int32_t r[8];
 #pragma unroll
-    for (int k = 0; k < 8; ++k) r[k] = row_of(g, corner_node(g, c.base, k));
+    for (int k = 0; k < 8; ++k) r[k] = row_of(g, slot_node(cn, k));
     // every corner's row is requested before any is used: one memory round trip per
     // chunk instead of eight (a NULL corner contributes w * 0, i.e. nothing)
     if (form == PLX_SH_F32) {
@@ -239,7 +227,7 @@ __device__ __forceinline__ bool gather_sample(const GridView &g, int form, const
                                  "+f"(v[k][q].v[e + 3]));
 #pragma unroll
         for (int k = 0; k < 8; ++k) {
-            const float w = corner_weight(c.f, k);
+            const float w = slot_weight(cn, k);
 #pragma unroll
             for (int q = 0; q < kNV; ++q) acc[q] = fmaf(w, v[k][q >> 3].v[q & 7], acc[q]);
         }
@@ -268,7 +256,7 @@ __device__ __forceinline__ bool gather_sample(const GridView &g, int form, const
                                  "+r"(v[k][q].v[e + 3]));
 #pragma unroll
         for (int k = 0; k < 8; ++k) {
-            const float w = corner_weight(c.f, k);
+            const float w = slot_weight(cn, k);
             uint32_t wd[16];
 #pragma unroll
             for (int e = 0; e < 16; ++e) wd[e] = v[k][e >> 3].v[e & 7];
@@ -363,9 +351,29 @@ constexpr int kRing = 512;  // ring capacity >= 31 + 32 kCand, a power of two
 // Is the cell of sample s (s_lo <= s < s_hi: every such sample is before t_far) non-empty?  The answer
 // must equal the double-float one exactly (it decides which samples are marched).  Plain FP32
 // coordinates are within rs.feps of the exact ones (the bound derived in ray_setup_od); a candidate whose
-// FP32 coordinate lies within rs.feps of a cell face, or (unless the ray is inner) of the box, on any axis
-// is re-evaluated in double-float, so the cheap path is taken only where both agree.
-template <bool INNER>
+// FP32 coordinate lies within rs.feps of a cell face or of the box on any axis is re-evaluated in
+// double-float, so the cheap path is taken only where both agree.
+// The double-float decision for sample s (rare: near a cell face or the box), kept out of line so
+// that the unrolled candidate loops stay small.
+// Everything is passed by value, so that no caller's setup has to live in addressable memory.
+static __device__ __noinline__ bool exact_occupied(const uint32_t *__restrict__ occ, int R, float g0x, float g0x_lo,
+                                            float g0y, float g0y_lo, float g0z, float g0z_lo, float stx,
+                                            float stx_lo, float sty, float sty_lo, float stz, float stz_lo, int s) {
+    RaySetup rs;
+    rs.g0[0] = DF{g0x, g0x_lo};
+    rs.g0[1] = DF{g0y, g0y_lo};
+    rs.g0[2] = DF{g0z, g0z_lo};
+    rs.st[0] = DF{stx, stx_lo};
+    rs.st[1] = DF{sty, sty_lo};
+    rs.st[2] = DF{stz, stz_lo};
+    DF gc[3];
+    coords_at(rs, s, gc);
+    GridView g;
+    g.R = R;
+    g.occ = occ;
+    return cell_occupied(g, locate(g, gc).base);
+}
+
 __device__ __forceinline__ bool test_candidate(const GridView &g, const RaySetup &rs, int s) {
     const float sf = (float)s;
     bool exact = false;
@@ -376,14 +384,12 @@ __device__ __forceinline__ bool test_candidate(const GridView &g, const RaySetup
         const float x = fmaf(sf, rs.st[a].hi, rs.g0[a].hi);
         const float fl = floorf(x);
         exact = exact || fabsf((x - fl) - 0.5f) > 0.5f - rs.feps;
-        if (!INNER) exact = exact || fabsf(x - half) > half - rs.feps;
+        exact = exact || fabsf(x - half) > half - rs.feps;
         b[a] = (int)fl;
     }
-    if (exact) {
-        DF gc[3];
-        coords_at(rs, s, gc);
-        return cell_occupied(g, locate(g, gc).base);
-    }
+    if (exact)
+        return exact_occupied(g.occ, g.R, rs.g0[0].hi, rs.g0[0].lo, rs.g0[1].hi, rs.g0[1].lo, rs.g0[2].hi, rs.g0[2].lo,
+                              rs.st[0].hi, rs.st[0].lo, rs.st[1].hi, rs.st[1].lo, rs.st[2].hi, rs.st[2].lo, s);
     // here 0 <= b < R - 1 on every axis; the linear id fits 32 bits below R = 1291
     const int64_t base = g.R <= 1290 ? (int64_t)((b[0] * g.R + b[1]) * g.R + b[2])
                                      : ((int64_t)b[0] * g.R + b[1]) * g.R + b[2];
@@ -432,18 +438,10 @@ __device__ __forceinline__ bool group_live(const GridView &g, const RaySetup &rs
 __device__ __forceinline__ unsigned test_round(const GridView &g, const RaySetup &rs, int first, int end, int lane,
                                                bool occ[kCand]) {
     const unsigned live = __ballot_sync(kFull, group_live(g, rs, first + kGroup * lane));
-    if (rs.inner) {  // uniform
 #pragma unroll
-        for (int j = 0; j < kCand; ++j) {
-            const int s = first + 32 * j + lane;
-            occ[j] = ((live >> (4 * j + (lane >> 3))) & 1u) && s < end && test_candidate<true>(g, rs, s);
-        }
-    } else {
-#pragma unroll
-        for (int j = 0; j < kCand; ++j) {
-            const int s = first + 32 * j + lane;
-            occ[j] = ((live >> (4 * j + (lane >> 3))) & 1u) && s < end && test_candidate<false>(g, rs, s);
-        }
+    for (int j = 0; j < kCand; ++j) {
+        const int s = first + 32 * j + lane;
+        occ[j] = ((live >> (4 * j + (lane >> 3))) & 1u) && s < end && test_candidate(g, rs, s);
     }
     return live;
 }

@@ -109,7 +109,7 @@ constexpr int kFwdWarps = 4;
 // Resident warps per SM the one-warp-per-ray render kernels are compiled for, per row form: the
 // register cap it implies trades a few spilled bytes for more warps to hide the gathers' latency.
 constexpr int kFwdWarpsSMF32 = 24;
-constexpr int kFwdWarpsSMBF16 = 20;
+constexpr int kFwdWarpsSMBF16 = 24;
 constexpr int fwd_blocks(int form) { return (form == PLX_SH_BF16 ? kFwdWarpsSMBF16 : kFwdWarpsSMF32) / kFwdWarps; }
 // Rays per warp in the render kernels: lanes 0 .. kRayBatch-1 set up that many consecutive rays at once
 // (double-float clip and anchor, SH basis, candidate range) into shared memory, and the warp then marches
@@ -147,7 +147,7 @@ __device__ __forceinline__ void march_forward(const GridView &g, const RenderPar
                 float acc[kNV];
                 int32_t rr[8];
                 float ff[3];
-                if (gather_sample(g, FORM, gc, acc, rr, ff)) {
+                if (gather_sample<true>(g, FORM, gc, acc, rr, ff)) {
                     sig = fmaxf(acc[0], 0.0f);
                     float pre[3];
                     colour_of(acc, rs.Y, pre, col);

@@ -304,7 +304,7 @@ __global__ void __launch_bounds__(kChunkWarps * 32, kGatherBlocks) march_chunks_
             float acc[kNV];
             int32_t rr[8];
             float ff[3];
-            gather_sample(g, FORM, gc, acc, rr, ff);
+            gather_sample<true>(g, FORM, gc, acc, rr, ff);
             sig = fmaxf(acc[0], 0.0f);
             float pre[3];
             colour_of(acc, rs.Y, pre, col);
