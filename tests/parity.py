@@ -142,3 +142,30 @@ def psnr(x, y):
     """Peak signal-to-noise ratio in dB for colours on a unit peak."""
     mse = float(np.mean((np.asarray(x, np.float64) - np.asarray(y, np.float64)) ** 2))
     return float("inf") if mse == 0.0 else -10.0 * math.log10(mse)
+
+
+# FP32 summation allowance for gradient entries whose terms cancel.  Each term of an adjoint entry is a
+# product of several rounded FP32 quantities (transmittance, alpha, colour gradient, trilinear and basis
+# factors), so it carries a relative error of a few units of roundoff, and the atomic accumulation adds
+# one rounding per addition in an order that changes from run to run.  Where the terms cancel, the
+# entry's error is a few roundoffs of the summed magnitudes, not of the entry, and can exceed the floor
+# 1e-4 * 1e-3 max|g| (about 1.7 roundoffs of max|g|).  On the dense 32^3 step the largest error measured
+# on a GB300 was 3.7 roundoffs of the oracle's magnitude adjoint; the allowance is 8.
+FP32_SUM_U = 8 * 2.0 ** -24
+
+
+def dense32_step_case(n, seed, opts_bg=(1.0, 1.0, 1.0), stop_thresh=0.0):
+    """The dense 32^3 workload's own adjoint input: the perturbed grid (the ground truth plus N(0, 0.05)
+    on every value) rendered along n seeded rays, and dL/dC of the MSE against the ground truth's render
+    (Eq. 3), both from the oracle.  Returns (scene, o, d, dL/dC float32)."""
+    import oracle
+    import synth
+
+    gt = synth.scene_config("dense32")
+    sc = synth.perturb(gt, 0.05, seed=1)
+    o, d = synth.random_rays(n, seed=seed)
+    kw = dict(bg=opts_bg, stop_thresh=stop_thresh)
+    target, _ = oracle.render(gt.R, gt.idx, gt.rows, o.astype(float), d.astype(float), **kw)
+    pred, _ = oracle.render(gt.R, sc.idx, sc.rows, o.astype(float), d.astype(float), **kw)
+    gw = oracle.mse(pred, target.astype(np.float32).astype(np.float64))[1].astype(np.float32)
+    return sc, o, d, gw
