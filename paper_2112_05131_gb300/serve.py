@@ -8,6 +8,13 @@ over all scenes; when a request's last tile has rendered, its image is copied ba
 pinned host memory on a second stream, so copies overlap the next launches.  Latency is
 measured from a request's arrival to the moment its image is in host memory.
 
+Admission is by device memory: each request is charged the device bytes of its image
+while it is active (from admission until its image is back in host memory), and a
+request waits in the pending queue, in arrival order, until its charge fits the
+server's byte budget (by default the device's free memory at start-up, less a margin)
+and a camera slot is free.  Requests admitted while others are on the GPU join the
+next launch, so their work overlaps on the device.
+
 Everything on the GPU runs in libplenoxel; this module only schedules: it fills tile
 records (numpy), issues copies and launches, and polls CUDA events.
 """
@@ -42,10 +49,15 @@ class Done:
     finished: float
     pixels: int
     image: Optional[np.ndarray] = None
+    admitted: float = 0.0    # when the request left the pending queue
 
     @property
     def latency(self) -> float:
         return self.finished - self.arrival
+
+    @property
+    def admission_wait(self) -> float:
+        return self.admitted - self.arrival
 
 
 @dataclass
@@ -55,6 +67,8 @@ class _Active:
     slot: int                    # camera slot
     x0: np.ndarray
     y0: np.ndarray
+    charge: int                  # device bytes held until the image is back on the host
+    admitted: float
     next: int = 0                # next tile to launch
     launched_all_in: int = -1    # launch id that holds the last tile
 
@@ -64,6 +78,18 @@ def tile_origins(W: int, H: int) -> Tuple[np.ndarray, np.ndarray]:
     ty, tx = np.meshgrid(np.arange(0, H, TILE_H, dtype=np.int32), np.arange(0, W, TILE_W, dtype=np.int32),
                          indexing="ij")
     return tx.reshape(-1), ty.reshape(-1)
+
+
+def request_device_bytes(W: int, H: int) -> int:
+    """Device bytes a request holds while active: its FP32 RGB image, rounded up to the caching
+    allocator's 512-byte granularity."""
+    return (W * H * 3 * 4 + 511) // 512 * 512
+
+
+def default_memory_budget(device="cuda", margin: float = 0.1) -> int:
+    """The device's free memory now, less `margin` of it (kept for the allocator and other work)."""
+    free, _ = torch.cuda.mem_get_info(torch.device(device))
+    return int(free * (1.0 - margin))
 
 
 def scene_device_bytes(R: int, M: int, form: int = 1) -> int:
@@ -77,10 +103,16 @@ class TileServer:
     """Continuous batching of image requests over up to 8 resident scenes of one SH form."""
 
     def __init__(self, grids: Sequence[Grid], opts: RenderOpts = RenderOpts(), max_rays_per_launch: int = 1 << 18,
-                 max_inflight: int = 2, max_active: int = 64, keep_images: bool = False, device="cuda"):
+                 max_inflight: int = 2, max_active: int = 64, keep_images: bool = False, device="cuda",
+                 mem_budget: Optional[int] = None):
         if not 1 <= len(grids) <= MAX_TILE_SCENES:
             raise ValueError(f"1..{MAX_TILE_SCENES} scenes")
         self.grids = list(grids)
+        # device bytes that active requests may hold at once, and what they hold now
+        self.mem_budget = int(mem_budget) if mem_budget is not None else default_memory_budget(device)
+        self.mem_in_use = 0
+        self.mem_peak = 0
+        self.clock_now = 0.0
         self.opts = opts
         self.dev = torch.device(device)
         self.max_tiles = max(1, max_rays_per_launch // (TILE_W * TILE_H))
@@ -110,13 +142,23 @@ class TileServer:
 
     # ------------------------------------------------------------------ requests
     def submit(self, req: Request):
+        if not 0 <= req.scene < len(self.grids):
+            raise ValueError(f"request {req.rid}: no scene {req.scene}")
+        if request_device_bytes(req.W, req.H) > self.mem_budget:
+            raise ValueError(f"request {req.rid}: its {req.W}x{req.H} image needs more device memory than the "
+                             f"server's whole budget ({self.mem_budget} bytes)")
         self.pending.append(req)
 
     def _activate(self):
+        # first come, first served: the head of the queue waits for memory, and nothing overtakes it
         while self.pending and self.free_slots and len(self.active) + len(self.copying) < self.max_active:
-            req = self.pending.popleft()
-            if not 0 <= req.scene < len(self.grids):
-                raise ValueError(f"request {req.rid}: no scene {req.scene}")
+            req = self.pending[0]
+            charge = request_device_bytes(req.W, req.H)
+            if self.mem_in_use + charge > self.mem_budget:
+                break
+            self.pending.popleft()
+            self.mem_in_use += charge
+            self.mem_peak = max(self.mem_peak, self.mem_in_use)
             slot = self.free_slots.pop()
             self.cams_host[slot] = torch.from_numpy(np.asarray(req.cam, np.float32))
             with torch.cuda.stream(self.render_stream):
@@ -126,7 +168,7 @@ class TileServer:
             if key not in self._origins:
                 self._origins[key] = tile_origins(req.W, req.H)
             x0, y0 = self._origins[key]
-            self.active.append(_Active(req, image, slot, x0, y0))
+            self.active.append(_Active(req, image, slot, x0, y0, charge, self.clock_now))
 
     # ------------------------------------------------------------------ launches
     def _launch(self):
@@ -190,7 +232,8 @@ class TileServer:
                 img = host.numpy().copy() if self.keep_images else None
                 self._pinned[(a.req.W, a.req.H)].append(host)
                 self.free_slots.append(a.slot)
-                self.done.append(Done(a.req.rid, a.req.arrival, now, a.req.W * a.req.H, img))
+                self.mem_in_use -= a.charge  # the image is released once its copy has completed
+                self.done.append(Done(a.req.rid, a.req.arrival, now, a.req.W * a.req.H, img, a.admitted))
             else:
                 still.append((cev, a, host))
         self.copying = still
@@ -200,6 +243,7 @@ class TileServer:
 
     def step(self, now: float):
         """One scheduler iteration: poll completions, activate arrived requests, launch while there is room."""
+        self.clock_now = now
         self._poll(now)
         self._activate()
         while len(self.inflight) < self.max_inflight and self.active:
@@ -234,6 +278,8 @@ def requests_from(mix) -> List[Request]:
 
 def latency_stats(done: Sequence[Done], wall: float) -> dict:
     lat = np.array([d.latency for d in done]) * 1e3
+    wait = np.array([d.admission_wait for d in done]) * 1e3
     px = sum(d.pixels for d in done)
     return {"requests": len(done), "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
-            "mean_ms": float(lat.mean()), "Mrays_per_s": px / wall / 1e6, "wall_s": wall}
+            "mean_ms": float(lat.mean()), "admission_wait_p50_ms": float(np.percentile(wait, 50)),
+            "admission_wait_p99_ms": float(np.percentile(wait, 99)), "Mrays_per_s": px / wall / 1e6, "wall_s": wall}

@@ -118,3 +118,39 @@ def test_server_poisson_trace(cuda_lib):
     st = latency_stats(done, max(d.finished for d in done))
     assert st["p99_ms"] >= st["p50_ms"] > 0
     assert srv.launches >= 2
+
+
+def test_server_admits_by_device_memory(cuda_lib):
+    """A byte budget that holds only two of the requests' images: requests queue until memory frees up,
+    the bytes held never exceed the budget, two requests do run at once, every request completes, and
+    each image is the same as when it is rendered alone; a request larger than the whole budget is
+    refused."""
+    from paper_2112_05131_gb300.grid import RenderOpts
+    from paper_2112_05131_gb300.serve import Request, TileServer, request_device_bytes
+
+    scenes = _scenes(1)
+    grids = [g for _, g in scenes]
+    opts = RenderOpts(0.5, BG, 0.0)
+    cams = synth.cameras(8, 1, 1, 40.0, 2.6, upper=False, seed=11)
+    W = H = 192
+    reqs = []
+    for i in range(8):
+        c = cams[i].copy()
+        f = 0.5 * W / np.tan(np.radians(20.0))
+        c[12:18] = [f, f, 0.5 * W, 0.5 * H, W, H]
+        reqs.append(Request(i, i % 3, c, W, H, 0.0))
+    one = request_device_bytes(W, H)
+    budget = 2 * one + one // 2
+    srv = TileServer(grids, opts, max_rays_per_launch=4096, keep_images=True, mem_budget=budget)
+    done = srv.run(reqs)
+    assert sorted(d.rid for d in done) == list(range(8))
+    assert srv.mem_peak <= budget
+    assert srv.mem_peak == 2 * one  # two requests were active together, never three
+    assert srv.mem_in_use == 0
+    waits = sorted(d.admission_wait for d in done)
+    assert waits[-1] > 0.0  # later requests waited for memory
+    for d in done:
+        alone = TileServer(grids, opts, keep_images=True).run([reqs[d.rid]])[0].image
+        assert np.array_equal(alone.view(np.uint32), d.image.view(np.uint32)), f"request {d.rid}"
+    with pytest.raises(ValueError, match="budget"):
+        TileServer(grids, opts, mem_budget=one - 1).submit(reqs[0])
