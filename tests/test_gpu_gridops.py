@@ -65,3 +65,36 @@ def test_upsample_parity(cuda_lib, R, R2, frac):
     scale = np.max(np.abs(sc.rows), axis=0)[None, :]
     # FP32 weights and sums: error bounded by a few ulp of the largest input of the column
     assert np.all(np.abs(got - rows_ref) <= 4e-7 * (np.abs(rows_ref) + scale))
+
+
+@pytest.mark.parametrize("R", [128, 256])
+def test_prune_upsample_coarse_to_fine_sizes(cuda_lib, R):
+    """The coarse-to-fine workload's grid operations at its own sizes (128^3 -> 256^3 -> 512^3): a sparse scene
+    of the workload's generator, pruned at density 5 with dilation (bit-exact), then upsampled to 2R (map
+    bit-exact, values within the FP32 bound above); the 512^3 output has about 10 M rows.  Values are
+    compared in slices to bound host memory."""
+    from paper_2112_05131_gb300.grid import Grid
+
+    sc = synth.scene_config(f"sparse{R}_0.08", seed=3)
+    g = Grid.from_host(sc.R, sc.idx, sc.rows)
+    gp = g.prune(5.0, True)
+    idx_p, rows_p = oracle.prune(sc.R, sc.idx, sc.rows, 5.0, True)
+    assert np.array_equal(gp.idx.cpu().numpy(), idx_p)
+    assert np.array_equal(gp.rows.cpu().numpy()[:, :28], rows_p.astype(np.float32))
+    del g
+    R2 = 2 * R
+    gu = gp.upsample(R2)
+    gp.check()
+    idx_ref, rows_ref = oracle.upsample(R, idx_p, rows_p, R2)
+    assert np.array_equal(gu.idx.cpu().numpy(), idx_ref)
+    assert gu.M == rows_ref.shape[0]
+    scale = np.max(np.abs(rows_p), axis=0)[None, :]
+    worst = 0.0
+    for a in range(0, gu.M, 1 << 20):
+        b = min(gu.M, a + (1 << 20))
+        got = gu.rows[a:b, :28].cpu().numpy().astype(np.float64)
+        ref = rows_ref[a:b]
+        ratio = np.abs(got - ref) / (4e-7 * (np.abs(ref) + scale))
+        worst = max(worst, float(ratio.max()))
+    assert worst <= 1.0, worst
+    print(f"prune + upsample {R}^3 -> {R2}^3: {gp.M} -> {gu.M} rows, value err/tol {worst:.3f}")
