@@ -53,6 +53,7 @@ class C2FConfig:
     # sparse within the first minutes); each stage's log entry then holds it every `touched_every` steps
     track_touched: bool = False
     touched_every: int = 100
+    lr_scale: float = 1.0  # multiplies both learning-rate schedules (0 keeps the grid's values fixed)
 
 
 def paper_synthetic() -> C2FConfig:
@@ -128,10 +129,12 @@ class _Batches:
 
 
 def train(train_images: np.ndarray, cams: torch.Tensor, W: int, H: int, cfg: C2FConfig = C2FConfig(),
-          log: Optional[List[dict]] = None) -> Grid:
-    """Runs the coarse-to-fine schedule and returns the final grid.  `log` receives one record per stage."""
+          log: Optional[List[dict]] = None, start: Optional[Grid] = None) -> Grid:
+    """Runs the coarse-to-fine schedule and returns the final grid.  `log` receives one record per stage.
+    The run starts from `start` (updated in place) or, by default, a dense cfg.start_reso grid of density
+    cfg.init_sigma."""
     dev = cams.device
-    grid = dense_grid(cfg.start_reso, cfg.init_sigma, dev)
+    grid = start if start is not None else dense_grid(cfg.start_reso, cfg.init_sigma, dev)
     sc = StepConfig(batch=cfg.batch, opts=cfg.opts, lambda_tv_sigma=cfg.lambda_tv_sigma,
                     lambda_tv_sh=cfg.lambda_tv_sh, track_touched=cfg.track_touched)
     tr = Trainer(grid, cams, W, H, sc)
@@ -171,7 +174,7 @@ def train(train_images: np.ndarray, cams: torch.Tensor, W: int, H: int, cfg: C2F
         nxt = None
         if step + 1 < cfg.steps and not (ups and step + 1 == ups[0]):
             nxt = batches.get(step + 1, grid.reso)[0]
-        tr.step(pix, tgt, ss, sl, nsel, lr_sigma(step), lr_sh(step), next_pix=nxt)
+        tr.step(pix, tgt, ss, sl, nsel, cfg.lr_scale * lr_sigma(step), cfg.lr_scale * lr_sh(step), next_pix=nxt)
     tr.finish()
     torch.cuda.synchronize()
     grid.check()

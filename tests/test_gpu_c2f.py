@@ -44,3 +44,54 @@ def test_coarse_to_fine_small(cuda_lib, prune_by):
     p0, p1 = psnr(start, truth), psnr(final, truth)
     print(f"coarse-to-fine 16->32->64 ({prune_by} prune): held-out PSNR {p0:.2f} dB -> {p1:.2f} dB; stages {log}")
     assert p1 > p0 + 3.0
+
+
+def test_tv_only_in_first_stage(cuda_lib):
+    """tv_until (Supp. B.2: the synthetic scenes keep TV in the first stage only): from that step on the
+    loop adds no TV gradient.  With the learning rates scaled to 0 the grid keeps its values, so each
+    step's touched rows depend only on its rays and TV segments: the loop's count of rows with a gradient
+    equals, exactly, that of the same batches stepped with TV before tv_until and the adjoint alone
+    after it, and TV would have added rows at every step after it."""
+    from paper_2112_05131_gb300.coarse_to_fine import C2FConfig, _Batches, train
+    from paper_2112_05131_gb300.grid import Grid, RenderOpts
+    from paper_2112_05131_gb300.train import StepConfig, Trainer
+
+    R, W, H = 24, 32, 32
+    rng = np.random.default_rng(5)
+    idx = np.arange(R ** 3, dtype=np.int32)
+    rows = rng.normal(0, 0.4, size=(R ** 3, 28)).astype(np.float32)
+    rows[:, 0] = rng.uniform(0.5, 20.0, size=R ** 3).astype(np.float32)
+    cams = synth.cameras(8, W, H, 40.0, 2.6, upper=False, seed=6)
+    cams_t = torch.from_numpy(cams).cuda()
+    images = rng.uniform(size=(8, H, W, 3)).astype(np.float32)
+    cfg = C2FConfig(steps=10, start_reso=R, upsample_at=(), batch=64, tv_segment=256, tv_fraction=0.1, chunk=10,
+                    tv_until=5, lambda_tv_sigma=1e-5, lambda_tv_sh=1e-3, track_touched=True, touched_every=1,
+                    lr_scale=0.0)
+    log = []
+    g = train(images, cams_t, W, H, cfg, log, start=Grid.from_host(R, idx, rows))
+    assert np.array_equal(g.rows[:, :28].cpu().numpy(), rows)  # zero learning rates: values unchanged
+    frac = log[-1]["touched_frac"]
+    got = np.array([round(frac[s] * g.M) for s in range(cfg.steps)])
+
+    def counts(tv_steps):
+        ref = Grid.from_host(R, idx, rows)
+        tr = Trainer(ref, cams_t, W, H, StepConfig(batch=cfg.batch, opts=RenderOpts(0.5, (1.0, 1.0, 1.0), 0.0),
+                                                  lambda_tv_sigma=cfg.lambda_tv_sigma, lambda_tv_sh=cfg.lambda_tv_sh,
+                                                  overlap=False, track_touched=True))
+        b = _Batches(images, cfg, cams_t.device)
+        for s in range(cfg.steps):
+            pix, tgt, ss, sl, nsel = b.get(s, R)
+            if s in tv_steps:
+                tr.step(pix, tgt, ss, sl, nsel, 0.0, 0.0)
+            else:
+                tr.step(pix, tgt, None, None, 0, 0.0, 0.0)
+        tr.finish()
+        return tr.touched_counts()
+
+    expect = counts(set(range(cfg.tv_until)))
+    with_tv = counts(set(range(cfg.steps)))
+    assert np.array_equal(got, expect), (got, expect)
+    assert np.all(with_tv[cfg.tv_until:] > got[cfg.tv_until:])
+    assert np.array_equal(with_tv[: cfg.tv_until], got[: cfg.tv_until])
+    print(f"touched rows per step (of {g.M}), TV until step {cfg.tv_until}: {got.tolist()}; with TV throughout "
+          f"{with_tv.tolist()}")
