@@ -63,9 +63,6 @@ def parse_args():
     ap.add_argument("--c2f-steps", type=int, default=12800)
     ap.add_argument("--c2f-prune", choices=("density", "weight"), default="density",
                     help="coarse-to-fine pruning: density >= 5, or maximum weight >= 0.256 (Sec. 3.4)")
-    ap.add_argument("--c2f-paper", action="store_true",
-                    help="run the coarse-to-fine loop on the paper's synthetic schedule instead (256^3 start, "
-                         "weight prune and upsample at 38400, 128000 steps, TV in stage 1 only; about 2 minutes)")
     ap.add_argument("--skip-large-batch", action="store_true", help="leave out the 2^18-ray batch measurement")
     ap.add_argument("--only-render", action="store_true",
                     help="profiling aid: only the full-frame renders of the held-out views (FP32, then BF16-SH), "
@@ -358,6 +355,68 @@ def run_ours(args, world, rank, local):
         print(json.dumps(out), flush=True)
 
 
+def algorithmic_bytes(grid, wl, cams_t, opts, batches, host_seg, n, max_touched=8, max_tv=4):
+    """Algorithmic bytes per launch of each stage of the step on these batches (device (pix, target,
+    seg_start, seg_len, n_selected) tuples; host_seg: their TV segments on the host), from the node and
+    sample counts of plx_count_nodes, the rows the adjoint and TV reach, and the TV nodes' rows in the
+    index volume.  Returns (bytes per stage, mean counts per batch)."""
+    import torch
+
+    from paper_2112_05131_gb300.grid import gen_rays
+    from paper_2112_05131_gb300.train import StepConfig, Trainer
+
+    R, W, H = wl["R"], wl["W"], wl["H"]
+    dev = cams_t.device
+    nodes = occ = samples = 0
+    for b in batches:
+        o, d = gen_rays(cams_t, b[0], W, H)
+        c = grid.count_nodes(o, d, opts).sum(0).cpu().numpy()
+        nodes += int(c[0])
+        occ += int(c[1])
+        samples += int(c[2])
+    K = len(batches)
+    nodes /= K
+    occ /= K
+    samples /= K
+    # forward (chunks + combine with the MSE gradient): rays, colours, targets and dL/dC, one index read per
+    # distinct node, one 112-byte row per distinct occupied node, and each sample's stored (sigma, pre)
+    # (16 B) and index (2 B)
+    fwd_bytes = n * (24 + 12 + 24) + 4 * nodes + 112 * occ + 18 * samples  # + target in, dL/dC out
+    # adjoint: rays and dL/dC, the stored per-sample values and indices, one index read per distinct node,
+    # and a read-modify-write of each distinct occupied row's 112-byte gradient
+    bwd_bytes = n * (24 + 12) + 18 * samples + 4 * nodes + 2 * 112 * occ
+    # RMSProp: every touched row's gradient, value and state read and written (6 x 112 B), the touched
+    # mask (1 bit per row) and the row list (4 B written, 4 B read per touched row)
+    tr_count = Trainer(grid, cams_t, W, H, StepConfig(batch=n, opts=opts))
+    touched = []
+    for b in batches[:max_touched]:
+        o, d = gen_rays(cams_t, b[0], W, H)
+        tr_count.grad.zero_()
+        grid.render_backward(o, d, torch.full((n, 3), 1e-3, device=dev), opts, tr_count.grad)
+        grid.tv_grad(b[2], b[3], b[4], 1e-5, 1e-3, tr_count.grad)
+        touched.append(int((tr_count.grad[:, :28] != 0).any(1).sum()))
+        grid.rmsprop_step(tr_count.grad, tr_count.v, 0.0, 0.0, sparse=True)  # clears gradient and marks
+    del tr_count
+    rms_bytes = float(np.mean(touched)) * (6 * 112 + 8) + grid.M / 8
+    # TV: three index streams per selected node (self/+z, +y, +x), and for every distinct occupied row
+    # among the active nodes' self and +x/+y/+z, its 112 bytes read and its gradient read and written
+    idx_np = wl["train"].idx
+    tv_b = []
+    for ss, sl in host_seg[:max_tv]:
+        sel = np.concatenate([np.arange(a0, a0 + l0) for a0, l0 in zip(ss, sl)])
+        i, j, k = sel // (R * R), (sel // R) % R, sel % R
+        rows = [idx_np[sel]]
+        rows.append(np.where(i + 1 < R, idx_np[np.minimum(sel + R * R, R ** 3 - 1)], -1))
+        rows.append(np.where(j + 1 < R, idx_np[np.minimum(sel + R, R ** 3 - 1)], -1))
+        rows.append(np.where(k + 1 < R, idx_np[np.minimum(sel + 1, R ** 3 - 1)], -1))
+        rows = np.stack(rows)
+        distinct = np.unique(rows[rows >= 0]).size
+        tv_b.append(12 * sel.size + 3 * 112 * distinct)
+    tv_bytes = float(np.mean(tv_b))
+    per_launch = {"render": fwd_bytes, "render_backward": bwd_bytes, "rmsprop_step": rms_bytes, "tv_grad": tv_bytes}
+    return per_launch, {"nodes": nodes, "occ": occ, "samples": samples, "touched": touched}
+
+
 def extras(args, wl, dev_batches, cams_t, gt_grid, opts, timed_loop, st32, ms32, st_overlap):
     import torch
 
@@ -383,58 +442,13 @@ def extras(args, wl, dev_batches, cams_t, gt_grid, opts, timed_loop, st32, ms32,
     # timed batches (node and sample counts from plx_count_nodes, TV rows from the index volume)
     peak, peak_kind = load_peaks()
     train32 = Grid.from_host(R, wl["train"].idx, wl["train"].rows)
-    nodes = occ = samples = 0
-    nb = len(dev_batches)
     K, Wm = args.steps, args.warmup
-    for s in range(K):
-        b = dev_batches[(Wm + s) % nb]
-        o, d = gen_rays(cams_t, b[0], W, H)
-        c = train32.count_nodes(o, d, opts).sum(0).cpu().numpy()
-        nodes += int(c[0])
-        occ += int(c[1])
-        samples += int(c[2])
-    nodes /= K
-    occ /= K
-    samples /= K
+    nb = len(dev_batches)
+    sel_b = [dev_batches[(Wm + s) % nb] for s in range(K)]
+    host_seg = [(wl["batches"][(Wm + s) % nb][1], wl["batches"][(Wm + s) % nb][2]) for s in range(K)]
+    per_launch, counts = algorithmic_bytes(train32, wl, cams_t, opts, sel_b, host_seg, args.batch)
+    nodes, occ, samples, touched = counts["nodes"], counts["occ"], counts["samples"], counts["touched"]
     n = args.batch
-    # forward (chunks + combine with the MSE gradient): rays, colours, targets and dL/dC, one index read per
-    # distinct node, one 112-byte row per distinct occupied node, and each sample's stored (sigma, pre)
-    # (16 B) and index (2 B)
-    fwd_bytes = n * (24 + 12 + 24) + 4 * nodes + 112 * occ + 18 * samples  # + target in, dL/dC out
-    # adjoint: rays and dL/dC, the stored per-sample values and indices, one index read per distinct node,
-    # and a read-modify-write of each distinct occupied row's 112-byte gradient
-    bwd_bytes = n * (24 + 12) + 18 * samples + 4 * nodes + 2 * 112 * occ
-    # RMSProp: every touched row's gradient, value and state read and written (6 x 112 B), the touched
-    # mask (1 bit per row) and the row list (4 B written, 4 B read per touched row)
-    tr_count = Trainer(train32, cams_t, W, H, StepConfig(batch=args.batch, opts=opts))
-    touched = []
-    for s in range(min(K, 8)):
-        b = dev_batches[(Wm + s) % nb]
-        o, d = gen_rays(cams_t, b[0], W, H)
-        tr_count.grad.zero_()
-        train32.render_backward(o, d, torch.full((args.batch, 3), 1e-3, device=dev), opts, tr_count.grad)
-        train32.tv_grad(b[2], b[3], b[4], 1e-5, 1e-3, tr_count.grad)
-        touched.append(int((tr_count.grad[:, :28] != 0).any(1).sum()))
-        train32.rmsprop_step(tr_count.grad, tr_count.v, 0.0, 0.0, sparse=True)  # clears gradient and marks
-    del tr_count
-    rms_bytes = float(np.mean(touched)) * (6 * 112 + 8) + train32.M / 8
-    # TV: three index streams per selected node (self/+z, +y, +x), and for every distinct occupied row
-    # among the active nodes' self and +x/+y/+z, its 112 bytes read and its gradient read and written
-    idx_np = wl["train"].idx
-    tv_b = []
-    for s in range(min(K, 4)):
-        ss, sl = wl["batches"][(Wm + s) % nb][1], wl["batches"][(Wm + s) % nb][2]
-        sel = np.concatenate([np.arange(a0, a0 + l0) for a0, l0 in zip(ss, sl)])
-        i, j, k = sel // (R * R), (sel // R) % R, sel % R
-        rows = [idx_np[sel]]
-        rows.append(np.where(i + 1 < R, idx_np[np.minimum(sel + R * R, R ** 3 - 1)], -1))
-        rows.append(np.where(j + 1 < R, idx_np[np.minimum(sel + R, R ** 3 - 1)], -1))
-        rows.append(np.where(k + 1 < R, idx_np[np.minimum(sel + 1, R ** 3 - 1)], -1))
-        rows = np.stack(rows)
-        distinct = np.unique(rows[rows >= 0]).size
-        tv_b.append(12 * sel.size + 3 * 112 * distinct)
-    tv_bytes = float(np.mean(tv_b))
-    per_launch = {"render": fwd_bytes, "render_backward": bwd_bytes, "rmsprop_step": rms_bytes, "tv_grad": tv_bytes}
     launches = {"render": "march_chunks_fwd + march_combine (with the MSE gradient)",
                 "render_backward": "march_chunks_bwd",
                 "rmsprop_step": "rms_compact + rms_apply", "tv_grad": "tv_kernel"}
@@ -459,6 +473,12 @@ def extras(args, wl, dev_batches, cams_t, gt_grid, opts, timed_loop, st32, ms32,
                           "bytes_per_launch": per_launch,
                           "GBps": {k: per_launch[k] / (st32[k] / 1e3) / 1e9 for k in per_launch},
                           "frac_of_peak": {k: per_launch[k] / (st32[k] / 1e3) / 1e9 / peak for k in per_launch}}
+    # the forward march's own roofline on the training batch (the frame kernel's is in render.*.roofline)
+    res["roofline_forward"] = {"batch": {
+        "kernel": launches["render"], "bound": "hbm", "achieved": per_launch["render"] / (st32["render"] / 1e3) / 1e9,
+        "peak": peak, "unit": "GB/s", "frac": per_launch["render"] / (st32["render"] / 1e3) / 1e9 / peak,
+        "algorithmic_bytes_per_launch": per_launch["render"], "rays": n,
+        "timing": "CUDA events around the stage, serial run"}}
 
     # ---- end to end through the public API with host buffers (pinned), copies inside the timed region.
     # Each batch's inputs (pixel ids, targets, TV segment starts and lengths) sit in one pinned host buffer
@@ -542,6 +562,10 @@ def extras(args, wl, dev_batches, cams_t, gt_grid, opts, timed_loop, st32, ms32,
     if not args.skip_c2f and wl["test_cams"]:
         res["coarse_to_fine"] = coarse_to_fine(args, wl, cams_t, gt_grid, opts)
         torch.cuda.empty_cache()
+        # the paper's own synthetic schedule (Supp. B.2): 256^3 start, weight prune at 0.256 and upsample to
+        # 512^3 after 38400 of 128000 steps, TV in the first stage only
+        res["coarse_to_fine_paper"] = coarse_to_fine(args, wl, cams_t, gt_grid, opts, paper=True)
+        torch.cuda.empty_cache()
 
     # ---- coarse-to-fine grid operations on this workload's grid
     g = Grid.from_host(R, wl["train"].idx, wl["train"].rows)
@@ -603,7 +627,14 @@ def extras(args, wl, dev_batches, cams_t, gt_grid, opts, timed_loop, st32, ms32,
             del gh
 
     # ---- CPU oracle baseline on a bounded sample of the same workload
-    res["cpu_baseline"] = cpu_baseline(args, wl, budget_s=args.cpu_seconds)
+    res["cpu_baseline"] = cpu_baseline(args, wl, budget_s=args.cpu_seconds, dev=dev, opts=opts)
+    acc = res["cpu_baseline"].get("accuracy")
+    if acc:
+        # each result's colour error and PSNR loss against the FP64 oracle, beside its timing
+        for name in ("f32", "bf16_sh"):
+            if "render" in res and name in res["render"]:
+                res["render"][name]["accuracy"] = acc["render"][name]
+        res["bf16_sh"]["accuracy"] = acc["train_forward"]["bf16_sh"]
     return res
 
 
@@ -627,8 +658,15 @@ def frame_renders(args, wl, dev, opts, forms=((0, "f32"), (1, "bf16_sh"))):
         frames.append(gen_rays(tc_t, pix, W, H))
     rgb = torch.empty((npx, 3), device=dev)
     out = {}
+    peak, peak_kind = load_peaks()
+    nodes = occ = 0
     for form, name in forms:
         g = Grid.from_host(R, wl["gt"].idx, wl["gt"].rows, sh_form=form)
+        if form == 0:  # distinct nodes and occupied nodes per frame (the same for both forms)
+            for o, d in frames:
+                c = g.count_nodes(o, d, opts).sum(0).cpu().numpy()
+                nodes += int(c[0]) / len(frames)
+                occ += int(c[1]) / len(frames)
         for o, d in frames[:3]:
             g.render(o, d, opts, rgb)
         times = []
@@ -642,15 +680,28 @@ def frame_renders(args, wl, dev, opts, forms=((0, "f32"), (1, "bf16_sh"))):
         torch.cuda.synchronize()
         g.check()
         ms = np.array([x.elapsed_time(y) for x, y in times])
+        # algorithmic bytes of a frame: rays in (24 B) and colours out (12 B) per pixel, one index read per
+        # distinct node of the sampled non-empty cells, one row per distinct occupied node (112 B F32;
+        # 4 + 27 x 2 = 58 B BF16-SH)
+        row_b = 58 if form == 1 else 112
+        fb = npx * 36 + 4 * nodes + row_b * occ
+        ach = fb / (ms.mean() / 1e3) / 1e9
         out[name] = {"p50_ms": float(np.percentile(ms, 50)), "p99_ms": float(np.percentile(ms, 99)),
                      "mean_ms": float(ms.mean()), "frames": int(ms.size),
-                     "Mrays_per_s": npx / (ms.mean() / 1e3) / 1e6, "resolution": f"{W}x{H}"}
+                     "Mrays_per_s": npx / (ms.mean() / 1e3) / 1e6, "resolution": f"{W}x{H}",
+                     "roofline": {"kernel": "render_fwd_kernel", "bound": "hbm", "achieved": ach, "peak": peak,
+                                  "unit": "GB/s", "frac": ach / peak, "peak_source": f"{peak_kind} hbm_gbs, burst",
+                                  "algorithmic_bytes_per_launch": fb,
+                                  "distinct_nodes_per_ray": nodes / npx, "occupied_nodes_per_ray": occ / npx,
+                                  "timing": "mean of the frames' CUDA-event times"}}
         del g
     return out
 
 
 def large_batch(args, wl, cams_t, gt_grid, opts, n=1 << 18, steps=8, warmup=3):
-    """The same optimisation step on 2^18-ray batches of the workload (FP32 rows)."""
+    """The same optimisation step on 2^18-ray batches of the workload (FP32 rows): the overlapped step's
+    rate, then the same steps serially with CUDA events between the stages, and each stage's algorithmic
+    bandwidth against the peak, as for the 5000-ray batch."""
     import torch
 
     import synth
@@ -659,40 +710,64 @@ def large_batch(args, wl, cams_t, gt_grid, opts, n=1 << 18, steps=8, warmup=3):
 
     R, W, H = wl["R"], wl["W"], wl["H"]
     dev = cams_t.device
-    batches = []
+    batches, host_seg = [], []
     for b in range(4):
         pix = torch.from_numpy(synth.pixel_batch(wl["n_views"], W, H, n, seed=5000 + b)).to(dev)
         o, d = gen_rays(cams_t, pix, W, H)
         ss, sl = synth.tv_segments(R, wl["tv_fraction"], 4096 if R >= 128 else 256, seed=6000 + b)
         batches.append((pix, gt_grid.render(o, d, opts), torch.from_numpy(ss).to(dev), torch.from_numpy(sl).to(dev),
                         int(sl.sum())))
+        host_seg.append((ss, sl))
         del o, d
-    g = Grid.from_host(R, wl["train"].idx, wl["train"].rows)
-    tr = Trainer(g, cams_t, W, H, StepConfig(batch=n, opts=opts))
-    for s in range(warmup):
-        b = batches[s % 4]
-        tr.step(b[0], b[1], b[2], b[3], b[4], lr_sigma(s), lr_sh(s),
-                next_pix=batches[(s + 1) % 4][0] if s + 1 < warmup else None)
-    tr.finish()
     stream = torch.cuda.current_stream()
-    a, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    torch.cuda.synchronize()
-    a.record(stream)
-    for s in range(steps):
-        b = batches[s % 4]
-        tr.step(b[0], b[1], b[2], b[3], b[4], lr_sigma(warmup + s), lr_sh(warmup + s),
-                next_pix=batches[(s + 1) % 4][0] if s + 1 < steps else None)
-    tr.finish()
-    e.record(stream)
-    torch.cuda.synchronize()
-    ms = a.elapsed_time(e)
-    g.check()
-    del tr, g, batches
+
+    def run(overlap, per_stage):
+        g = Grid.from_host(R, wl["train"].idx, wl["train"].rows)
+        tr = Trainer(g, cams_t, W, H, StepConfig(batch=n, opts=opts, overlap=overlap))
+        for s in range(warmup):
+            b = batches[s % 4]
+            tr.step(b[0], b[1], b[2], b[3], b[4], lr_sigma(s), lr_sh(s),
+                    next_pix=batches[(s + 1) % 4][0] if s + 1 < warmup else None)
+        tr.finish()
+        evs = [[torch.cuda.Event(enable_timing=True) for _ in range(8)] for _ in range(steps)] if per_stage else None
+        a, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        a.record(stream)
+        for s in range(steps):
+            b = batches[s % 4]
+            tr.step(b[0], b[1], b[2], b[3], b[4], lr_sigma(warmup + s), lr_sh(warmup + s),
+                    events=evs[s] if per_stage else None,
+                    next_pix=batches[(s + 1) % 4][0] if s + 1 < steps else None)
+        tr.finish()
+        e.record(stream)
+        torch.cuda.synchronize()
+        ms = a.elapsed_time(e)
+        stages = None
+        if per_stage:
+            names = [nm.split("|")[-1 if overlap else 0] for nm in Trainer.STAGES]
+            stages = {name: statistics.mean(ev[i].elapsed_time(ev[i + 1]) for ev in evs)
+                      for i, name in enumerate(names) if name != "-"}
+        g.check()
+        del tr, g
+        return ms, stages
+
+    ms, _ = run(True, False)
+    ms_serial, st = run(False, True)
+    peak, _ = load_peaks()
+    g = Grid.from_host(R, wl["train"].idx, wl["train"].rows)
+    per_launch, counts = algorithmic_bytes(g, wl, cams_t, opts, batches, host_seg, n, max_touched=4)
+    del g, batches
+    gbps = {k: per_launch[k] / (st[k] / 1e3) / 1e9 for k in per_launch}
     return {"value": steps * n / (ms / 1e3), "unit": "rays/s", "batch": n, "steps": steps,
-            "ms_per_step": ms / steps, "rows": "f32"}
+            "ms_per_step": ms / steps, "rows": "f32",
+            "serial_ms_per_step": ms_serial / steps, "stage_ms_serial": st,
+            "algorithmic_bytes_per_launch": per_launch, "GBps": gbps,
+            "frac_of_peak": {k: v / peak for k, v in gbps.items()},
+            "touched_rows_per_step": float(np.mean(counts["touched"])),
+            "marched_samples_per_ray": counts["samples"] / n}
 
 
-def coarse_to_fine(args, wl, cams_t, gt_grid, opts):
+def coarse_to_fine(args, wl, cams_t, gt_grid, opts, paper=False):
     """Training images = the ground truth rendered for the 100 training views; a dense 128^3 start (sigma 0.1,
     SH 0); prune (sigma < 5, or maximum weight < 0.256 with --c2f-prune weight; dilated) and upsample at steps
     4266 and 8533 of 12800; TV 5e-4 / 1e-3 on 1% of the nodes; PSNR on the 25 held-out views against the ground
@@ -709,7 +784,7 @@ def coarse_to_fine(args, wl, cams_t, gt_grid, opts):
     test_t = torch.from_numpy(synth.cameras_config(wl["test_cams"])).to(cams_t.device)
     truth = render_views(gt_grid, test_t, W, H, opts)
     prep = time.perf_counter() - t0
-    if args.c2f_paper:
+    if paper:
         from paper_2112_05131_gb300.coarse_to_fine import paper_synthetic
 
         cfg = paper_synthetic()
@@ -732,11 +807,14 @@ def coarse_to_fine(args, wl, cams_t, gt_grid, opts):
     return out
 
 
-def serving(args, opts, n_requests=240, loads=(0.5, 0.8, 0.95)):
+def serving(args, opts, n_requests=2000, n_closed=480, loads=(0.5, 0.8, 0.95)):
     """Four resident BF16-SH scenes (128^3, 256^3, 384^3, 512^3 at 8% occupancy, blobs and shell); requests of
     256^2, 800^2, 1280x720 or 1920x1080 pixels from cameras on the upper hemisphere r = 4.  Capacity is the
-    closed-loop throughput (all requests queued at once); then Poisson arrivals at 50/80/95% of it.  Latency
-    runs from arrival to the image in pinned host memory."""
+    closed-loop throughput (n_closed requests queued at once); then n_requests Poisson arrivals at each of
+    50/80/95% of it, so that each p99 rests on 20 requests.  Latency runs from arrival to the image in pinned
+    host memory; the admission wait (arrival to leaving the queue, for a camera slot and device memory) is
+    reported beside it.  The server's memory budget is the device's free memory after loading the scenes,
+    less 10%."""
     import torch
 
     import synth
@@ -757,7 +835,7 @@ def serving(args, opts, n_requests=240, loads=(0.5, 0.8, 0.95)):
     gen_s = time.time() - t0
     srv = TileServer(grids, opts, max_rays_per_launch=1 << 19, max_inflight=2, max_active=48)
     srv.run(requests_from(synth.serving_requests(24, 4, seed=100)))  # warm-up: pools, caches
-    closed = requests_from(synth.serving_requests(n_requests, 4, seed=101))
+    closed = requests_from(synth.serving_requests(n_closed, 4, seed=101))
     t = time.perf_counter()
     done = srv.run(closed)
     wall = time.perf_counter() - t
@@ -765,7 +843,8 @@ def serving(args, opts, n_requests=240, loads=(0.5, 0.8, 0.95)):
     capacity_rps = len(done) / wall
     out = {"scenes": [f"{R}^3 ({g.M} rows, BF16 SH)" for R, g in zip(sizes, grids)],
            "capacity": {"requests_per_s": capacity_rps, **cap}, "scene_gen_s": gen_s,
-           "max_rays_per_launch": 1 << 19, "tile": "16x16"}
+           "max_rays_per_launch": 1 << 19, "tile": "16x16", "memory_budget_bytes": srv.mem_budget,
+           "requests_per_load": n_requests}
     for load in loads:
         rate = load * capacity_rps
         reqs = requests_from(synth.serving_requests(n_requests, 4, seed=200 + int(100 * load), rate=rate))
@@ -773,14 +852,16 @@ def serving(args, opts, n_requests=240, loads=(0.5, 0.8, 0.95)):
         done = srv.run(reqs)
         wall = time.perf_counter() - t
         out[f"load_{int(100 * load)}"] = {"rate_per_s": rate, **latency_stats(done, wall)}
+    out["memory_peak_bytes"] = srv.mem_peak
     del srv, grids
     return out
 
 
 # --------------------------------------------------------------------------- CPU oracle
-def cpu_baseline(args, wl, budget_s=15.0):
+def cpu_baseline(args, wl, budget_s=15.0, dev=None, opts=None):
     """The FP64 oracle, as it stands, on whole batches of the same workload (ray generation, forward,
-    MSE and adjoint), batch after batch until the time budget is spent."""
+    MSE and adjoint), batch after batch until the time budget is spent; with a device, also the
+    accuracy of both row forms against it (_oracle_accuracy)."""
     import oracle
 
     R = wl["R"]
@@ -818,11 +899,69 @@ def cpu_baseline(args, wl, budget_s=15.0):
         t1 = time.perf_counter() - t0
     finally:
         oracle.set_num_threads(cores)
-    return {"value": rays / spent, "unit": "rays/s", "cores": cores, "kind": "oracle",
-            "sample": f"{b} batches of {args.batch} rays ({rays} rays) of the {R}^3 workload: ray generation, "
-                      "forward, MSE and adjoint in FP64, OpenMP over rays", "seconds": spent,
-            "single_core": {"value": pix.shape[0] / t1, "unit": "rays/s", "cores": 1,
-                            "sample": f"the first {pix.shape[0]} rays of one batch", "seconds": t1}}
+    out = {"value": rays / spent, "unit": "rays/s", "cores": cores, "kind": "oracle",
+           "sample": f"{b} batches of {args.batch} rays ({rays} rays) of the {R}^3 workload: ray generation, "
+                     "forward, MSE and adjoint in FP64, OpenMP over rays", "seconds": spent,
+           "single_core": {"value": pix.shape[0] / t1, "unit": "rays/s", "cores": 1,
+                           "sample": f"the first {pix.shape[0]} rays of one batch", "seconds": t1}}
+    if dev is not None and wl["test_cams"]:
+        out["accuracy"] = _oracle_accuracy(wl, dev, opts)
+    return out
+
+
+def _oracle_accuracy(wl, dev, opts, per_view=64, seed=77):
+    """Part of the CPU-baseline leg: colour error and PSNR of both row forms against the FP64 oracle, on
+    `per_view` seeded pixels of every held-out view (the training grid, ground truth plus N(0, 0.02), so
+    that PSNR against the ground truth is finite).  Both the frame kernel (plx_render) and the training
+    forward (plx_render_train) render the pixels' rays as plx_gen_rays makes them; the oracle renders the
+    same FP32 rays on the F32 values, on the BF16-rounded values, and on the ground truth (the target).
+    colour_err_max is max |GPU - oracle on the same row values|; psnr_loss_db is PSNR(F32 vs target) -
+    PSNR(BF16-SH vs target)."""
+    import torch
+
+    import oracle
+    import synth
+    from paper_2112_05131_gb300.grid import Grid, gen_rays
+
+    R, W, H = wl["R"], wl["W"], wl["H"]
+    tc = synth.cameras_config(wl["test_cams"])
+    rng = np.random.default_rng(seed)
+    pix = np.concatenate([v * W * H + rng.choice(W * H, per_view, replace=False) for v in range(tc.shape[0])])
+    o, d = gen_rays(torch.from_numpy(tc).to(dev), torch.from_numpy(pix.astype(np.int64)).to(dev), W, H)
+    train = wl["train"]
+    rows16 = train.rows.astype(np.float32).copy()
+    rows16[:, 1:] = oracle.round_bf16(rows16[:, 1:])
+    o64, d64 = o.cpu().numpy().astype(np.float64), d.cpu().numpy().astype(np.float64)
+    kw = dict(step_vox=opts.step_vox, bg=opts.bg, stop_thresh=opts.stop_thresh)
+    target, _ = oracle.render(R, wl["gt"].idx, wl["gt"].rows.astype(np.float64), o64, d64, **kw)
+    ref = {0: oracle.render(R, train.idx, train.rows.astype(np.float64), o64, d64, **kw)[0],
+           1: oracle.render(R, train.idx, rows16.astype(np.float64), o64, d64, **kw)[0]}
+
+    def psnr(a, b):
+        return float(-10.0 * np.log10(np.mean((a - b) ** 2)))
+
+    out = {"pixels": int(pix.size), "sample": f"{per_view} seeded pixels of each of {tc.shape[0]} held-out views"}
+    for kernel in ("render", "train_forward"):
+        got = {}
+        for form in (0, 1):
+            g = Grid.from_host(R, train.idx, train.rows, sh_form=form)
+            if kernel == "render":
+                rgb = g.render(o, d, opts)
+            else:
+                rgb = g.render_train(o, d, opts, g.new_march_state(o.shape[0], opts))
+            got[form] = rgb.cpu().numpy().astype(np.float64)
+            del g
+        ent = {}
+        for form, name in ((0, "f32"), (1, "bf16_sh")):
+            err = np.abs(got[form] - ref[form])
+            ent[name] = {"colour_err_max": float(err.max()),
+                         "colour_err_rel_max": float(np.max(err / np.maximum(np.abs(ref[form]), 1e-3))),
+                         "psnr_vs_target_db": psnr(got[form], target)}
+        ent["bf16_sh"]["psnr_loss_db"] = ent["f32"]["psnr_vs_target_db"] - ent["bf16_sh"]["psnr_vs_target_db"]
+        ent["bf16_sh"]["psnr_vs_oracle_f32_db"] = psnr(got[1], ref[0])
+        out[kernel] = ent
+    torch.cuda.empty_cache()
+    return out
 
 
 def run_reference(args, world, rank):
