@@ -480,66 +480,41 @@ def extras(args, wl, dev_batches, cams_t, gt_grid, opts, timed_loop, st32, ms32,
         "algorithmic_bytes_per_launch": per_launch["render"], "rays": n,
         "timing": "CUDA events around the stage, serial run"}}
 
-    # ---- end to end through the public API with host buffers (pinned), copies inside the timed region.
-    # Each batch's inputs (pixel ids, targets, TV segment starts and lengths) sit in one pinned host buffer
-    # and go to the device in one copy, one step ahead (two device buffers), so that the next batch is
-    # planned beside this step's march (Trainer.step's next_pix); the first step of a loop also copies its
-    # own.  Each step reads its loss back to pinned host memory.
-    tr = Trainer(train32, cams_t, W, H, StepConfig(batch=args.batch, opts=opts))
+    # ---- end to end through the public API with host buffers (page-locked), copies inside the timed region:
+    # each step is one plx_trainer_step_host call, which uploads the next batch's inputs (pixel ids, targets,
+    # TV segment starts and lengths) and plans them during this step's march, and downloads the step's loss
+    # beside the adjoint; the first step of a loop uploads its own inputs at its start.
     n = args.batch
     max_seg = max(ss.shape[0] for _, ss, _ in wl["batches"])
-    nbytes = n * 8 + n * 12 + 2 * max_seg * 8
-    host = []
+    tr = Trainer(train32, cams_t, W, H, StepConfig(batch=n, opts=opts, max_segments=max_seg))
+    hb, h2d_b = [], []
     for i, (pix, ss, sl) in enumerate(wl["batches"]):
-        buf = torch.zeros(nbytes, dtype=torch.uint8).pin_memory()
-        # int64 parts first (8-byte aligned views), then the FP32 targets
-        parts = [torch.from_numpy(pix).view(torch.uint8),
-                 torch.from_numpy(np.pad(ss, (0, max_seg - ss.shape[0]))).view(torch.uint8),
-                 torch.from_numpy(np.pad(sl, (0, max_seg - sl.shape[0]))).view(torch.uint8),
-                 dev_batches[i][1].cpu().view(torch.uint8).reshape(-1)]
-        torch.cat(parts, out=buf)
-        host.append((buf, ss.shape[0], int(sl.sum())))
-    d_buf = [torch.empty(nbytes, dtype=torch.uint8, device=dev) for _ in range(2)]
-
-    def views(buf, ns):
-        o_ss, o_sl, o_tgt = n * 8, n * 8 + max_seg * 8, n * 8 + 2 * max_seg * 8
-        pix = buf[:o_ss].view(torch.int64)
-        ss = buf[o_ss:o_sl].view(torch.int64)[:ns]
-        sl = buf[o_sl:o_tgt].view(torch.int64)[:ns]
-        tgt = buf[o_tgt:].view(torch.float32).view(n, 3)
-        return pix, tgt, ss, sl
-
-    dv = [views(b, max_seg) for b in d_buf]
-    loss_host = torch.empty(1, dtype=torch.float32).pin_memory()
+        hb.append(Trainer.host_batch(torch.from_numpy(pix).pin_memory(), dev_batches[i][1].cpu().pin_memory(),
+                                     torch.from_numpy(ss).pin_memory(), torch.from_numpy(sl).pin_memory(),
+                                     int(sl.sum())))
+        h2d_b.append(n * 8 + n * 12 + 16 * ss.shape[0])
+    loss_host = [torch.zeros(1, dtype=torch.float32).pin_memory() for _ in range(2)]
     stream = torch.cuda.current_stream()
 
-    def e2e_step(s, first, last):
-        h = host[s % nb]
-        cur, nxt = s % 2, (s + 1) % 2
-        if first:
-            d_buf[cur].copy_(h[0], non_blocking=True)
-        if not last:
-            d_buf[nxt].copy_(host[(s + 1) % nb][0], non_blocking=True)
-        pix, tgt, ss, sl = dv[cur]
-        tr.loss.zero_()
-        tr.step(pix, tgt, ss[: h[1]], sl[: h[1]], h[2], lr_sigma(s), lr_sh(s), next_pix=None if last else dv[nxt][0])
-        loss_host.copy_(tr.loss, non_blocking=True)
+    def e2e_step(s, last):
+        tr.step_host(hb[s % nb], lr_sigma(s), lr_sh(s), next_batch=None if last else hb[(s + 1) % nb],
+                     loss_out=loss_host[s % 2])
 
     for s in range(args.warmup):
-        e2e_step(s, s == 0, s == args.warmup - 1)
+        e2e_step(s, s == args.warmup - 1)
     tr.finish()
     torch.cuda.synchronize()
     a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     a.record(stream)
     for s in range(K):
-        e2e_step(Wm + s, s == 0, s == K - 1)
+        e2e_step(Wm + s, s == K - 1)
     tr.finish()
     b.record(stream)
     torch.cuda.synchronize()
     ms_e2e = a.elapsed_time(b)
-    h2d = nbytes
+    h2d = float(np.mean([h2d_b[(Wm + s) % nb] for s in range(K)]))
     res["e2e"] = {"value": K * args.batch / (ms_e2e / 1e3), "unit": "rays/s", "h2d_bytes_per_step": h2d,
-                  "d2h_bytes_per_step": 4, "ms_per_step": ms_e2e / K}
+                  "d2h_bytes_per_step": 4, "ms_per_step": ms_e2e / K, "api": "plx_trainer_step_host"}
     del tr, train32
     torch.cuda.empty_cache()
 

@@ -462,6 +462,7 @@ typedef struct {
     float beta;               /* RMSProp (Sec. 3.5) */
     float eps;
     int32_t sparse_rmsprop;   /* 1: update only rows marked touched (plx_rmsprop_step) */
+    int32_t max_segments;     /* most TV segments of a host-fed step (plx_trainer_step_host); 0: none */
 } plx_trainer_desc;
 
 /* Device workspace of a trainer for this grid and descriptor (0 for
@@ -492,6 +493,35 @@ plx_status plx_trainer_step(plx_trainer *trainer, const int64_t *d_pix, int64_t 
                             float lr_sigma, float lr_sh, const int64_t *d_next_pix, int32_t pix_is_ahead,
                             float *d_loss, float *d_loss_sparsity, int64_t *d_touched, void *const *events,
                             int32_t *set_out, void *stream);
+
+/* A batch in host memory for plx_trainer_step_host: pixel ids int64 [n],
+ * targets float [n][3] and TV segments int64 [n_seg] (NULL or n_seg = 0 for
+ * none; n_selected nodes in all).  The buffers should be page-locked
+ * (cudaHostAlloc or registered) so that the copies are asynchronous; they are
+ * the caller's and must stay unchanged until the step that reads them has
+ * completed. */
+typedef struct {
+    const int64_t *pix;
+    const float *target;
+    const int64_t *seg_start;
+    const int64_t *seg_len;
+    int64_t n, n_seg, n_selected;
+} plx_host_batch;
+
+/* One step of plx_trainer_step fed from host memory, for callers whose
+ * batches are produced on the host: the batch's inputs are copied into the
+ * trainer's own device buffers (two sets) and the step's MSE is copied back
+ * to *h_loss (page-locked; nullable).  With `next` (nullable) the following
+ * batch's inputs are copied and planned during this step's march, so that the
+ * next call, passing the same host arrays (the same pix pointer and n) as
+ * `batch`, starts with them on the device; otherwise its inputs are copied at
+ * its start.  The copies run on the trainer's streams beside the march: the
+ * next batch's upload before its plan, the loss download once the forward has
+ * produced it, beside the adjoint.  n <= batch and n_seg <= max_segments of
+ * the descriptor.  `stream` is ordered as for plx_trainer_step and also waits
+ * for the loss download, so that *h_loss is complete once `stream` is. */
+plx_status plx_trainer_step_host(plx_trainer *trainer, const plx_host_batch *batch, const plx_host_batch *next,
+                                 float lr_sigma, float lr_sh, float *h_loss, void *stream);
 
 /* Applies the pending update on `stream`. */
 plx_status plx_trainer_finish(plx_trainer *trainer, void *stream);

@@ -38,7 +38,13 @@ class plx_render_opts(ctypes.Structure):
 
 class plx_trainer_desc(ctypes.Structure):
     _fields_ = [("batch", c_int32), ("opts", plx_render_opts), ("lambda_tv_sigma", c_float), ("lambda_tv_sh", c_float),
-                ("lambda_sparsity", c_float), ("beta", c_float), ("eps", c_float), ("sparse_rmsprop", c_int32)]
+                ("lambda_sparsity", c_float), ("beta", c_float), ("eps", c_float), ("sparse_rmsprop", c_int32),
+                ("max_segments", c_int32)]
+
+
+class plx_host_batch(ctypes.Structure):
+    _fields_ = [("pix", c_void_p), ("target", c_void_p), ("seg_start", c_void_p), ("seg_len", c_void_p),
+                ("n", c_int64), ("n_seg", c_int64), ("n_selected", c_int64)]
 
 
 # name -> (restype, argtypes); every name here is declared in include/plenoxel.h
@@ -81,6 +87,8 @@ SIGNATURES = {
     "plx_trainer_step": (c_int32, [c_void_p, c_void_p, c_int64, c_void_p, c_void_p, c_void_p, c_int64, c_int64, c_float,
                                    c_float, c_void_p, c_int32, c_void_p, c_void_p, c_void_p, c_void_p,
                                    ctypes.POINTER(c_int32), c_void_p]),
+    "plx_trainer_step_host": (c_int32, [c_void_p, ctypes.POINTER(plx_host_batch), ctypes.POINTER(plx_host_batch),
+                                        c_float, c_float, c_void_p, c_void_p]),
     "plx_trainer_finish": (c_int32, [c_void_p, c_void_p]),
     "plx_trainer_buffers": (c_int32, [c_void_p, c_int32, ctypes.POINTER(c_void_p), ctypes.POINTER(c_void_p),
                                       ctypes.POINTER(c_void_p), ctypes.POINTER(c_void_p), ctypes.POINTER(c_size_t)]),

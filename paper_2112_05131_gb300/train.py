@@ -68,6 +68,8 @@ class StepConfig:
     # record, every step, how many rows received a gradient (plx_count_touched; Sec. 3.8's gradient
     # sparsity), into Trainer.touched_counts()
     track_touched: bool = False
+    # most TV segments of a step fed from host memory (step_host)
+    max_segments: int = 0
 
 
 class Trainer:
@@ -100,6 +102,7 @@ class Trainer:
             desc.lambda_sparsity = float(cfg.lambda_sparsity)
             desc.beta, desc.eps = float(cfg.beta), float(cfg.eps)
             desc.sparse_rmsprop = 1 if cfg.sparse_rmsprop else 0
+            desc.max_segments = int(cfg.max_segments)
             nbytes = int(L.load().plx_trainer_workspace_bytes(grid.handle, ctypes.byref(desc)))
             if nbytes == 0:
                 raise ValueError("no trainer workspace for this grid and batch")
@@ -162,6 +165,37 @@ class Trainer:
     def _update(self, main, lrs):
         c = self.cfg
         self.grid.rmsprop_step(self.grad, self.v, lrs[0], lrs[1], c.beta, c.eps, sparse=c.sparse_rmsprop, stream=main)
+
+    @staticmethod
+    def host_batch(pix: torch.Tensor, target: torch.Tensor, seg_start: Optional[torch.Tensor] = None,
+                   seg_len: Optional[torch.Tensor] = None, n_selected: int = 0):
+        """A batch in (page-locked) host memory for step_host: the tensors are referenced, not copied."""
+        for t, dt, name in ((pix, torch.int64, "pix"), (target, torch.float32, "target")):
+            if t.device.type != "cpu" or t.dtype != dt or not t.is_contiguous():
+                raise ValueError(f"{name}: a contiguous host tensor of {dt} is required")
+        b = L.plx_host_batch()
+        b.pix, b.target = pix.data_ptr(), target.data_ptr()
+        b.n = pix.shape[0]
+        if seg_start is not None and n_selected > 0:
+            b.seg_start, b.seg_len = seg_start.data_ptr(), seg_len.data_ptr()
+            b.n_seg, b.n_selected = seg_start.shape[0], int(n_selected)
+        b._keep = (pix, target, seg_start, seg_len)
+        return b
+
+    def step_host(self, batch, lr_s: float, lr_h: float, next_batch=None, loss_out: Optional[torch.Tensor] = None,
+                  stream=None):
+        """One overlapped step fed from host memory (plx_trainer_step_host): `batch` and `next_batch` come from
+        host_batch; the step's MSE lands in `loss_out` (a page-locked float32 host tensor of one element)
+        once `stream` (default: the current stream) has reached the step's end."""
+        if self._native is None:
+            raise RuntimeError("host-fed steps need the native (overlap) trainer")
+        if loss_out is not None and (loss_out.device.type != "cpu" or loss_out.dtype != torch.float32):
+            raise ValueError("loss_out: a float32 host tensor is required")
+        main = stream if stream is not None else torch.cuda.current_stream()
+        L.call("plx_trainer_step_host", self._native, ctypes.byref(batch),
+               ctypes.byref(next_batch) if next_batch is not None else None, float(lr_s), float(lr_h),
+               _p(loss_out) if loss_out is not None else None, _stream(main))
+        self._ahead = None
 
     def finish(self, stream=None):
         """Applies the pending RMSProp update (overlap mode defers each step's update to the next call)."""
