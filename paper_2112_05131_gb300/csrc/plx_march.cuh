@@ -228,6 +228,8 @@ __device__ __forceinline__ bool gather_sample(const GridView &g, int form, const
 #pragma unroll
         for (int k = 0; k < 8; ++k) {
             const float w = slot_weight(cn, k);
+            // scalar FMAs: packed pairs (fma.rn.f32x2) measured no faster here (the F32 gather is bound by
+            // its loads, not by FMA issue)
 #pragma unroll
             for (int q = 0; q < kNV; ++q) acc[q] = fmaf(w, v[k][q >> 3].v[q & 7], acc[q]);
         }
@@ -345,8 +347,10 @@ __device__ __forceinline__ Composite composite(float sig, bool valid, float Tc, 
 // skipped sample lies in a cell whose 8 corners are NULL (all values zero):
 // its alpha is exactly 0, it multiplies T by exactly 1 and adds nothing, so
 // the compacted march evaluates the same sum.
-constexpr int kCand = 8;    // candidates per lane per refill
-constexpr int kRing = 512;  // ring capacity >= 31 + 32 kCand, a power of two
+constexpr int kGroupLog = 3;
+constexpr int kCand = 1 << kGroupLog;  // candidates per lane per refill
+constexpr int kRing = kCand <= 8 ? 512 : 1024;  // ring capacity >= 31 + 32 kCand, a power of two
+static_assert(kRing >= 31 + 32 * kCand, "ring capacity");
 
 // Is the cell of sample s (s_lo <= s < s_hi: every such sample is before t_far) non-empty?  The answer
 // must equal the double-float one exactly (it decides which samples are marched).  Plain FP32
@@ -399,9 +403,9 @@ __device__ __forceinline__ bool test_candidate(const GridView &g, const RaySetup
 // --------------------------------------------------------------------------- coarse skipping
 // Before the per-sample test, candidates are screened in groups of kGroup consecutive samples
 // against the coarse mask (one bit per 8^3-cell block): a group none of whose samples can lie in a
-// non-empty cell is skipped whole.  A round of 32 kCand = 256 candidates is 32 groups, one per lane;
-// candidate 32 j + l of the round belongs to group 4 j + l / 8.
-constexpr int kGroup = 8;
+// non-empty cell is skipped whole.  A round of 32 kCand candidates is 32 groups, one per lane;
+// candidate 32 j + l of the round belongs to group (32 j + l) / kGroup.
+constexpr int kGroup = 1 << kGroupLog;
 static_assert(32 * kCand == 32 * kGroup, "a round is one group per lane");
 
 // Can a sample with index in [s0, s0 + kGroup) lie in a cell with an occupied corner?  Never false
@@ -441,7 +445,7 @@ __device__ __forceinline__ unsigned test_round(const GridView &g, const RaySetup
 #pragma unroll
     for (int j = 0; j < kCand; ++j) {
         const int s = first + 32 * j + lane;
-        occ[j] = ((live >> (4 * j + (lane >> 3))) & 1u) && s < end && test_candidate(g, rs, s);
+        occ[j] = ((live >> ((32 * j + lane) >> kGroupLog)) & 1u) && s < end && test_candidate(g, rs, s);
     }
     return live;
 }
