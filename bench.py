@@ -186,7 +186,7 @@ def load_peaks():
 # DRAM traffic of the step's kernels, from a one-pass ncu capture summarised in profiles/, valid only
 # while the library's sources are those the capture ran (their digest is recorded beside the table)
 TRAFFIC_PROFILE = os.path.join(ROOT, "profiles", "traffic_sparse512.md")
-STAGE_KERNELS = {"render": ("march_chunks_fwd_kernel", "march_combine_kernel"),
+STAGE_KERNELS = {"render": ("march_chunks_fwd_kernel",),
                  "render_backward": ("march_chunks_bwd_kernel",),
                  "rmsprop_step": ("rms_compact_kernel", "rms_apply_kernel"),
                  "tv_grad": ("tv_kernel",)}
@@ -449,7 +449,7 @@ def extras(args, wl, dev_batches, cams_t, gt_grid, opts, timed_loop, st32, ms32,
     per_launch, counts = algorithmic_bytes(train32, wl, cams_t, opts, sel_b, host_seg, args.batch)
     nodes, occ, samples, touched = counts["nodes"], counts["occ"], counts["samples"], counts["touched"]
     n = args.batch
-    launches = {"render": "march_chunks_fwd + march_combine (with the MSE gradient)",
+    launches = {"render": "march_chunks_fwd (chunks, then each ray's combine with the MSE gradient)",
                 "render_backward": "march_chunks_bwd",
                 "rmsprop_step": "rms_compact + rms_apply", "tv_grad": "tv_kernel"}
     # the dominant kernel: the largest share of the timed (overlapped) step's critical path, from its stage

@@ -298,6 +298,7 @@ plx_status march_state(const plx_grid *grid, const float *d_origins, const float
     char *b = static_cast<char *>(d_state);
     ptrs->hdr = reinterpret_cast<plx::MarchHeader *>(b + L.hdr_off);
     ptrs->n_occ = reinterpret_cast<int32_t *>(b + L.nocc_off);
+    ptrs->done = reinterpret_cast<int32_t *>(b + L.done_off);
     ptrs->range = reinterpret_cast<int2 *>(b + L.first_off);
     ptrs->items = reinterpret_cast<int2 *>(b + L.items_off);
     ptrs->part = reinterpret_cast<float4 *>(b + L.part_off);

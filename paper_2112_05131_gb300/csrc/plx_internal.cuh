@@ -419,7 +419,7 @@ enum : int32_t { kMarchChunked = 1, kMarchRecompute = 2 };
 constexpr size_t kRaySetupBytes = 128;  // the march's per-ray setup (RaySetup, plx_march.cuh)
 
 struct MarchLayout {
-    size_t hdr_off, nocc_off, first_off, items_off, part_off, live_off, samp_off, vals_off, setup_off, total;
+    size_t hdr_off, nocc_off, done_off, first_off, items_off, part_off, live_off, samp_off, vals_off, setup_off, total;
     // the plan stores each chunk's sample indices (uint16) when every index fits
     static bool store_samples(int max_chunks) { return (int64_t)max_chunks * 32 <= 65536; }
     static size_t round256(size_t b) { return (b + 255) & ~size_t(255); }
@@ -428,7 +428,8 @@ struct MarchLayout {
         const size_t slots = size_t(n) * size_t(max_chunks);
         L.hdr_off = 0;
         L.nocc_off = 256;
-        L.first_off = L.nocc_off + round256(size_t(n) * 4);
+        L.done_off = L.nocc_off + round256(size_t(n) * 4);
+        L.first_off = L.done_off + round256(size_t(n) * 4);
         L.items_off = L.first_off + round256(slots * 8);
         L.part_off = L.items_off + round256(slots * 8);
         L.live_off = L.part_off + round256(slots * 16);
@@ -443,6 +444,7 @@ struct MarchLayout {
 struct MarchPtrs {
     MarchHeader *hdr;
     int32_t *n_occ;   // [n] compacted samples per ray
+    int32_t *done;    // [n] the ray's chunks the forward has finished (set to 0 by the plan)
     int2 *range;      // [n][max_chunks] the sample-index range [first, last + 1) of each chunk
     int2 *items;      // [total_items] (ray, chunk)
     float4 *part;     // [n][max_chunks] (C_loc, P), then (R_after, T_before)

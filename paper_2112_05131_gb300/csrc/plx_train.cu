@@ -13,7 +13,8 @@
 //   chunks   (one resident wave, warps stride over the items)
 //                              gathers a chunk and composites it from T = 1:
 //                              local colour C_loc and transmittance product P;
-//   combine  (warp per ray)    T_before(k) = prod_{j<k} P_j, C = sum_k
+//   combine  (in the chunks kernel, by the warp that finishes a ray's last chunk)
+//                              T_before(k) = prod_{j<k} P_j, C = sum_k
 //                              T_before(k) C_loc(k) + T_end bg, and, for the
 //                              adjoint, R_after(k) = sum_{j>k} T_before(j)
 //                              C_loc(j) + T_end bg (a suffix sum of
@@ -41,7 +42,6 @@ namespace {
 
 constexpr int kPlanWarps = 4;
 constexpr int kChunkWarps = 4;
-constexpr int kCombineWarps = 8;
 
 int sm_count() {
     static std::mutex mu;
@@ -175,6 +175,7 @@ __global__ void __launch_bounds__(kPlanWarps * 32) march_plan_kernel(GridView g,
                 for (int k = 0; k < nch; ++k) st.items[base + k] = make_int2((int)ray, k);
             }
             st.n_occ[ray] = n_occ;
+            st.done[ray] = 0;
         }
         __syncthreads();  // the next ray reuses the shared setup
     }
@@ -260,78 +261,14 @@ __device__ __forceinline__ int item_samples(const GridView &g, const RaySetup &r
     return cnt;
 }
 
-// ---------------------------------------------------------------------------- chunks (forward)
-template <int FORM>
-__global__ void __launch_bounds__(kChunkWarps * 32, kGatherBlocks) march_chunks_fwd_kernel(
-    GridView g, const float *__restrict__ ro, const float *__restrict__ rd, RenderParams p, MarchPtrs st,
-    MarchHeader expect) {
-    __shared__ int s_buf[kChunkWarps][32];
-    __shared__ SetupPipe s_pipe[kChunkWarps];
-    const int lane = threadIdx.x & 31;
-    const int wid = threadIdx.x >> 5;
-    const MarchHeader h = *st.hdr;
-    if (!header_matches(h, expect)) {  // no plan of these rays: nothing to march (reported by the combine)
-        return;
-    }
-    const int total = h.total_items;
-    const int stride = gridDim.x * kChunkWarps;
-    const int mc = st.max_chunks;
-    int it = blockIdx.x * kChunkWarps + wid;
-    ItemIn cur = load_item(st, ro, rd, item_at(st, it, total), lane);
-    setup_fetch(s_pipe[wid], 0, st, cur.ray, lane);
-    int2 id_next = item_at(st, it + stride, total);
-    int buf = 0;
-    for (; it < total; it += stride, buf ^= 1) {
-        const ItemIn nxt = load_item(st, ro, rd, id_next, lane);
-        setup_fetch(s_pipe[wid], buf ^ 1, st, nxt.ray, lane);
-        id_next = item_at(st, it + 2 * stride, total);
-        const int64_t ray = cur.ray;
-        const int k = cur.k;
-        setup_wait_prev();
-        const RaySetup &rs = s_pipe[wid].slot[buf];
-        int s;
-        const int cnt = item_samples(g, rs, p, st, cur, s_buf[wid], lane, s);
-        cur = nxt;
-        if (cnt < 0) {
-            __syncwarp();
-            continue;
-        }
-        const bool valid = lane < cnt;
-        float sig = 0.0f, col[3] = {0.0f, 0.0f, 0.0f};
-        if (valid) {
-            DF gc[3];
-            coords_at(rs, s, gc);
-            float acc[kNV];
-            int32_t rr[8];
-            float ff[3];
-            gather_sample<true>(g, FORM, gc, acc, rr, ff);
-            sig = fmaxf(acc[0], 0.0f);
-            float pre[3];
-            colour_of(acc, rs.Y, pre, col);
-            if (st.vals) st.vals[(ray * mc + k) * 32 + lane] = make_float4(sig, pre[0], pre[1], pre[2]);
-        }
-        const Composite cp = composite(sig, valid, 1.0f, p, lane);  // stop_thresh is 0 on this path
-        const float w = cp.take ? cp.T * cp.alpha : 0.0f;
-        const float c0 = warp_sum(w * col[0]);
-        const float c1 = warp_sum(w * col[1]);
-        const float c2 = warp_sum(w * col[2]);
-        const unsigned live = __ballot_sync(kFull, valid && sig > 0.0f);
-        if (lane == 0) {
-            st.part[ray * mc + k] = make_float4(c0, c1, c2, cp.chunk_prod);
-            st.live[ray * mc + k] = live ? 1 : 0;
-        }
-        __syncwarp();  // every lane is done with this slot before the next fetch overwrites it
-    }
-    asm volatile("cp.async.wait_all;\n" ::: "memory");
-}
-
 // ---------------------------------------------------------------------------- combine
-// One ray's combine: T before each chunk, the colour (and, with `target`, the MSE gradient and the
-// ray's squared error into *loss_slot), and the colour arriving after each chunk for the adjoint.
-__device__ __forceinline__ void combine_ray(const RenderParams &p, const MarchPtrs &st, int64_t ray, int lane,
-                                            float *__restrict__ rgb, float *__restrict__ T_out,
-                                            const float *__restrict__ target, float *__restrict__ grad_rgb,
-                                            float inv_n, float *loss_slot) {
+// One ray's combine: T before each chunk, the colour (and, with `target`, the MSE gradient 2 (C - target)
+// / n of Sec. 3.5), and the colour arriving after each chunk for the adjoint.  Returns, in lane 0, the
+// ray's squared error |C - target|^2 (0 without a target).
+__device__ __forceinline__ float combine_ray(const RenderParams &p, const MarchPtrs &st, int64_t ray, int lane,
+                                             float *__restrict__ rgb, float *__restrict__ T_out,
+                                             const float *__restrict__ target, float *__restrict__ grad_rgb,
+                                             float inv_n) {
     const int mc = st.max_chunks;
     const int nch = (st.n_occ[ray] + 31) >> 5;
     float4 *part = st.part + ray * mc;
@@ -355,8 +292,8 @@ __device__ __forceinline__ void combine_ray(const RenderParams &p, const MarchPt
     C[0] = warp_sum(C[0]);
     C[1] = warp_sum(C[1]);
     C[2] = warp_sum(C[2]);
+    float sq = 0.0f;
     if (lane == 0) {
-        float sq = 0.0f;
 #pragma unroll
         for (int ch = 0; ch < 3; ++ch) {
             const float c = fmaf(Tc, p.bg[ch], C[ch]);
@@ -368,7 +305,6 @@ __device__ __forceinline__ void combine_ray(const RenderParams &p, const MarchPt
             }
         }
         if (T_out) T_out[ray] = Tc;
-        if (loss_slot) *loss_slot = sq;
     }
     // reverse over chunks: the colour that arrives after each chunk
     float Rs[3] = {Tc * p.bg[0], Tc * p.bg[1], Tc * p.bg[2]};
@@ -388,37 +324,98 @@ __device__ __forceinline__ void combine_ray(const RenderParams &p, const MarchPt
         }
         if (valid) part[k] = make_float4(Ra[0], Ra[1], Ra[2], q.w);
     }
+    return sq;
 }
 
-// With `target`, the kernel also forms the MSE gradient 2 (C - target) / n (Sec. 3.5) and adds
-// L = sum |C - target|^2 / n to *loss (one atomic per CTA).
-__global__ void __launch_bounds__(kCombineWarps * 32) march_combine_kernel(GridView g, int64_t n, RenderParams p,
-                                                                           MarchPtrs st, MarchHeader expect,
-                                                                           float *__restrict__ rgb,
-                                                                           float *__restrict__ T_out,
-                                                                           const float *__restrict__ target,
-                                                                           float *__restrict__ grad_rgb,
-                                                                           float *__restrict__ loss, float inv_n) {
-    __shared__ float s_loss[kCombineWarps];
+// ---------------------------------------------------------------------------- chunks (forward)
+// The warp that finishes a ray's last chunk (a counter per ray, after a fence that publishes the chunk)
+// combines the ray (combine_ray); after the items, the warps combine the rays without chunks.  With
+// `target`, L = sum |C - target|^2 / n is added to *loss (one atomic per CTA).
+template <int FORM>
+__global__ void __launch_bounds__(kChunkWarps * 32, kGatherBlocks) march_chunks_fwd_kernel(
+    GridView g, const float *__restrict__ ro, const float *__restrict__ rd, RenderParams p, MarchPtrs st,
+    MarchHeader expect, int64_t n, float *__restrict__ rgb, float *__restrict__ T_out,
+    const float *__restrict__ target, float *__restrict__ grad_rgb, float *__restrict__ loss, float inv_n) {
+    __shared__ int s_buf[kChunkWarps][32];
+    __shared__ SetupPipe s_pipe[kChunkWarps];
+    __shared__ float s_loss[kChunkWarps];
     const int lane = threadIdx.x & 31;
     const int wid = threadIdx.x >> 5;
-    const int64_t ray = (int64_t)blockIdx.x * kCombineWarps + wid;
-    if (target && loss && lane == 0) s_loss[wid] = 0.0f;
-    if (!header_matches(*st.hdr, expect)) {  // uniform over the grid: no plan of these rays
+    const MarchHeader h = *st.hdr;
+    if (!header_matches(h, expect)) {  // uniform over the grid: no plan of these rays
         if (blockIdx.x == 0 && threadIdx.x == 0) report(g.status, kDevStateMismatch);
         return;
     }
-    if (ray < n) combine_ray(p, st, ray, lane, rgb, T_out, target, grad_rgb, inv_n, target && loss ? &s_loss[wid] : nullptr);
+    float sq_warp = 0.0f;  // lane 0: the squared errors of the rays this warp combined
+    const int total = h.total_items;
+    const int stride = gridDim.x * kChunkWarps;
+    const int mc = st.max_chunks;
+    int it = blockIdx.x * kChunkWarps + wid;
+    ItemIn cur = load_item(st, ro, rd, item_at(st, it, total), lane);
+    setup_fetch(s_pipe[wid], 0, st, cur.ray, lane);
+    int2 id_next = item_at(st, it + stride, total);
+    int buf = 0;
+    for (; it < total; it += stride, buf ^= 1) {
+        const ItemIn nxt = load_item(st, ro, rd, id_next, lane);
+        setup_fetch(s_pipe[wid], buf ^ 1, st, nxt.ray, lane);
+        id_next = item_at(st, it + 2 * stride, total);
+        const int64_t ray = cur.ray;
+        const int k = cur.k;
+        const int nch = (cur.n_occ + 31) >> 5;
+        setup_wait_prev();
+        const RaySetup &rs = s_pipe[wid].slot[buf];
+        int s;
+        int cnt = item_samples(g, rs, p, st, cur, s_buf[wid], lane, s);
+        cur = nxt;
+        if (cnt < 0) cnt = 0;  // a rescan that disagrees with the plan (reported): the chunk adds nothing
+        const bool valid = lane < cnt;
+        float sig = 0.0f, col[3] = {0.0f, 0.0f, 0.0f};
+        if (valid) {
+            DF gc[3];
+            coords_at(rs, s, gc);
+            float acc[kNV];
+            int32_t rr[8];
+            float ff[3];
+            gather_sample<true>(g, FORM, gc, acc, rr, ff);
+            sig = fmaxf(acc[0], 0.0f);
+            float pre[3];
+            colour_of(acc, rs.Y, pre, col);
+            if (st.vals) st.vals[(ray * mc + k) * 32 + lane] = make_float4(sig, pre[0], pre[1], pre[2]);
+        }
+        const Composite cp = composite(sig, valid, 1.0f, p, lane);  // stop_thresh is 0 on this path
+        const float w = cp.take ? cp.T * cp.alpha : 0.0f;
+        const float c0 = warp_sum(w * col[0]);
+        const float c1 = warp_sum(w * col[1]);
+        const float c2 = warp_sum(w * col[2]);
+        const unsigned live = __ballot_sync(kFull, valid && sig > 0.0f);
+        int finished = 0;
+        if (lane == 0) {
+            st.part[ray * mc + k] = make_float4(c0, c1, c2, cp.chunk_prod);
+            st.live[ray * mc + k] = live ? 1 : 0;
+            __threadfence();  // the chunk is visible before the count says so
+            finished = atomicAdd(st.done + ray, 1) + 1;
+        }
+        finished = __shfl_sync(kFull, finished, 0);
+        if (finished == nch) {  // uniform: every chunk of the ray is in; combine it
+            __threadfence();
+            sq_warp += combine_ray(p, st, ray, lane, rgb, T_out, target, grad_rgb, inv_n);
+        }
+        __syncwarp();  // every lane is done with this slot before the next fetch overwrites it
+    }
+    asm volatile("cp.async.wait_all;\n" ::: "memory");
+    // the rays without a chunk (no sample in a non-empty cell): colour = background
+    for (int64_t ray = (int64_t)blockIdx.x * kChunkWarps + wid; ray < n; ray += (int64_t)gridDim.x * kChunkWarps)
+        if (st.n_occ[ray] == 0) sq_warp += combine_ray(p, st, ray, lane, rgb, T_out, target, grad_rgb, inv_n);
     if (target && loss) {
+        if (lane == 0) s_loss[wid] = sq_warp;
         __syncthreads();
         if (threadIdx.x == 0) {
             float acc = 0.0f;
-            for (int w = 0; w < kCombineWarps; ++w) acc += s_loss[w];
+            for (int w = 0; w < kChunkWarps; ++w) acc += s_loss[w];
             if (acc != 0.0f) atomicAdd(loss, acc * inv_n);
         }
     }
 }
-
 
 // ---------------------------------------------------------------------------- adjoint
 
@@ -554,12 +551,13 @@ cudaError_t launch_render_planned(const GridView &g, const float *o, const float
     }
     if (n == 0) return cudaSuccess;
     const unsigned grid = chunk_grid(n, st.max_chunks);
+    const float inv_n = (float)(1.0 / (double)n);
     if (g.form == PLX_SH_F32)
-        march_chunks_fwd_kernel<PLX_SH_F32><<<grid, kChunkWarps * 32, 0, s>>>(g, o, d, p, st, hdr);
+        march_chunks_fwd_kernel<PLX_SH_F32><<<grid, kChunkWarps * 32, 0, s>>>(g, o, d, p, st, hdr, n, rgb, T_end,
+                                                                                target, grad_rgb, loss, inv_n);
     else
-        march_chunks_fwd_kernel<PLX_SH_BF16><<<grid, kChunkWarps * 32, 0, s>>>(g, o, d, p, st, hdr);
-    march_combine_kernel<<<(unsigned)((n + kCombineWarps - 1) / kCombineWarps), kCombineWarps * 32, 0, s>>>(
-        g, n, p, st, hdr, rgb, T_end, target, grad_rgb, loss, (float)(1.0 / (double)n));
+        march_chunks_fwd_kernel<PLX_SH_BF16><<<grid, kChunkWarps * 32, 0, s>>>(g, o, d, p, st, hdr, n, rgb, T_end,
+                                                                                 target, grad_rgb, loss, inv_n);
     return cudaGetLastError();
 }
 

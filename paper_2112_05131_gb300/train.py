@@ -26,8 +26,9 @@ from . import _lib as L
 from .grid import ROW, Grid, RenderOpts, _need, _p, _stream, gen_rays
 
 # kernels one step enqueues with stop_thresh = 0: gen_rays, march_plan (header, setup, plan),
-# render_planned_mse (chunks, combine with the MSE gradient), backward_train, tv, rmsprop (compact, apply)
-LAUNCHES_PER_STEP = 10
+# render_planned_mse (chunks, each ray combined with the MSE gradient by the warp that finishes it),
+# backward_train, tv, rmsprop (compact, apply)
+LAUNCHES_PER_STEP = 9
 
 
 def lr_sigma(step: int, init: float = 30.0, final: float = 0.05, max_steps: int = 250000, delay_steps: int = 15000,
