@@ -474,11 +474,12 @@ def extras(args, wl, dev_batches, cams_t, gt_grid, opts, timed_loop, st32, ms32,
                           "GBps": {k: per_launch[k] / (st32[k] / 1e3) / 1e9 for k in per_launch},
                           "frac_of_peak": {k: per_launch[k] / (st32[k] / 1e3) / 1e9 / peak for k in per_launch}}
     # the forward march's own roofline on the training batch (the frame kernel's is in render.*.roofline)
+    fwd_traffic, fwd_traffic_note = profiled_traffic("render", args.workload)
     res["roofline_forward"] = {"batch": {
         "kernel": launches["render"], "bound": "hbm", "achieved": per_launch["render"] / (st32["render"] / 1e3) / 1e9,
         "peak": peak, "unit": "GB/s", "frac": per_launch["render"] / (st32["render"] / 1e3) / 1e9 / peak,
-        "algorithmic_bytes_per_launch": per_launch["render"], "rays": n,
-        "timing": "CUDA events around the stage, serial run"}}
+        "algorithmic_bytes_per_launch": per_launch["render"], "rays": n, "traffic": fwd_traffic,
+        "traffic_source": fwd_traffic_note, "timing": "CUDA events around the stage, serial run"}}
 
     # ---- end to end through the public API with host buffers (page-locked), copies inside the timed region:
     # each step is one plx_trainer_step_host call, which uploads the next batch's inputs (pixel ids, targets,
