@@ -41,6 +41,9 @@ namespace plx {
 namespace {
 
 constexpr int kPlanWarps = 4;
+// Batches up to this many rays combine each ray inside the chunk kernel (one launch fewer on the
+// step's critical path); larger ones launch the combine as a kernel of its own.
+constexpr int64_t kFuseCombineMaxRays = 32768;
 constexpr int kChunkWarps = 4;
 
 int sm_count() {
@@ -328,13 +331,15 @@ __device__ __forceinline__ float combine_ray(const RenderParams &p, const MarchP
 }
 
 // ---------------------------------------------------------------------------- chunks (forward)
-// The warp that finishes a ray's last chunk (a counter per ray, after a fence that publishes the chunk)
-// combines the ray (combine_ray); after the items, the warps combine the rays without chunks.  With
-// `target`, L = sum |C - target|^2 / n is added to *loss (one atomic per CTA).
+// With `fuse`, the warp that finishes a ray's last chunk (a counter per ray, after a fence that publishes
+// the chunk) combines the ray (combine_ray), and after the items the warps combine the rays without
+// chunks; with `target`, L = sum |C - target|^2 / n is added to *loss (one atomic per CTA).  For large
+// batches (kFuseCombineMaxRays) the combine is a kernel of its own instead: the resident wave would
+// otherwise combine tens of rays per warp, one dependent round trip after another.
 template <int FORM>
 __global__ void __launch_bounds__(kChunkWarps * 32, kGatherBlocks) march_chunks_fwd_kernel(
     GridView g, const float *__restrict__ ro, const float *__restrict__ rd, RenderParams p, MarchPtrs st,
-    MarchHeader expect, int64_t n, float *__restrict__ rgb, float *__restrict__ T_out,
+    MarchHeader expect, int fuse, int64_t n, float *__restrict__ rgb, float *__restrict__ T_out,
     const float *__restrict__ target, float *__restrict__ grad_rgb, float *__restrict__ loss, float inv_n) {
     __shared__ int s_buf[kChunkWarps][32];
     __shared__ SetupPipe s_pipe[kChunkWarps];
@@ -343,7 +348,7 @@ __global__ void __launch_bounds__(kChunkWarps * 32, kGatherBlocks) march_chunks_
     const int wid = threadIdx.x >> 5;
     const MarchHeader h = *st.hdr;
     if (!header_matches(h, expect)) {  // uniform over the grid: no plan of these rays
-        if (blockIdx.x == 0 && threadIdx.x == 0) report(g.status, kDevStateMismatch);
+        if (fuse && blockIdx.x == 0 && threadIdx.x == 0) report(g.status, kDevStateMismatch);
         return;
     }
     float sq_warp = 0.0f;  // lane 0: the squared errors of the rays this warp combined
@@ -392,17 +397,20 @@ __global__ void __launch_bounds__(kChunkWarps * 32, kGatherBlocks) march_chunks_
         if (lane == 0) {
             st.part[ray * mc + k] = make_float4(c0, c1, c2, cp.chunk_prod);
             st.live[ray * mc + k] = live ? 1 : 0;
-            __threadfence();  // the chunk is visible before the count says so
-            finished = atomicAdd(st.done + ray, 1) + 1;
+            if (fuse) {
+                __threadfence();  // the chunk is visible before the count says so
+                finished = atomicAdd(st.done + ray, 1) + 1;
+            }
         }
         finished = __shfl_sync(kFull, finished, 0);
-        if (finished == nch) {  // uniform: every chunk of the ray is in; combine it
+        if (fuse && finished == nch) {  // uniform: every chunk of the ray is in; combine it
             __threadfence();
             sq_warp += combine_ray(p, st, ray, lane, rgb, T_out, target, grad_rgb, inv_n);
         }
         __syncwarp();  // every lane is done with this slot before the next fetch overwrites it
     }
     asm volatile("cp.async.wait_all;\n" ::: "memory");
+    if (!fuse) return;
     // the rays without a chunk (no sample in a non-empty cell): colour = background
     for (int64_t ray = (int64_t)blockIdx.x * kChunkWarps + wid; ray < n; ray += (int64_t)gridDim.x * kChunkWarps)
         if (st.n_occ[ray] == 0) sq_warp += combine_ray(p, st, ray, lane, rgb, T_out, target, grad_rgb, inv_n);
@@ -412,6 +420,36 @@ __global__ void __launch_bounds__(kChunkWarps * 32, kGatherBlocks) march_chunks_
         if (threadIdx.x == 0) {
             float acc = 0.0f;
             for (int w = 0; w < kChunkWarps; ++w) acc += s_loss[w];
+            if (acc != 0.0f) atomicAdd(loss, acc * inv_n);
+        }
+    }
+}
+
+// The combine as a kernel of its own (large batches): a warp per ray; with `target`, L is added to *loss
+// (one atomic per CTA).
+constexpr int kCombineWarps = 8;
+__global__ void __launch_bounds__(kCombineWarps * 32) march_combine_kernel(GridView g, int64_t n, RenderParams p,
+                                                                           MarchPtrs st, MarchHeader expect,
+                                                                           float *__restrict__ rgb,
+                                                                           float *__restrict__ T_out,
+                                                                           const float *__restrict__ target,
+                                                                           float *__restrict__ grad_rgb,
+                                                                           float *__restrict__ loss, float inv_n) {
+    __shared__ float s_loss[kCombineWarps];
+    const int lane = threadIdx.x & 31;
+    const int wid = threadIdx.x >> 5;
+    const int64_t ray = (int64_t)blockIdx.x * kCombineWarps + wid;
+    if (!header_matches(*st.hdr, expect)) {  // uniform over the grid: no plan of these rays
+        if (blockIdx.x == 0 && threadIdx.x == 0) report(g.status, kDevStateMismatch);
+        return;
+    }
+    const float sq = ray < n ? combine_ray(p, st, ray, lane, rgb, T_out, target, grad_rgb, inv_n) : 0.0f;
+    if (target && loss) {
+        if (lane == 0) s_loss[wid] = sq;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            float acc = 0.0f;
+            for (int w = 0; w < kCombineWarps; ++w) acc += s_loss[w];
             if (acc != 0.0f) atomicAdd(loss, acc * inv_n);
         }
     }
@@ -552,12 +590,16 @@ cudaError_t launch_render_planned(const GridView &g, const float *o, const float
     if (n == 0) return cudaSuccess;
     const unsigned grid = chunk_grid(n, st.max_chunks);
     const float inv_n = (float)(1.0 / (double)n);
+    const int fuse = n <= kFuseCombineMaxRays ? 1 : 0;
     if (g.form == PLX_SH_F32)
-        march_chunks_fwd_kernel<PLX_SH_F32><<<grid, kChunkWarps * 32, 0, s>>>(g, o, d, p, st, hdr, n, rgb, T_end,
-                                                                                target, grad_rgb, loss, inv_n);
+        march_chunks_fwd_kernel<PLX_SH_F32><<<grid, kChunkWarps * 32, 0, s>>>(g, o, d, p, st, hdr, fuse, n, rgb,
+                                                                                T_end, target, grad_rgb, loss, inv_n);
     else
-        march_chunks_fwd_kernel<PLX_SH_BF16><<<grid, kChunkWarps * 32, 0, s>>>(g, o, d, p, st, hdr, n, rgb, T_end,
-                                                                                 target, grad_rgb, loss, inv_n);
+        march_chunks_fwd_kernel<PLX_SH_BF16><<<grid, kChunkWarps * 32, 0, s>>>(g, o, d, p, st, hdr, fuse, n, rgb,
+                                                                                 T_end, target, grad_rgb, loss, inv_n);
+    if (!fuse)
+        march_combine_kernel<<<(unsigned)((n + kCombineWarps - 1) / kCombineWarps), kCombineWarps * 32, 0, s>>>(
+            g, n, p, st, hdr, rgb, T_end, target, grad_rgb, loss, inv_n);
     return cudaGetLastError();
 }
 

@@ -25,9 +25,9 @@ import torch
 from . import _lib as L
 from .grid import ROW, Grid, RenderOpts, _need, _p, _stream, gen_rays
 
-# kernels one step enqueues with stop_thresh = 0: gen_rays, march_plan (header, setup, plan),
-# render_planned_mse (chunks, each ray combined with the MSE gradient by the warp that finishes it),
-# backward_train, tv, rmsprop (compact, apply)
+# kernels one step of up to 32768 rays enqueues with stop_thresh = 0: gen_rays, march_plan (header, setup,
+# plan), render_planned_mse (chunks, each ray combined with the MSE gradient by the warp that finishes it;
+# larger batches launch the combine separately), backward_train, tv, rmsprop (compact, apply)
 LAUNCHES_PER_STEP = 9
 
 

@@ -25,8 +25,9 @@ def _batches(gt_grid, cams_t, n, k, R):
 
 def test_host_fed_steps_equal_device_fed_steps(cuda_lib):
     """Zero learning rates keep the rows fixed, so every step of both trainers sees the same grid: the loss
-    of each step and its gradient (adjoint and TV) agree up to the order of FP32 atomic additions (the
-    colours are the same bits; the loss is their warps' sum, added atomically).  Steps are staged by the previous call except step 2,
+    of each step and its gradient (adjoint and TV) agree up to the order of FP32 additions (the colours
+    are the same bits; the loss is an FP32 sum of the rays' squared errors whose grouping depends on which
+    warp finishes which ray: 1e-5 relative bounds it for 2000 rays).  Steps are staged by the previous call except step 2,
     whose inputs are uploaded at its own start."""
     from paper_2112_05131_gb300.grid import Grid, RenderOpts
     from paper_2112_05131_gb300.train import StepConfig, Trainer
@@ -55,7 +56,7 @@ def test_host_fed_steps_equal_device_fed_steps(cuda_lib):
         nxt = hb[s + 1] if s + 1 < K and s != 1 else None
         tb.step_host(hb[s], 0.0, 0.0, next_batch=nxt, loss_out=loss_out)
         torch.cuda.synchronize()
-        assert abs(loss_out.item() - ta.loss.item()) <= 1e-6 * abs(ta.loss.item()), (s, loss_out.item(), ta.loss.item())
+        assert abs(loss_out.item() - ta.loss.item()) <= 1e-5 * abs(ta.loss.item()), (s, loss_out.item(), ta.loss.item())
         g_a, g_b = ta.grad[:, :28].cpu().numpy(), tb.grad[:, :28].cpu().numpy()
         tol = 1e-4 * np.maximum(np.abs(g_a), 1e-3 * np.abs(g_a).max())  # the gradient tolerance of the parity tests
         w = float(np.max(np.abs(g_b - g_a) / tol))

@@ -66,7 +66,8 @@ def test_train_march_dense32(cuda_lib, form, stop):
 
 
 @pytest.mark.parametrize("form", [0, 1])
-@pytest.mark.parametrize("R,n", [(48, 1237), (67, 3001)])  # several CTAs, ragged tails of rays and chunks
+@pytest.mark.parametrize("R,n", [(48, 1237), (67, 3001),
+                                 (96, 40011)])  # several CTAs, ragged tails; the last above the fused-combine limit
 def test_train_march_sparse(cuda_lib, R, n, form):
     from paper_2112_05131_gb300.grid import RenderOpts
 
