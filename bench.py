@@ -768,6 +768,12 @@ def coarse_to_fine(args, wl, cams_t, gt_grid, opts, paper=False):
     else:
         cfg = C2FConfig(steps=args.c2f_steps, upsample_at=(args.c2f_steps // 3, 2 * args.c2f_steps // 3),
                         prune_by=args.c2f_prune, track_touched=True, touched_every=500)
+    # untimed warm-up: a short run at 32^3 through every operation the timed run uses (the batch sampler's
+    # torch ops, the step, prune, upsample), so that no first-use cost of a library kernel (a driver JIT of
+    # a kernel shipped without code for this GPU took ~4 s on a fresh box) lands in the timed wall
+    warm = C2FConfig(steps=8, start_reso=32, upsample_at=(4,), prune_by=cfg.prune_by, prune_tau=-1e30,
+                     weight_tau=-1.0, chunk=4)  # thresholds that keep every row
+    train(images, cams_t, W, H, warm)
     log = []
     torch.cuda.synchronize()
     t0 = time.perf_counter()
@@ -778,7 +784,7 @@ def coarse_to_fine(args, wl, cams_t, gt_grid, opts, paper=False):
            "prune_by": cfg.prune_by, "tv_until": cfg.tv_until, "wall_s": wall, "steps_per_s": cfg.steps / wall,
            "stages": log, "final_reso": g.reso, "final_rows": g.M,
            "psnr_test_db": psnr(final, truth), "views": {"train": images.shape[0], "test": truth.shape[0]},
-           "images_render_s": prep}
+           "images_render_s": prep, "warm_up": "8 untimed steps at 32^3 with one prune and upsample first"}
     del g, images, truth, final
     return out
 
