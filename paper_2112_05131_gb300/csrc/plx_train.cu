@@ -45,6 +45,9 @@ constexpr int kPlanWarps = 4;
 // step's critical path); larger ones launch the combine as a kernel of its own.
 constexpr int64_t kFuseCombineMaxRays = 32768;
 constexpr int kChunkWarps = 4;
+// Resident CTAs per SM of the forward chunk kernel: 80 registers (at 4, 5 and 8 CTAs, 128, 96 and 64
+// registers, the 5000-ray step measured 109.1, 109.0 and 111.2 us against 106.8 us at 6).
+constexpr int kChunkFwdBlocks = 6;
 
 int sm_count() {
     static std::mutex mu;
@@ -337,7 +340,7 @@ __device__ __forceinline__ float combine_ray(const RenderParams &p, const MarchP
 // batches (kFuseCombineMaxRays) the combine is a kernel of its own instead: the resident wave would
 // otherwise combine tens of rays per warp, one dependent round trip after another.
 template <int FORM>
-__global__ void __launch_bounds__(kChunkWarps * 32, kGatherBlocks) march_chunks_fwd_kernel(
+__global__ void __launch_bounds__(kChunkWarps * 32, kChunkFwdBlocks) march_chunks_fwd_kernel(
     GridView g, const float *__restrict__ ro, const float *__restrict__ rd, RenderParams p, MarchPtrs st,
     MarchHeader expect, int fuse, int64_t n, float *__restrict__ rgb, float *__restrict__ T_out,
     const float *__restrict__ target, float *__restrict__ grad_rgb, float *__restrict__ loss, float inv_n) {
@@ -588,7 +591,7 @@ cudaError_t launch_render_planned(const GridView &g, const float *o, const float
         return e;
     }
     if (n == 0) return cudaSuccess;
-    const unsigned grid = chunk_grid(n, st.max_chunks);
+    const unsigned grid = chunk_grid(n, st.max_chunks, kChunkFwdBlocks);
     const float inv_n = (float)(1.0 / (double)n);
     const int fuse = n <= kFuseCombineMaxRays ? 1 : 0;
     if (g.form == PLX_SH_F32)
