@@ -18,6 +18,7 @@ struct plx_grid {
     char *ws;
     plx::WorkspaceLayout layout;
     plx::GridView view;
+    int rms_parity;  // which of the two list lengths the next sparse RMSProp call uses
 };
 
 namespace {
@@ -522,9 +523,19 @@ plx_status plx_rmsprop_step(plx_grid *grid, float *d_grad_rows, float *d_v, floa
     if (!(beta >= 0.0f && beta < 1.0f) || !(eps >= 0.0f) || !std::isfinite(lr_sigma) || !std::isfinite(lr_sh))
         return fail(PLX_EINVAL, "bad RMSProp hyper-parameters");
     if (sparse != 0 && sparse != 1) return fail(PLX_EINVAL, "sparse must be 0 or 1");
-    return cuda_status(plx::launch_rmsprop(grid->view, grid->rows, grid->desc.sh_form == PLX_SH_BF16 ? grid->rows_h : nullptr,
-                                           d_grad_rows, d_v, lr_sigma, lr_sh, beta, eps, sparse,
-                                           static_cast<cudaStream_t>(stream)), "plx_rmsprop_step");
+    // sparse calls alternate between the status block's two list lengths: each starts at zero (the
+    // block is zeroed at creation) and the call that uses one zeroes the other for the next call
+    plx::GridView v = grid->view;
+    char *status = grid->ws + grid->layout.status_off;
+    const size_t off[2] = {plx::WorkspaceLayout::kListCountOff, plx::WorkspaceLayout::kListCount2Off};
+    v.tcount = reinterpret_cast<int *>(status + off[grid->rms_parity]);
+    int *next = reinterpret_cast<int *>(status + off[grid->rms_parity ^ 1]);
+    const plx_status r = cuda_status(plx::launch_rmsprop(v, grid->rows, grid->desc.sh_form == PLX_SH_BF16 ? grid->rows_h : nullptr,
+                                                         d_grad_rows, d_v, lr_sigma, lr_sh, beta, eps, sparse,
+                                                         sparse ? next : nullptr, static_cast<cudaStream_t>(stream)),
+                                     "plx_rmsprop_step");
+    if (r == PLX_OK && sparse) grid->rms_parity ^= 1;
+    return r;
 }
 
 size_t plx_prune_workspace_bytes(int32_t reso) {

@@ -62,7 +62,8 @@ __host__ __device__ inline int64_t coarse_blocks_per_axis(int64_t R) { return ((
 
 struct WorkspaceLayout {
     size_t status_off, occ_off, coarse_off, touched_off, list_off, total;
-    static constexpr size_t kListCountOff = 64;
+    static constexpr size_t kListCountOff = 64;   // two list lengths, used by alternate sparse RMSProp calls
+    static constexpr size_t kListCount2Off = 96;
     static constexpr size_t kOccBoxOff = 128;
     static size_t round256(size_t b) { return (b + 255) & ~size_t(255); }
     static WorkspaceLayout make(int64_t R, int64_t M) {
@@ -486,8 +487,10 @@ cudaError_t launch_pack_bf16(const GridView &g, uint16_t *rows_h, cudaStream_t s
 cudaError_t launch_tv(const GridView &g, const int64_t *seg_start, const int64_t *seg_len, int64_t n_seg,
                       int64_t n_selected, float scale_sigma, float scale_sh, float *grad_rows, float *loss,
                       cudaStream_t s);
+// sparse: g.tcount is this call's list length (zero on entry), next_count the next call's (zeroed here)
 cudaError_t launch_rmsprop(const GridView &g, float *rows, uint16_t *rows_h, float *grad, float *v,
-                           float lr_sigma, float lr_sh, float beta, float eps, int sparse, cudaStream_t s);
+                           float lr_sigma, float lr_sh, float beta, float eps, int sparse, int *next_count,
+                           cudaStream_t s);
 
 // prune / upsample (plx_gridops.cu)
 size_t prune_ws_bytes(int64_t R);

@@ -420,15 +420,25 @@ __global__ void __launch_bounds__(1024) count_touched_kernel(GridView g, int64_t
     }
 }
 
-// Sparse mode, pass 1: the rows marked in the touched bitmask, as a list, and the mask cleared.  A
-// warp takes 32 mask words at a time; the order of the list does not matter (rows update independently).
-__global__ void __launch_bounds__(256) rms_compact_kernel(GridView g, int64_t n_words) {
+// Sparse mode, pass 1: the rows marked in the touched bitmask, as a list, and the mask cleared.  A CTA
+// takes 256 consecutive mask words at a time (a word per thread), adds its count to the list's length
+// with one atomic and writes its rows in ascending order: warp by warp, then word by word, the lanes of
+// a word's set bits storing consecutive entries (one coalesced store per non-empty word).  The list is
+// ascending within each CTA's range, which keeps the update's row accesses in long ascending runs.
+// The count this call's update reads starts at zero; the call also zeroes the other count, which the
+// next call uses (the two alternate, so no separate reset sits between the adjoint and the update).
+constexpr int kCompactThreads = 256;
+__global__ void __launch_bounds__(kCompactThreads) rms_compact_kernel(GridView g, int64_t n_words,
+                                                                      int *__restrict__ next_count) {
     chain_release();  // the update (chained) may be scheduled as this pass drains
+    __shared__ int s_warp[kCompactThreads / 32];
+    __shared__ int s_base;
     const int lane = threadIdx.x & 31;
-    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int64_t n_warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    for (int64_t w0 = warp * 32; w0 < n_words; w0 += n_warps * 32) {
-        const int64_t w = w0 + lane;
+    const int wid = threadIdx.x >> 5;
+    const unsigned lt = (1u << lane) - 1u;
+    if (blockIdx.x == 0 && threadIdx.x == 0) *next_count = 0;
+    for (int64_t c0 = (int64_t)blockIdx.x * kCompactThreads; c0 < n_words; c0 += (int64_t)gridDim.x * kCompactThreads) {
+        const int64_t w = c0 + threadIdx.x;
         uint32_t word = 0u;
         if (w < n_words) {
             word = g.touched[w];
@@ -443,15 +453,29 @@ __global__ void __launch_bounds__(256) rms_compact_kernel(GridView g, int64_t n_
             const int t = __shfl_up_sync(kFull, incl, off);
             if (lane >= off) incl += t;
         }
-        const int total = __shfl_sync(kFull, incl, 31);
-        int base = 0;
-        if (lane == 0 && total) base = atomicAdd(g.tcount, total);
-        base = __shfl_sync(kFull, base, 0) + incl - c;
-        while (word) {
-            const int b = __ffs(word) - 1;
-            word &= word - 1u;
-            g.tlist[base++] = (int32_t)(w * 32 + b);
+        if (lane == 31) s_warp[wid] = incl;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            int tot = 0;
+#pragma unroll
+            for (int q = 0; q < kCompactThreads / 32; ++q) {
+                const int t = s_warp[q];
+                s_warp[q] = tot;
+                tot += t;
+            }
+            s_base = tot ? atomicAdd(g.tcount, tot) : 0;
         }
+        __syncthreads();
+        const int excl = s_base + s_warp[wid] + incl - c;  // list position of this word's first row
+        unsigned nz = __ballot_sync(kFull, word != 0u);
+        while (nz) {
+            const int src = __ffs(nz) - 1;
+            nz &= nz - 1u;
+            const uint32_t wj = __shfl_sync(kFull, word, src);
+            const int pj = __shfl_sync(kFull, excl, src);
+            if ((wj >> lane) & 1u) g.tlist[pj + __popc(wj & lt)] = (int32_t)((c0 + 32 * wid + src) * 32 + lane);
+        }
+        __syncthreads();  // s_warp and s_base are rewritten by the next round
     }
 }
 
@@ -515,7 +539,7 @@ __global__ void __launch_bounds__(256) rms_apply_kernel(GridView g, float *__res
 }
 
 cudaError_t launch_rmsprop(const GridView &g, float *rows, uint16_t *rows_h, float *grad, float *v, float lr_sigma,
-                           float lr_sh, float beta, float eps, int sparse, cudaStream_t s) {
+                           float lr_sh, float beta, float eps, int sparse, int *next_count, cudaStream_t s) {
     const int64_t n_words = (g.M + 31) / 32;
     if (n_words == 0) return cudaSuccess;
     int sms = 152;
@@ -525,10 +549,9 @@ cudaError_t launch_rmsprop(const GridView &g, float *rows, uint16_t *rows_h, flo
     }
     const int64_t apply_blocks = std::min<int64_t>((g.M + 255) / 256, (int64_t)sms * kRmsGridPerSm);
     if (sparse) {
-        cudaError_t e = cudaMemsetAsync(g.tcount, 0, sizeof(int), s);
-        if (e != cudaSuccess) return e;
-        const int64_t blocks = std::min<int64_t>((n_words + 255) / 256, (int64_t)sms * 8);
-        rms_compact_kernel<<<(unsigned)blocks, 256, 0, s>>>(g, n_words);
+        if (!next_count) return cudaErrorInvalidValue;
+        const int64_t blocks = std::min<int64_t>((n_words + kCompactThreads - 1) / kCompactThreads, (int64_t)sms * 8);
+        rms_compact_kernel<<<(unsigned)blocks, kCompactThreads, 0, s>>>(g, n_words, next_count);
         return launch_chained(rms_apply_kernel<true>, (unsigned)apply_blocks, 256, s, g, rows, rows_h, grad, v,
                               lr_sigma, lr_sh, beta, eps);
     }
