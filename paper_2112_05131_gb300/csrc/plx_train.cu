@@ -428,31 +428,100 @@ __global__ void __launch_bounds__(kChunkWarps * 32, kChunkFwdBlocks) march_chunk
     }
 }
 
-// The combine as a kernel of its own (large batches): a warp per ray; with `target`, L is added to *loss
-// (one atomic per CTA).
-constexpr int kCombineWarps = 8;
-__global__ void __launch_bounds__(kCombineWarps * 32) march_combine_kernel(GridView g, int64_t n, RenderParams p,
-                                                                           MarchPtrs st, MarchHeader expect,
-                                                                           float *__restrict__ rgb,
-                                                                           float *__restrict__ T_out,
-                                                                           const float *__restrict__ target,
-                                                                           float *__restrict__ grad_rgb,
-                                                                           float *__restrict__ loss, float inv_n) {
-    __shared__ float s_loss[kCombineWarps];
+// The combine of a ray of at most kCombineShort chunks by one thread: the same quantities as combine_ray,
+// accumulated chunk by chunk (for one or two chunks the same roundings as combine_ray's warp sums).
+// Returns the ray's squared error |C - target|^2 (0 without a target).
+constexpr int kCombineShort = 4;
+__device__ __forceinline__ float combine_short(const RenderParams &p, const MarchPtrs &st, int64_t ray, int nch,
+                                               float *__restrict__ rgb, float *__restrict__ T_out,
+                                               const float *__restrict__ target, float *__restrict__ grad_rgb,
+                                               float inv_n) {
+    float4 *part = st.part + ray * st.max_chunks;
+    float4 q[kCombineShort];
+#pragma unroll
+    for (int k = 0; k < kCombineShort; ++k) q[k] = k < nch ? part[k] : make_float4(0.0f, 0.0f, 0.0f, 1.0f);
+    float Tc = 1.0f, Tb[kCombineShort];
+    float C[3] = {0.0f, 0.0f, 0.0f};
+#pragma unroll
+    for (int k = 0; k < kCombineShort; ++k) {
+        Tb[k] = Tc;
+        if (k < nch) {
+            C[0] = __fadd_rn(C[0], __fmul_rn(Tc, q[k].x));
+            C[1] = __fadd_rn(C[1], __fmul_rn(Tc, q[k].y));
+            C[2] = __fadd_rn(C[2], __fmul_rn(Tc, q[k].z));
+            Tc *= q[k].w;
+        }
+    }
+    float sq = 0.0f;
+#pragma unroll
+    for (int ch = 0; ch < 3; ++ch) {
+        const float c = fmaf(Tc, p.bg[ch], C[ch]);
+        rgb[3 * ray + ch] = c;
+        if (target) {
+            const float diff = c - __ldg(target + 3 * ray + ch);
+            grad_rgb[3 * ray + ch] = 2.0f * diff * inv_n;
+            sq = fmaf(diff, diff, sq);
+        }
+    }
+    if (T_out) T_out[ray] = Tc;
+    // back to front: the colour arriving after each chunk
+    float R[3] = {Tc * p.bg[0], Tc * p.bg[1], Tc * p.bg[2]};
+#pragma unroll
+    for (int k = kCombineShort - 1; k >= 0; --k) {
+        if (k < nch) {
+            part[k] = make_float4(R[0], R[1], R[2], Tb[k]);
+            R[0] = __fadd_rn(R[0], __fmul_rn(Tb[k], q[k].x));
+            R[1] = __fadd_rn(R[1], __fmul_rn(Tb[k], q[k].y));
+            R[2] = __fadd_rn(R[2], __fmul_rn(Tb[k], q[k].z));
+        }
+    }
+    return sq;
+}
+
+// The combine as a kernel of its own (large batches): a thread per ray for the rays of at most
+// kCombineShort chunks (most rays), the longer rays listed in shared memory and then combined a warp per
+// ray (combine_ray); with `target`, L is added to *loss (one atomic per CTA).
+constexpr int kCombineThreads = 256;
+__global__ void __launch_bounds__(kCombineThreads) march_combine_kernel(GridView g, int64_t n, RenderParams p,
+                                                                        MarchPtrs st, MarchHeader expect,
+                                                                        float *__restrict__ rgb,
+                                                                        float *__restrict__ T_out,
+                                                                        const float *__restrict__ target,
+                                                                        float *__restrict__ grad_rgb,
+                                                                        float *__restrict__ loss, float inv_n) {
+    constexpr int kWarps = kCombineThreads / 32;
+    __shared__ int s_long[kCombineThreads];
+    __shared__ int s_nlong;
+    __shared__ float s_loss[kWarps];
     const int lane = threadIdx.x & 31;
     const int wid = threadIdx.x >> 5;
-    const int64_t ray = (int64_t)blockIdx.x * kCombineWarps + wid;
     if (!header_matches(*st.hdr, expect)) {  // uniform over the grid: no plan of these rays
         if (blockIdx.x == 0 && threadIdx.x == 0) report(g.status, kDevStateMismatch);
         return;
     }
-    const float sq = ray < n ? combine_ray(p, st, ray, lane, rgb, T_out, target, grad_rgb, inv_n) : 0.0f;
+    if (threadIdx.x == 0) s_nlong = 0;
+    __syncthreads();
+    const int64_t ray0 = (int64_t)blockIdx.x * kCombineThreads;
+    const int64_t ray = ray0 + threadIdx.x;
+    float sq = 0.0f;
+    if (ray < n) {
+        const int nch = (st.n_occ[ray] + 31) >> 5;
+        if (nch > kCombineShort)
+            s_long[atomicAdd(&s_nlong, 1)] = threadIdx.x;
+        else
+            sq = combine_short(p, st, ray, nch, rgb, T_out, target, grad_rgb, inv_n);
+    }
+    __syncthreads();
+    const int nl = s_nlong;
+    for (int i = wid; i < nl; i += kWarps)  // uniform over the warp
+        sq += combine_ray(p, st, ray0 + s_long[i], lane, rgb, T_out, target, grad_rgb, inv_n);
     if (target && loss) {
+        sq = warp_sum(sq);
         if (lane == 0) s_loss[wid] = sq;
         __syncthreads();
         if (threadIdx.x == 0) {
             float acc = 0.0f;
-            for (int w = 0; w < kCombineWarps; ++w) acc += s_loss[w];
+            for (int w = 0; w < kWarps; ++w) acc += s_loss[w];
             if (acc != 0.0f) atomicAdd(loss, acc * inv_n);
         }
     }
@@ -601,7 +670,7 @@ cudaError_t launch_render_planned(const GridView &g, const float *o, const float
         march_chunks_fwd_kernel<PLX_SH_BF16><<<grid, kChunkWarps * 32, 0, s>>>(g, o, d, p, st, hdr, fuse, n, rgb,
                                                                                  T_end, target, grad_rgb, loss, inv_n);
     if (!fuse)
-        march_combine_kernel<<<(unsigned)((n + kCombineWarps - 1) / kCombineWarps), kCombineWarps * 32, 0, s>>>(
+        march_combine_kernel<<<(unsigned)((n + kCombineThreads - 1) / kCombineThreads), kCombineThreads, 0, s>>>(
             g, n, p, st, hdr, rgb, T_end, target, grad_rgb, loss, inv_n);
     return cudaGetLastError();
 }
