@@ -64,6 +64,9 @@ def parse_args():
     ap.add_argument("--c2f-prune", choices=("density", "weight"), default="density",
                     help="coarse-to-fine pruning: density >= 5, or maximum weight >= 0.256 (Sec. 3.4)")
     ap.add_argument("--skip-large-batch", action="store_true", help="leave out the 2^18-ray batch measurement")
+    ap.add_argument("--only-large-batch", action="store_true",
+                    help="profiling aid: only the 2^18-ray batch measurement (overlapped, then serial steps), "
+                         "no 5000-ray step")
     ap.add_argument("--only-render", action="store_true",
                     help="profiling aid: only the full-frame renders of the held-out views (FP32, then BF16-SH), "
                          "no training step; the first plx_render launches are three untimed FP32 frames")
@@ -268,6 +271,11 @@ def run_ours(args, world, rank, local):
 
     if args.only_render:
         print(json.dumps({"only_render": True, "workload": args.workload, "render": frame_renders(args, wl, dev, opts)}))
+        return
+    if args.only_large_batch:
+        gt = Grid.from_host(R, wl["gt"].idx, wl["gt"].rows)
+        print(json.dumps({"only_large_batch": True, "workload": args.workload,
+                          "batch_262144": large_batch(args, wl, cams_t, gt, opts)}))
         return
 
     gt_grid = Grid.from_host(R, wl["gt"].idx, wl["gt"].rows)

@@ -28,9 +28,9 @@ constexpr unsigned kFull = 0xffffffffu;
 // is visible, so no thread touches global memory before the stream order allows (launched plainly,
 // chain_wait() returns at once).  chain_release() lets the next chained kernel be scheduled once
 // every CTA of this grid has issued it.  Only the launch latency and CTA ramp are overlapped.
-// Used for the RMSProp update after its compaction; chaining the march kernels as well made each
-// faster alone but took from the TV kernel beside them the SM slots it fills between launches, and
-// the overlapped step measured slower.
+// Used for the RMSProp update after its compaction and for the large-batch combine after the chunk
+// kernel; chaining the 5000-ray march kernels as well made each faster alone but took from the TV
+// kernel beside them the SM slots it fills between launches, and the overlapped step measured slower.
 __device__ __forceinline__ void chain_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 __device__ __forceinline__ void chain_release() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
 

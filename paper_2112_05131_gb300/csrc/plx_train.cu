@@ -347,6 +347,7 @@ __global__ void __launch_bounds__(kChunkWarps * 32, kChunkFwdBlocks) march_chunk
     __shared__ int s_buf[kChunkWarps][32];
     __shared__ SetupPipe s_pipe[kChunkWarps];
     __shared__ float s_loss[kChunkWarps];
+    chain_release();  // a chained combine (large batches) may be scheduled; it waits for this grid to finish
     const int lane = threadIdx.x & 31;
     const int wid = threadIdx.x >> 5;
     const MarchHeader h = *st.hdr;
@@ -431,7 +432,7 @@ __global__ void __launch_bounds__(kChunkWarps * 32, kChunkFwdBlocks) march_chunk
 // The combine of a ray of at most kCombineShort chunks by one thread: the same quantities as combine_ray,
 // accumulated chunk by chunk (for one or two chunks the same roundings as combine_ray's warp sums).
 // Returns the ray's squared error |C - target|^2 (0 without a target).
-constexpr int kCombineShort = 4;
+constexpr int kCombineShort = 8;
 __device__ __forceinline__ float combine_short(const RenderParams &p, const MarchPtrs &st, int64_t ray, int nch,
                                                float *__restrict__ rgb, float *__restrict__ T_out,
                                                const float *__restrict__ target, float *__restrict__ grad_rgb,
@@ -493,6 +494,7 @@ __global__ void __launch_bounds__(kCombineThreads) march_combine_kernel(GridView
     __shared__ int s_long[kCombineThreads];
     __shared__ int s_nlong;
     __shared__ float s_loss[kWarps];
+    chain_wait();  // launched chained to the chunk kernel: nothing is read before it has finished
     const int lane = threadIdx.x & 31;
     const int wid = threadIdx.x >> 5;
     if (!header_matches(*st.hdr, expect)) {  // uniform over the grid: no plan of these rays
@@ -669,10 +671,10 @@ cudaError_t launch_render_planned(const GridView &g, const float *o, const float
     else
         march_chunks_fwd_kernel<PLX_SH_BF16><<<grid, kChunkWarps * 32, 0, s>>>(g, o, d, p, st, hdr, fuse, n, rgb,
                                                                                  T_end, target, grad_rgb, loss, inv_n);
-    if (!fuse)
-        march_combine_kernel<<<(unsigned)((n + kCombineThreads - 1) / kCombineThreads), kCombineThreads, 0, s>>>(
-            g, n, p, st, hdr, rgb, T_end, target, grad_rgb, loss, inv_n);
-    return cudaGetLastError();
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess || fuse) return e;
+    return launch_chained(march_combine_kernel, (unsigned)((n + kCombineThreads - 1) / kCombineThreads),
+                          kCombineThreads, s, g, n, p, st, hdr, rgb, T_end, target, grad_rgb, loss, inv_n);
 }
 
 cudaError_t launch_render_train(const GridView &g, const float *o, const float *d, int64_t n, const RenderParams &p,
