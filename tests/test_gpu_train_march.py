@@ -117,6 +117,42 @@ def test_train_march_long_rays_many_chunks(cuda_lib):
     print(f"long rays (max {int(aux[:, 1].max())} samples): colour err/tol {wc:.3f}, grad err/tol {wg:.3f}")
 
 
+def test_train_march_large_batch_combine(cuda_lib):
+    """A batch above the fused-combine limit (33001 rays) on a dense 128^3 grid, so that the separate
+    combine kernel takes both of its paths: rays of at most 8 chunks (at most 256 samples) a thread each,
+    longer rays (up to ~430 samples) a warp each.  Colours and gradients against the oracle; the long rays
+    get the same cancellation allowance as in the long-ray test above.  Each row receives ~30 samples'
+    contributions, so the FP32 atomic sums stay within that allowance (a 40^3 grid under the same rays
+    gives rows thousands of additions, beyond what a per-path rounding bound covers).  The colours are
+    kept away from the ReLU kink (a DC term of 3 per channel, the other coefficients N(0, 0.2)): among
+    7.5 M samples with zero-mean colours a few pre-activations lie within FP32 rounding of 0, where the
+    FP32 march (its stored pre-activations interpolate the corners in slot order) and the FP64 oracle
+    may take different ReLU masks and so disagree by that sample's whole SH gradient."""
+    from paper_2112_05131_gb300.grid import RenderOpts
+
+    R = 128
+    rng = np.random.default_rng(11)
+    idx = np.arange(R ** 3, dtype=np.int32)
+    rows = np.empty((R ** 3, 28), np.float32)
+    rows[:, 0] = rng.uniform(0.0, 2.0, size=R ** 3)
+    rows[:, 1:] = rng.normal(0, 0.2, size=(R ** 3, 27))
+    rows[:, [1, 10, 19]] += 3.0
+    sc = synth.Scene(R, idx, rows)
+    n = 33001
+    o, d = synth.random_rays(n, seed=12, spread=0.9)
+    gw = (rng.normal(size=(n, 3)) * 1e-3).astype(np.float32)
+    opts = RenderOpts(0.5, BG, 0.0)
+    rgb, T, grad, ref, aux, gref, rows_ = _both(sc, o, d, gw, opts)
+    ns = aux[:, 1]
+    assert np.any(ns > 8 * 32) and np.any((ns > 32) & (ns <= 8 * 32)), (ns.max(), np.median(ns))
+    wc, _ = check_colours(rgb, ref, aux, rows_, delta_of(R, 0.5), BG)
+    mag = oracle.render_backward_mag(R, sc.idx, rows_, o.astype(float), d.astype(float), gw.astype(float),
+                                     step_vox=0.5, bg=BG)
+    wg = check_grads(grad, gref, extra_abs=FP32_CANCEL_U * mag)
+    print(f"large batch (max {int(ns.max())} samples, {int(np.sum(ns > 256))} rays above 8 chunks): "
+          f"colour err/tol {wc:.3f}, grad err/tol {wg:.3f}")
+
+
 def test_train_march_matches_render_and_is_deterministic(cuda_lib):
     from paper_2112_05131_gb300.grid import Grid, RenderOpts
 
