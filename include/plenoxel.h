@@ -341,7 +341,10 @@ plx_status plx_tv_grad(const plx_grid *grid, const int64_t *d_seg_start, const i
  *   sparse = 1: visit only rows marked in the grid's touched bitmask (by
  *               plx_render_backward / plx_tv_grad since the last step), which
  *               is exact whenever every non-zero gradient came from those calls.
- * Both modes clear the touched bitmask. */
+ * Both modes clear the touched bitmask.  Successive calls on one grid must be
+ * ordered on the device (one stream, or events between streams): a sparse
+ * call builds its row list in the grid's workspace and resets the list
+ * length that the grid's next sparse call uses. */
 plx_status plx_rmsprop_step(plx_grid *grid, float *d_grad_rows, float *d_v, float lr_sigma,
                             float lr_sh, float beta, float eps, int32_t sparse, void *stream);
 

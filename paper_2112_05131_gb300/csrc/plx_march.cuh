@@ -463,9 +463,15 @@ __device__ __forceinline__ void refill(const GridView &g, const RaySetup &rs, in
     const unsigned lt = (1u << lane) - 1u;
     while (st.tail - st.head < 32 && !st.exhausted) {
         bool occ[kCand];
-        if (test_round(g, rs, st.next, rs.s_hi, lane, occ)) {  // uniform
+        const unsigned live = test_round(g, rs, st.next, rs.s_hi, lane, occ);
+        if (live) {  // uniform
 #pragma unroll
             for (int j = 0; j < kCand; ++j) {
+                // candidates 32 j .. 32 j + 31 form the round's groups 32 j / kGroup onwards: none of them
+                // live, none occupied
+                constexpr int kPerIter = 32 / kGroup;
+                constexpr unsigned kIterMask = kPerIter >= 32 ? kFull : (1u << kPerIter) - 1u;
+                if (((live >> (kPerIter * j)) & kIterMask) == 0u) continue;  // uniform
                 const unsigned m = __ballot_sync(kFull, occ[j]);
                 if (occ[j]) ring[(st.tail + __popc(m & lt)) & (kRing - 1)] = st.next + 32 * j + lane;
                 st.tail += __popc(m);

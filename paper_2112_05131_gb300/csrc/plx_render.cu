@@ -111,15 +111,17 @@ constexpr int kFwdWarps = 4;
 constexpr int kFwdWarpsSMF32 = 24;
 constexpr int kFwdWarpsSMBF16 = 24;
 constexpr int fwd_blocks(int form) { return (form == PLX_SH_BF16 ? kFwdWarpsSMBF16 : kFwdWarpsSMF32) / kFwdWarps; }
-// Rays per warp in the render kernels: lanes 0 .. kRayBatch-1 set up that many consecutive rays at once
-// (double-float clip and anchor, SH basis, candidate range) into shared memory, and the warp then marches
-// them one after another, so the setup's cost is shared by kRayBatch rays instead of repeated in every
-// lane of every ray's warp.
+// Rays per warp in the render kernels: the rays are set up in parallel, a lane each (double-float clip
+// and anchor, SH basis, candidate range; in plx_render by the CTA's first warp for all its rays, in the
+// tiles kernel by lanes 0 .. kRayBatch-1 of each warp) into shared memory, and each warp then marches its
+// kRayBatch rays one after another, so the setup's cost is shared instead of repeated in every lane of
+// every ray's warp.
 constexpr int kRayBatch = 4;
 // The CTA's kFwdWarps * kRayBatch consecutive rays are dealt to its warps in turn (ray r of warp w is the
 // CTA's ray r kFwdWarps + w), so that neighbouring rays, which cost about the same, are spread over the
 // warps and the CTA's warps finish together.
 constexpr bool kDealRays = true;
+static_assert(kDealRays && kFwdWarps * kRayBatch <= 32, "render_fwd_kernel's first warp sets up the CTA's rays");
 __device__ __forceinline__ int64_t batch_ray(int64_t cta_ray0, int wid, int r) {
     return cta_ray0 + (kDealRays ? (int64_t)r * kFwdWarps + wid : (int64_t)wid * kRayBatch + r);
 }
@@ -179,11 +181,13 @@ __global__ void __launch_bounds__(kFwdWarps * 32, fwd_blocks(FORM)) render_fwd_k
     const int lane = threadIdx.x & 31;
     const int wid = threadIdx.x >> 5;
     const int64_t cta_ray0 = (int64_t)blockIdx.x * kFwdWarps * kRayBatch;
-    if (lane < kRayBatch) {
-        const int64_t ray = batch_ray(cta_ray0, wid, lane);
-        if (ray < n) s_rs[wid][lane] = ray_setup(g, p, ro, rd, ray);
+    // the first warp sets up all of the CTA's rays, a lane each (one pass of the setup's instructions for
+    // kFwdWarps * kRayBatch rays instead of one per warp)
+    if (wid == 0 && lane < kFwdWarps * kRayBatch) {
+        const int64_t ray = cta_ray0 + lane;  // = batch_ray(cta_ray0, lane % kFwdWarps, lane / kFwdWarps)
+        if (ray < n) s_rs[lane % kFwdWarps][lane / kFwdWarps] = ray_setup(g, p, ro, rd, ray);
     }
-    __syncwarp();
+    __syncthreads();
     for (int r = 0; r < kRayBatch; ++r) {
         const int64_t ray = batch_ray(cta_ray0, wid, r);
         if (ray >= n) break;  // uniform per warp
